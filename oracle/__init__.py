@@ -1,0 +1,128 @@
+"""CPU oracle for the LOD construction — TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+reference leg of ``bench.py`` may import this package.  The library under
+``paper_2302_14801_gb300`` never imports it and shares no code with it.
+
+``build(points, T, mode, max_depth)`` runs the plain single-threaded C++
+restatement in ``lod_oracle.cpp`` (see its header for the passages of the
+paper each step follows) and returns its output as numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lod_oracle.cpp")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+FILTER = 0
+PICK = 1
+
+
+def compile_oracle(force: bool = False) -> str:
+    """Compile the oracle with g++ (plain -O2, no target-specific flags)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(compile_oracle())
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        lib.oracle_build.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
+                                     ctypes.c_uint32, ctypes.c_uint32,
+                                     ctypes.POINTER(ctypes.c_void_p)]
+        lib.oracle_build.restype = ctypes.c_int
+        lib.oracle_n_nodes.argtypes = [ctypes.c_void_p]
+        lib.oracle_n_nodes.restype = ctypes.c_uint64
+        lib.oracle_n_voxels.argtypes = [ctypes.c_void_p]
+        lib.oracle_n_voxels.restype = ctypes.c_uint64
+        lib.oracle_get_nodes.argtypes = [ctypes.c_void_p, i32p, u8p, u8p, u8p, u8p, u32p, u32p,
+                                         u64p, u64p, u64p, u32p]
+        lib.oracle_get_nodes.restype = None
+        lib.oracle_get_voxels.argtypes = [ctypes.c_void_p, u32p]
+        lib.oracle_get_voxels.restype = None
+        lib.oracle_get_points.argtypes = [ctypes.c_void_p, i32p, u32p]
+        lib.oracle_get_points.restype = None
+        lib.oracle_free.argtypes = [ctypes.c_void_p]
+        lib.oracle_free.restype = None
+        lib.oracle_splitmix64.argtypes = [ctypes.c_uint64]
+        lib.oracle_splitmix64.restype = ctypes.c_uint64
+        _lib = lib
+    return _lib
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def splitmix64(x: int) -> int:
+    return int(_load().oracle_splitmix64(ctypes.c_uint64(x)))
+
+
+def build(points: np.ndarray, leaf_threshold: int = 50000, mode: int = FILTER,
+          max_depth: int = 21) -> dict:
+    """Run the oracle on an (N, 4) int32 point array; return numpy arrays.
+
+    Keys: ``min`` (n,3) int32, ``level``, ``log2_size``, ``child_mask``,
+    ``flags`` (uint8), ``parent``, ``first_child`` (uint32),
+    ``point_offset``, ``point_count``, ``voxel_offset`` (uint64),
+    ``voxel_count`` (uint32); ``points`` (N,4) int32 and ``index`` (N,)
+    uint32 in leaf layout order; ``voxels`` (V,4) uint32 rows of
+    (cell, rgba, count, pick_index), each node's voxels sorted by cell.
+    """
+    lib = _load()
+    pts = np.ascontiguousarray(points, dtype=np.int32).reshape(-1, 4)
+    n = pts.shape[0]
+    h = ctypes.c_void_p()
+    rc = lib.oracle_build(pts.ctypes.data if n else None, n, leaf_threshold, mode, max_depth,
+                          ctypes.byref(h))
+    if rc != 0:
+        raise ValueError(f"oracle_build failed with status {rc}")
+    try:
+        nn = int(lib.oracle_n_nodes(h))
+        nv = int(lib.oracle_n_voxels(h))
+        out = {
+            "min": np.empty((nn, 3), np.int32),
+            "level": np.empty(nn, np.uint8),
+            "log2_size": np.empty(nn, np.uint8),
+            "child_mask": np.empty(nn, np.uint8),
+            "flags": np.empty(nn, np.uint8),
+            "parent": np.empty(nn, np.uint32),
+            "first_child": np.empty(nn, np.uint32),
+            "point_offset": np.empty(nn, np.uint64),
+            "point_count": np.empty(nn, np.uint64),
+            "voxel_offset": np.empty(nn, np.uint64),
+            "voxel_count": np.empty(nn, np.uint32),
+            "voxels": np.empty((nv, 4), np.uint32),
+            "points": np.empty((n, 4), np.int32),
+            "index": np.empty(n, np.uint32),
+        }
+        lib.oracle_get_nodes(h, _ptr(out["min"], ctypes.c_int32), _ptr(out["level"], ctypes.c_uint8),
+                             _ptr(out["log2_size"], ctypes.c_uint8),
+                             _ptr(out["child_mask"], ctypes.c_uint8),
+                             _ptr(out["flags"], ctypes.c_uint8), _ptr(out["parent"], ctypes.c_uint32),
+                             _ptr(out["first_child"], ctypes.c_uint32),
+                             _ptr(out["point_offset"], ctypes.c_uint64),
+                             _ptr(out["point_count"], ctypes.c_uint64),
+                             _ptr(out["voxel_offset"], ctypes.c_uint64),
+                             _ptr(out["voxel_count"], ctypes.c_uint32))
+        lib.oracle_get_voxels(h, _ptr(out["voxels"], ctypes.c_uint32))
+        lib.oracle_get_points(h, _ptr(out["points"], ctypes.c_int32), _ptr(out["index"], ctypes.c_uint32))
+    finally:
+        lib.oracle_free(h)
+    return out

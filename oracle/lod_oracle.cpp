@@ -1,0 +1,344 @@
+// CPU oracle for the LOD construction — TEST INFRASTRUCTURE ONLY.
+//
+// Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline leg may
+// load this library.  The product path never links or calls it, and it
+// shares no code, header, table or helper with the CUDA library.
+//
+// It is a plain, single-threaded restatement of what the method computes,
+// written top-down per node from the definitions, with no blocking, fusion
+// or bottom-up merging:
+//
+//  * Root cube (Section 3 with the reading that the paper's float coordinates
+//    become int32): the bounding box minimum is the cube's min corner and
+//    its edge S is the smallest power of two strictly greater than the
+//    largest per-axis extent.  N = 0 gives an empty root leaf at the origin.
+//  * Split into leaves (Section 3.1): a node holding more than T points is
+//    subdivided into its non-empty octants; a node with at most T points is
+//    a leaf.  The fixed 8-level grid plus one 4-level extension of Section
+//    3.1.5 becomes "recurse until it fits", capped by max_depth and by unit
+//    cubes (such capped leaves may exceed T and are flagged overfull).
+//    Merging 2x2x2 groups whose sum stays below T (Section 3.1.2) yields the
+//    same tree apart from the T boundary, which follows "at most T points".
+//  * Octant index k = (bx << 2) | (by << 1) | bz, b = the half a point falls
+//    into along each axis; children are listed in ascending k.
+//  * Node order: breadth first by level, within a level by the parent's
+//    order and then ascending octant (ascending path key).
+//  * Leaf point layout (Section 3.1.3 allocates each leaf's points; the
+//    layout is free there): leaves are laid out depth first in octant
+//    order, so every subtree owns one contiguous point range.
+//  * Voxel sampling (Section 3.2): every inner node gets the occupied cells
+//    of a 128^3 grid over its cube.  Cell-wise average (Section 3.2.3) with
+//    exact u64 sums over all original points of the cube and a rounded-half-
+//    up integer mean, alpha 255; sample pick (replacing the random pick of
+//    Section 3.2.2, Listing 1) keeps the point of minimal splitmix64(index).
+//
+// Function-level citations are beside each function.
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <utility>
+#include <vector>
+
+namespace {
+
+struct OPoint {
+  int32_t x, y, z;
+  uint32_t rgba;
+};
+
+struct ONode {
+  int32_t min[3] = {0, 0, 0};
+  uint32_t level = 0;
+  uint32_t log2_size = 0;
+  uint32_t child_mask = 0;
+  uint32_t flags = 0;  // bit0 leaf, bit1 overfull
+  uint32_t parent = UINT32_MAX;
+  uint32_t first_child = UINT32_MAX;
+  uint64_t point_offset = 0;
+  uint64_t point_count = 0;
+  uint64_t voxel_offset = 0;
+  uint32_t voxel_count = 0;
+};
+
+struct OVoxel {
+  uint32_t cell, rgba, count, pick_index;
+};
+
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint32_t kLeaf = 1u;
+constexpr uint32_t kOverfull = 2u;
+
+// splitmix64: the first output of a splitmix64 generator whose state is x
+// (Steele, Lea & Flood, "Fast splittable pseudorandom number generators",
+// OOPSLA 2014): advance the state by the golden-ratio increment, then two
+// xor-shift-multiply rounds and a final xor-shift, all modulo 2^64.
+uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Offset of point p from the cube min c along one axis, as a non-negative
+// 64-bit integer (the cube contains p, so 0 <= d < 2^log2_size <= 2^32).
+inline int64_t rel(int32_t p, int32_t c) { return (int64_t)p - (int64_t)c; }
+
+// 128^3 grid coordinate of an offset d inside a cube of edge 2^L
+// (Section 3.2: samples are projected onto a 128^3 grid per node).
+inline uint32_t grid_coord(int64_t d, uint32_t L) {
+  if (L >= 7) return (uint32_t)(d >> (L - 7));
+  return (uint32_t)(d << (7 - L));
+}
+
+struct Builder {
+  const OPoint* pts;
+  uint64_t n;
+  uint32_t T, mode, max_depth;
+  std::vector<ONode> nodes;
+  std::vector<std::vector<uint32_t>> leaf_lists;  // per node id; only leaves
+  std::vector<OVoxel> voxels;
+  std::vector<OPoint> leaf_points;
+  std::vector<uint32_t> leaf_index;
+
+  // Section 3.2 + 3.2.3 / replacement of 3.2.2: the voxels of one inner node
+  // computed directly from every original point inside its cube.
+  void voxelize(ONode& nd, const std::vector<uint32_t>& idx) {
+    std::vector<std::pair<uint32_t, uint32_t>> keyed;  // (cell, point index)
+    keyed.reserve(idx.size());
+    for (uint32_t i : idx) {
+      const OPoint& p = pts[i];
+      uint32_t qx = grid_coord(rel(p.x, nd.min[0]), nd.log2_size);
+      uint32_t qy = grid_coord(rel(p.y, nd.min[1]), nd.log2_size);
+      uint32_t qz = grid_coord(rel(p.z, nd.min[2]), nd.log2_size);
+      keyed.emplace_back(qx | (qy << 7) | (qz << 14), i);
+    }
+    std::sort(keyed.begin(), keyed.end());
+    nd.voxel_offset = voxels.size();
+    size_t a = 0;
+    while (a < keyed.size()) {
+      size_t b = a;
+      while (b < keyed.size() && keyed[b].first == keyed[a].first) ++b;
+      OVoxel v;
+      v.cell = keyed[a].first;
+      v.count = (uint32_t)(b - a);
+      if (mode == 0) {
+        // Cell-wise average (Section 3.2.3): sum each channel over all
+        // samples of the cell, then the arithmetic mean, rounded half up.
+        uint64_t sr = 0, sg = 0, sb = 0;
+        for (size_t j = a; j < b; ++j) {
+          uint32_t c = pts[keyed[j].second].rgba;
+          sr += c & 0xFFu;
+          sg += (c >> 8) & 0xFFu;
+          sb += (c >> 16) & 0xFFu;
+        }
+        uint64_t cnt = b - a;
+        uint32_t r = (uint32_t)((sr + cnt / 2) / cnt);
+        uint32_t g = (uint32_t)((sg + cnt / 2) / cnt);
+        uint32_t bl = (uint32_t)((sb + cnt / 2) / cnt);
+        v.rgba = r | (g << 8) | (bl << 16) | (255u << 24);
+        v.pick_index = kNone;
+      } else {
+        // Sample pick: the one point of the cell whose splitmix64(index) is
+        // smallest (splitmix64 is a bijection, so the minimum is unique).
+        uint32_t best = keyed[a].second;
+        uint64_t best_h = splitmix64(best);
+        for (size_t j = a + 1; j < b; ++j) {
+          uint64_t h = splitmix64(keyed[j].second);
+          if (h < best_h) {
+            best_h = h;
+            best = keyed[j].second;
+          }
+        }
+        v.rgba = pts[best].rgba;
+        v.pick_index = best;
+      }
+      voxels.push_back(v);
+      a = b;
+    }
+    nd.voxel_count = (uint32_t)(voxels.size() - nd.voxel_offset);
+  }
+
+  // Depth-first leaf layout: each node's point_offset is where its subtree
+  // starts; a leaf copies its points there in input order.
+  uint64_t layout(uint32_t id, uint64_t offset) {
+    ONode& nd = nodes[id];
+    nd.point_offset = offset;
+    if (nd.flags & kLeaf) {
+      const std::vector<uint32_t>& l = leaf_lists[id];
+      for (size_t j = 0; j < l.size(); ++j) {
+        leaf_points[offset + j] = pts[l[j]];
+        leaf_index[offset + j] = l[j];
+      }
+      return offset + l.size();
+    }
+    uint32_t c = nd.first_child;
+    for (uint32_t k = 0; k < 8; ++k)
+      if (nd.child_mask & (1u << k)) offset = layout(c++, offset);
+    return offset;
+  }
+
+  void run() {
+    // Root cube.
+    ONode root;
+    if (n > 0) {
+      int32_t lo[3] = {pts[0].x, pts[0].y, pts[0].z};
+      int32_t hi[3] = {pts[0].x, pts[0].y, pts[0].z};
+      for (uint64_t i = 1; i < n; ++i) {
+        const int32_t c[3] = {pts[i].x, pts[i].y, pts[i].z};
+        for (int a = 0; a < 3; ++a) {
+          lo[a] = std::min(lo[a], c[a]);
+          hi[a] = std::max(hi[a], c[a]);
+        }
+      }
+      int64_t extent = 0;
+      for (int a = 0; a < 3; ++a) extent = std::max(extent, (int64_t)hi[a] - (int64_t)lo[a]);
+      uint32_t L = 0;
+      while ((int64_t(1) << L) <= extent) ++L;  // smallest 2^L > extent
+      for (int a = 0; a < 3; ++a) root.min[a] = lo[a];
+      root.log2_size = L;
+    }
+    nodes.push_back(root);
+    leaf_lists.emplace_back();
+
+    // Breadth-first split, one level at a time (Section 3.1).
+    std::vector<std::pair<uint32_t, std::vector<uint32_t>>> cur, next;
+    {
+      std::vector<uint32_t> all(n);
+      for (uint64_t i = 0; i < n; ++i) all[i] = (uint32_t)i;
+      cur.emplace_back(0u, std::move(all));
+    }
+    while (!cur.empty()) {
+      next.clear();
+      for (auto& item : cur) {
+        uint32_t id = item.first;
+        std::vector<uint32_t>& idx = item.second;
+        nodes[id].point_count = idx.size();
+        const bool split = idx.size() > T && nodes[id].level < max_depth && nodes[id].log2_size > 0;
+        if (!split) {
+          nodes[id].flags = kLeaf | (idx.size() > T ? kOverfull : 0u);
+          leaf_lists[id] = std::move(idx);
+          continue;
+        }
+        // Inner node: partition into octants.
+        const ONode parent = nodes[id];
+        const uint32_t half = parent.log2_size - 1;
+        std::vector<uint32_t> part[8];
+        for (uint32_t i : idx) {
+          const OPoint& p = pts[i];
+          uint32_t bx = (uint32_t)((rel(p.x, parent.min[0]) >> half) & 1);
+          uint32_t by = (uint32_t)((rel(p.y, parent.min[1]) >> half) & 1);
+          uint32_t bz = (uint32_t)((rel(p.z, parent.min[2]) >> half) & 1);
+          part[(bx << 2) | (by << 1) | bz].push_back(i);
+        }
+        nodes[id].first_child = (uint32_t)nodes.size();
+        for (uint32_t k = 0; k < 8; ++k) {
+          if (part[k].empty()) continue;
+          nodes[id].child_mask |= 1u << k;
+          ONode ch;
+          const int64_t step = int64_t(1) << half;
+          ch.min[0] = (int32_t)(parent.min[0] + ((k >> 2) & 1) * step);
+          ch.min[1] = (int32_t)(parent.min[1] + ((k >> 1) & 1) * step);
+          ch.min[2] = (int32_t)(parent.min[2] + (k & 1) * step);
+          ch.level = parent.level + 1;
+          ch.log2_size = half;
+          ch.parent = id;
+          nodes.push_back(ch);
+          leaf_lists.emplace_back();
+          next.emplace_back((uint32_t)(nodes.size() - 1), std::move(part[k]));
+        }
+        voxelize(nodes[id], idx);
+      }
+      std::swap(cur, next);
+    }
+    leaf_points.resize(n);
+    leaf_index.resize(n);
+    layout(0, 0);
+  }
+};
+
+}  // namespace
+
+struct oracle_result {
+  Builder b;
+};
+
+extern "C" {
+
+// Returns 0 on success, 1 on invalid arguments, 2 on allocation failure.
+int oracle_build(const void* points, uint64_t n, uint32_t leaf_threshold, uint32_t mode,
+                 uint32_t max_depth, oracle_result** out) {
+  if (!out || (n > 0 && !points) || leaf_threshold == 0 || mode > 1 || max_depth > 32 ||
+      n > 0xFFFFFFFFull)
+    return 1;
+  oracle_result* r = new (std::nothrow) oracle_result();
+  if (!r) return 2;
+  r->b.pts = static_cast<const OPoint*>(points);
+  r->b.n = n;
+  r->b.T = leaf_threshold;
+  r->b.mode = mode;
+  r->b.max_depth = max_depth;
+  try {
+    r->b.run();
+  } catch (const std::bad_alloc&) {
+    delete r;
+    return 2;
+  }
+  *out = r;
+  return 0;
+}
+
+uint64_t oracle_n_nodes(const oracle_result* r) { return r->b.nodes.size(); }
+uint64_t oracle_n_voxels(const oracle_result* r) { return r->b.voxels.size(); }
+
+// Node fields as separate arrays, each sized oracle_n_nodes().
+void oracle_get_nodes(const oracle_result* r, int32_t* min3, uint8_t* level, uint8_t* log2_size,
+                      uint8_t* child_mask, uint8_t* flags, uint32_t* parent, uint32_t* first_child,
+                      uint64_t* point_offset, uint64_t* point_count, uint64_t* voxel_offset,
+                      uint32_t* voxel_count) {
+  const std::vector<ONode>& v = r->b.nodes;
+  for (size_t i = 0; i < v.size(); ++i) {
+    for (int a = 0; a < 3; ++a) min3[3 * i + a] = v[i].min[a];
+    level[i] = (uint8_t)v[i].level;
+    log2_size[i] = (uint8_t)v[i].log2_size;
+    child_mask[i] = (uint8_t)v[i].child_mask;
+    flags[i] = (uint8_t)v[i].flags;
+    parent[i] = v[i].parent;
+    first_child[i] = v[i].first_child;
+    point_offset[i] = v[i].point_offset;
+    point_count[i] = v[i].point_count;
+    voxel_offset[i] = v[i].voxel_offset;
+    voxel_count[i] = v[i].voxel_count;
+  }
+}
+
+// Voxels as rows of (cell, rgba, count, pick_index).
+void oracle_get_voxels(const oracle_result* r, uint32_t* out4) {
+  const std::vector<OVoxel>& v = r->b.voxels;
+  for (size_t i = 0; i < v.size(); ++i) {
+    out4[4 * i + 0] = v[i].cell;
+    out4[4 * i + 1] = v[i].rgba;
+    out4[4 * i + 2] = v[i].count;
+    out4[4 * i + 3] = v[i].pick_index;
+  }
+}
+
+// Leaf points in layout order (rows x, y, z, rgba) and their input indices.
+void oracle_get_points(const oracle_result* r, int32_t* out4, uint32_t* index) {
+  const Builder& b = r->b;
+  for (uint64_t i = 0; i < b.n; ++i) {
+    out4[4 * i + 0] = b.leaf_points[i].x;
+    out4[4 * i + 1] = b.leaf_points[i].y;
+    out4[4 * i + 2] = b.leaf_points[i].z;
+    out4[4 * i + 3] = (int32_t)b.leaf_points[i].rgba;
+    index[i] = b.leaf_index[i];
+  }
+}
+
+void oracle_free(oracle_result* r) { delete r; }
+
+uint64_t oracle_splitmix64(uint64_t x) { return splitmix64(x); }
+
+}  // extern "C"

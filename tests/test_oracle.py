@@ -1,0 +1,355 @@
+"""CPU pins of the oracle: values and structures fixed by the paper's
+definitions and by mathematics, not by the oracle itself.
+
+* splitmix64: the published first output for seed 0 (Steele, Lea & Flood,
+  OOPSLA 2014; the value every reference implementation prints).
+* Hand-derived closed forms: root cube sizing, octant bit order, node order,
+  rounding of the cell mean (Section 3.2.3), the unique minimal-hash pick,
+  duplicate-point chains capped by unit cubes and max_depth (Section 3.1.5
+  reading), complete lattices and a line with closed-form counts.
+* An independent brute-force checker (tests/bruteforce.py) on random tiny
+  clouds with small T (deep trees), in both modes.
+* Cross-mode identities: identical cells and counts in both modes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from bruteforce import check, splitmix64_py
+from paper_2302_14801_gb300 import synth
+
+NONE = 0xFFFFFFFF
+
+
+def P(rows):
+    """Rows of (x, y, z, r, g, b) -> (N, 4) int32 points with alpha 255."""
+    a = np.asarray(rows, dtype=np.int64).reshape(-1, 6)
+    out = np.empty((len(a), 4), np.int32)
+    out[:, :3] = a[:, :3]
+    out[:, 3] = synth.pack_rgba(a[:, 3], a[:, 4], a[:, 5])
+    return out
+
+
+def test_splitmix64_published_seed0():
+    # First output of splitmix64 seeded with 0 (the standard test vector).
+    assert oracle.splitmix64(0) == 0xE220A8397B1DCDAF
+
+
+def test_splitmix64_matches_generator_stream():
+    # splitmix64(x) is the first output of a generator in state x, so the
+    # second output of a generator seeded with 0 is splitmix64(golden).
+    # The published second output for seed 0 is 0x6E789E6AA1B965F4.
+    assert oracle.splitmix64(0x9E3779B97F4A7C15) == 0x6E789E6AA1B965F4
+
+
+def test_splitmix64_is_a_bijection_on_samples():
+    # Invert with modular inverses derived here (Newton iteration), which is
+    # independent of how the forward map is coded.
+    def inv_mul(a):
+        x = a
+        for _ in range(6):
+            x = (x * (2 - a * x)) & ((1 << 64) - 1)
+        return x
+
+    def unxorshift(y, s):
+        x = y
+        for _ in range(64 // s + 1):
+            x = y ^ (x >> s)
+        return x
+
+    M = (1 << 64) - 1
+    for x in [0, 1, 2, 12345, 2**32 - 1, 2**63 + 7]:
+        h = oracle.splitmix64(x)
+        z = unxorshift(h, 31)
+        z = (z * inv_mul(0x94D049BB133111EB)) & M
+        z = unxorshift(z, 27)
+        z = (z * inv_mul(0xBF58476D1CE4E5B9)) & M
+        z = unxorshift(z, 30)
+        assert (z - 0x9E3779B97F4A7C15) & M == x
+
+
+def test_empty_input():
+    r = oracle.build(np.zeros((0, 4), np.int32), 10, 0)
+    assert len(r["level"]) == 1
+    assert list(r["min"][0]) == [0, 0, 0] and r["log2_size"][0] == 0
+    assert r["flags"][0] == 1 and r["point_count"][0] == 0 and len(r["voxels"]) == 0
+
+
+@pytest.mark.parametrize("ext,log2", [(0, 0), (1, 1), (3, 2), (4, 3), (5, 3), (7, 3), (8, 4),
+                                      (2**31 - 1, 31), (2**31, 32), (2**32 - 1, 32)])
+def test_root_cube_edge_is_smallest_power_of_two_above_extent(ext, log2):
+    lo = -(2**31)
+    hi = lo + ext
+    pts = P([(lo, 5, 5, 1, 2, 3), (hi, 5, 5, 4, 5, 6)])
+    r = oracle.build(pts, 10, 0)
+    assert r["log2_size"][0] == log2
+    assert list(r["min"][0]) == [lo, 5, 5]
+
+
+def test_octant_bit_order_and_node_order():
+    # Cube [0,8)^3 (extent 7).  One point in each of four octants; T = 1.
+    # Octant k = 4*bx + 2*by + bz, so x-high is k=4, y-high k=2, z-high k=1.
+    pts = P([(0, 0, 7, 10, 0, 0), (7, 0, 0, 20, 0, 0), (0, 0, 0, 30, 0, 0), (0, 7, 0, 40, 0, 0)])
+    r = oracle.build(pts, 1, 0)
+    assert r["log2_size"][0] == 3
+    assert r["child_mask"][0] == (1 << 0) | (1 << 1) | (1 << 2) | (1 << 4)
+    assert r["first_child"][0] == 1
+    assert [list(m) for m in r["min"][1:]] == [[0, 0, 0], [0, 0, 4], [0, 4, 0], [4, 0, 0]]
+    assert list(r["level"]) == [0, 1, 1, 1, 1]
+    assert list(r["parent"]) == [NONE, 0, 0, 0, 0]
+    # depth-first leaf layout follows the same octant order
+    assert [int(v) for v in r["points"][:, 3] & 255] == [30, 10, 40, 20]
+    assert list(r["point_offset"]) == [0, 0, 1, 2, 3]
+    # root voxels: cube edge 8 < 128, so q = d * 16 per axis
+    cells = sorted(int(c) for c in r["voxels"][:, 0])
+    assert cells == sorted([0, 112 * 16384, 112, 112 * 128])
+
+
+@pytest.mark.parametrize("reds,mean", [((1, 2), 2), ((1, 2, 2), 2), ((0, 1, 1, 1), 1),
+                                       ((1, 1, 1, 2), 1), ((254, 255), 255), ((0, 1), 1),
+                                       ((0, 0, 1), 0), ((3, 4, 4, 4), 4), ((100,), 100)])
+def test_cell_mean_rounds_half_up(reds, mean):
+    # All sample points share root cell 0 (cube edge 2^20, cells 2^13 wide);
+    # a far point forces a split (T = len-1 ... ) so the root is inner.
+    rows = [(i, 0, 0, r, 7, 200) for i, r in enumerate(reds)]
+    rows.append((2**20 - 1, 0, 0, 0, 0, 0))
+    pts = P(rows)
+    r = oracle.build(pts, 1, 0)
+    v = r["voxels"][r["voxel_offset"][0]:r["voxel_offset"][0] + r["voxel_count"][0]]
+    v0 = v[v[:, 0] == 0][0]
+    assert v0[2] == len(reds)
+    assert v0[1] == mean | (7 << 8) | (200 << 16) | (255 << 24)
+    assert v0[3] == NONE
+
+
+def test_pick_is_unique_minimal_splitmix64():
+    # Indices 0, 1, 2 in one cell.  Published hashes: h(1) = 0x910a2dec89025cc1
+    # < h(2) = 0x975835de1c9756ce < h(0) = 0xe220a8397b1dcdaf, so index 1 wins.
+    pts = P([(0, 0, 0, 11, 0, 0), (1, 0, 0, 22, 0, 0), (2, 0, 0, 33, 0, 0), (2**20 - 1, 0, 0, 44, 0, 0)])
+    r = oracle.build(pts, 1, 1)
+    v = r["voxels"][r["voxel_offset"][0]:r["voxel_offset"][0] + r["voxel_count"][0]]
+    v0 = v[v[:, 0] == 0][0]
+    assert v0[2] == 3 and v0[3] == 1 and (int(v0[1]) & 255) == 22
+
+
+def test_single_leaf_when_n_at_most_T():
+    pts = synth.sphere(500, seed=9)
+    r = oracle.build(pts, 500, 0)
+    assert len(r["level"]) == 1 and r["flags"][0] == 1 and len(r["voxels"]) == 0
+    r = oracle.build(pts, 499, 0)
+    assert r["flags"][0] == 0 and len(r["level"]) > 1
+
+
+def test_all_identical_points_unit_cube_overfull():
+    pts = P([(5, 5, 5, 1, 2, 3)] * 10)
+    r = oracle.build(pts, 3, 0)
+    assert len(r["level"]) == 1 and r["log2_size"][0] == 0 and r["flags"][0] == 3
+
+
+@pytest.mark.parametrize("max_depth,expect_nodes,last_level", [(21, 12, 10), (5, 7, 5), (0, 1, 0)])
+def test_duplicate_chain_capped(max_depth, expect_nodes, last_level):
+    # 9 copies of the origin and one point at x = 1023: edge 1024 (log2 10).
+    # The 9 copies descend a chain of single children until the unit cube at
+    # level 10, or until max_depth; that last node is an overfull leaf.
+    pts = P([(0, 0, 0, 1, 1, 1)] * 9 + [(1023, 0, 0, 2, 2, 2)])
+    r = oracle.build(pts, 3, 0, max_depth)
+    assert len(r["level"]) == expect_nodes
+    deepest = int(np.argmax(r["level"]))
+    assert r["level"][deepest] == last_level and r["point_count"][deepest] == (9 if max_depth else 10)
+    assert r["flags"][deepest] == 3
+
+
+@pytest.mark.parametrize("T,n_nodes,n_inner,n_vox", [(8, 73, 9, 512 + 8 * 64), (7, 585, 73, 512 + 512 + 64 * 8),
+                                                     (64, 9, 1, 512), (512, 1, 0, 0)])
+def test_complete_lattice_closed_form(T, n_nodes, n_inner, n_vox):
+    g = np.stack(np.meshgrid(np.arange(8), np.arange(8), np.arange(8), indexing="ij"), -1).reshape(-1, 3)
+    rows = np.concatenate([g, np.full((512, 3), 9)], axis=1)
+    r = oracle.build(P(rows), T, 0)
+    assert len(r["level"]) == n_nodes
+    assert int(((r["flags"] & 1) == 0).sum()) == n_inner
+    assert len(r["voxels"]) == n_vox
+    assert np.all(r["voxels"][:, 2] == 1)  # edge <= 8 < 128: every point its own cell
+    assert np.all(r["voxels"][:, 1] == (9 | (9 << 8) | (9 << 16) | (255 << 24)))
+
+
+def test_line_closed_form_counts_and_means():
+    # 1024 points (i, 0, 0), R = i mod 256.  Edge 1024 (log2 10), T = 100:
+    # levels 0..3 inner (1+2+4+8 = 15 nodes), 16 leaves of 64 at level 4.
+    # A level-l inner node spans 1024/2^l points in 128 cells of 8/2^l.
+    n = 1024
+    rows = [(i, 0, 0, i % 256, 0, 0) for i in range(n)]
+    r = oracle.build(P(rows), 100, 0)
+    assert len(r["level"]) == 31
+    assert list(np.bincount(r["level"])) == [1, 2, 4, 8, 16]
+    assert int((r["flags"] & 1).sum()) == 16
+    assert len(r["voxels"]) == 15 * 128
+    root = r["voxels"][r["voxel_offset"][0]:r["voxel_offset"][0] + 128]
+    assert np.all(root[:, 2] == 8)
+    for v in root:
+        j = int(v[0])  # cell j holds x = 8j..8j+7, red = (8j mod 256) + 0..7
+        assert int(v[1]) & 255 == (8 * j) % 256 + 4  # mean x.5 rounds up
+    for lvl, cnt in [(1, 4), (2, 2), (3, 1)]:
+        for i in np.nonzero(r["level"] == lvl)[0]:
+            v = r["voxels"][r["voxel_offset"][i]:r["voxel_offset"][i] + r["voxel_count"][i]]
+            assert len(v) == 128 and np.all(v[:, 2] == cnt)
+
+
+def test_constant_colour_mean_exact():
+    pts = synth.sphere(20000, seed=4)
+    pts[:, 3] = synth.pack_rgba(np.full(20000, 17), np.full(20000, 99), np.full(20000, 250))
+    r = oracle.build(pts, 1000, 0)
+    assert len(r["voxels"]) > 0
+    assert np.all(r["voxels"][:, 1] == (17 | (99 << 8) | (250 << 16) | (255 << 24)))
+
+
+def _random_cloud(rng, n, spread_log2):
+    kind = rng.integers(0, 3)
+    if kind == 0:
+        xyz = rng.integers(-(2**spread_log2), 2**spread_log2, size=(n, 3))
+    elif kind == 1:  # clustered, with duplicates
+        c = rng.integers(0, 2**spread_log2, size=(4, 3))
+        xyz = c[rng.integers(0, 4, size=n)] + rng.integers(0, 3, size=(n, 3))
+    else:  # points on a plane
+        xyz = rng.integers(0, 2**spread_log2, size=(n, 3))
+        xyz[:, 2] = 77
+    out = np.empty((n, 4), np.int32)
+    out[:, :3] = xyz
+    out[:, 3] = rng.integers(-(2**31), 2**31, size=n)
+    return out
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_bruteforce_random_tiny(seed):
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(1, 400))
+    T = int(rng.integers(1, 17))
+    max_depth = int(rng.choice([21, 3, 1, 6]))
+    pts = _random_cloud(rng, n, int(rng.integers(1, 24)))
+    for mode in (0, 1):
+        r = oracle.build(pts, T, mode, max_depth)
+        check(pts, r, T, mode, max_depth)
+
+
+def test_bruteforce_sphere_small():
+    pts = synth.sphere(1500, seed=5)
+    for mode in (0, 1):
+        r = oracle.build(pts, 16, mode)
+        check(pts, r, 16, mode, 21)
+
+
+def test_cross_mode_identical_cells_and_counts():
+    pts = synth.aerial(30000, seed=6, n_buildings=20)
+    a = oracle.build(pts, 2000, 0)
+    b = oracle.build(pts, 2000, 1)
+    for k in ("min", "level", "log2_size", "child_mask", "flags", "parent", "first_child",
+              "point_offset", "point_count", "voxel_count"):
+        assert np.array_equal(a[k], b[k]), k
+    assert np.array_equal(a["voxels"][:, [0, 2]], b["voxels"][:, [0, 2]])
+
+
+def test_invariants_medium():
+    pts = synth.indoor(200000, seed=7, n_prims=64)
+    r = oracle.build(pts, 5000, 1)
+    leaf = (r["flags"] & 1) == 1
+    assert int(r["point_count"][leaf].sum()) == len(pts)
+    assert np.all(r["point_count"][leaf & ((r["flags"] & 2) == 0)] <= 5000)
+    assert np.all(r["point_count"][~leaf] > 5000)
+    # parent subtree count = sum of children
+    for i in np.nonzero(~leaf)[0]:
+        k = bin(int(r["child_mask"][i])).count("1")
+        f = int(r["first_child"][i])
+        assert int(r["point_count"][f:f + k].sum()) == int(r["point_count"][i])
+        v = r["voxels"][r["voxel_offset"][i]:r["voxel_offset"][i] + r["voxel_count"][i]]
+        assert int(v[:, 2].sum()) == int(r["point_count"][i])
+    # each picked point lies in its cell with the minimal hash among its cell
+    assert sorted(r["index"].tolist()) == list(range(len(pts)))
+
+
+def test_parent_voxel_counts_are_sums_of_nested_child_cells():
+    # A parent cell covers a 2x2x2 block of cells of the child in its octant.
+    pts = synth.sphere(60000, seed=8)
+    r = oracle.build(pts, 3000, 0)
+    vox = r["voxels"]
+    for i in np.nonzero((r["flags"] & 1) == 0)[0]:
+        pv = vox[r["voxel_offset"][i]:r["voxel_offset"][i] + r["voxel_count"][i]]
+        pc = {int(c): int(n) for c, n in zip(pv[:, 0], pv[:, 2])}
+        acc = {}
+        f = int(r["first_child"][i])
+        k_list = [k for k in range(8) if r["child_mask"][i] >> k & 1]
+        for rank, k in enumerate(k_list):
+            j = f + rank
+            ox, oy, oz = (k >> 2) & 1, (k >> 1) & 1, k & 1
+            if r["flags"][j] & 1:
+                # leaf child: project its points directly
+                lp = r["points"][r["point_offset"][j]:r["point_offset"][j] + r["point_count"][j], :3]
+                L = int(r["log2_size"][i])
+                d = lp.astype(np.int64) - r["min"][i].astype(np.int64)
+                q = d >> (L - 7) if L >= 7 else d << (7 - L)
+                for c in (q[:, 0] | (q[:, 1] << 7) | (q[:, 2] << 14)).tolist():
+                    acc[c] = acc.get(c, 0) + 1
+                continue
+            cv = vox[r["voxel_offset"][j]:r["voxel_offset"][j] + r["voxel_count"][j]]
+            for c, n in zip(cv[:, 0].tolist(), cv[:, 2].tolist()):
+                x, y, z = c & 127, (c >> 7) & 127, c >> 14
+                pcell = (ox * 64 + (x >> 1)) | ((oy * 64 + (y >> 1)) << 7) | ((oz * 64 + (z >> 1)) << 14)
+                acc[pcell] = acc.get(pcell, 0) + n
+        assert acc == pc
+
+
+def test_rejects_bad_arguments():
+    pts = synth.sphere(10, seed=1)
+    with pytest.raises(ValueError):
+        oracle.build(pts, 0, 0)
+    with pytest.raises(ValueError):
+        oracle.build(pts, 10, 2)
+    with pytest.raises(ValueError):
+        oracle.build(pts, 10, 0, 33)
+
+
+def test_bruteforce_checker_catches_planted_mistakes():
+    """The checker must fail on plausible oracle mistakes, planted here on
+    the CPU in a copy of a correct result."""
+    pts = synth.sphere(800, seed=11)
+    good = oracle.build(pts, 12, 0)
+    check(pts, good, 12, 0, 21)
+
+    def mutated(fn):
+        bad = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in good.items()}
+        fn(bad)
+        return bad
+
+    plants = [
+        lambda b: b["voxels"].__setitem__((0, 1), b["voxels"][0, 1] ^ 1),        # mean off by one
+        lambda b: b["voxels"].__setitem__((0, 2), b["voxels"][0, 2] + 1),        # count
+        lambda b: b["min"].__setitem__((1, 0), b["min"][1, 0] + 1),              # child min
+        lambda b: b["point_offset"].__setitem__(-1, b["point_offset"][-1] + 1),  # layout
+        lambda b: b["points"].__setitem__(slice(None), b["points"][::-1]),       # leaf contents
+        lambda b: b["voxels"].__setitem__((0, 0), b["voxels"][0, 0] ^ 1),        # transposed cell bit
+    ]
+    for fn in plants:
+        with pytest.raises(AssertionError):
+            check(pts, mutated(fn), 12, 0, 21)
+
+
+def test_bruteforce_pick_catches_wrong_argmin():
+    pts = synth.sphere(600, seed=12)
+    good = oracle.build(pts, 10, 1)
+    check(pts, good, 10, 1, 21)
+    bad = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in good.items()}
+    # find a voxel with >= 2 members and replace the pick by another member
+    v = bad["voxels"]
+    i = int(np.nonzero(v[:, 2] >= 2)[0][0])
+    node = int(np.nonzero((bad["voxel_offset"] <= i) & (i < bad["voxel_offset"] + bad["voxel_count"]))[0][0])
+    L = int(bad["log2_size"][node])
+    d = pts[:, :3].astype(np.int64) - bad["min"][node].astype(np.int64)
+    s = 1 << L
+    inside = np.all((d >= 0) & (d < s), axis=1)
+    q = (d * 128) // s
+    cell = q[:, 0] + 128 * q[:, 1] + 16384 * q[:, 2]
+    members = np.nonzero(inside & (cell == v[i, 0]))[0]
+    other = [m for m in members.tolist() if m != v[i, 3]][0]
+    v[i, 3] = other
+    v[i, 1] = int(pts[other, 3]) & 0xFFFFFFFF
+    with pytest.raises(AssertionError):
+        check(pts, bad, 10, 1, 21)
+    assert splitmix64_py(0) == 0xE220A8397B1DCDAF
