@@ -1,0 +1,250 @@
+/*
+ * lod.h — C ABI of the GB300 (sm_103a) LOD builder for point clouds.
+ *
+ * The library builds the hybrid voxel-point octree of "GPU-Accelerated LOD
+ * Generation for Point Clouds" (Schuetz, Kerbl, Klaus, Wimmer 2023):
+ *   - Section 3.1: the input points are split top-down into an octree whose
+ *     leaves hold at most T original points (hierarchical counting sort);
+ *   - Section 3.2: every inner node is then filled bottom-up with the
+ *     occupied cells ("voxels") of a 128^3 grid laid over its cube.
+ * Two sampling modes are provided:
+ *   - LOD_FILTER: the cell-wise average of Section 3.2.3, made exact — each
+ *     voxel carries the integer mean (rounded half up) of the RGB of all
+ *     original points inside its cell, accumulated as unsigned 64-bit sums;
+ *     alpha is 255.
+ *   - LOD_PICK: replaces the random pick of Section 3.2.2 (Listing 1) by an
+ *     order-independent rule — each voxel keeps the original point of
+ *     minimal splitmix64(input index); pick_index is that index.
+ *
+ * Every entry point is extern "C", takes plain pointers and sizes, and
+ * returns an int status (LOD_OK on success).  Pointers documented as
+ * "device" must be CUDA device memory of the current device; "host" means
+ * ordinary (optionally pinned) host memory.  A stream argument is a
+ * cudaStream_t passed as void* (NULL = the legacy default stream).
+ *
+ * Ownership.  Inputs stay owned by the caller and must remain valid and
+ * unmodified until the call that consumes them has completed (for
+ * lod_build: until it returns; for lod_submit: until lod_poll/lod_wait
+ * returns the result).  Every output buffer is owned by an lod_result_t and
+ * released by lod_free().  Nothing is retained after lod_free().
+ *
+ * Thread safety.  lod_build / lod_build_batched / lod_build_from_host may be
+ * called from several host threads on different streams.  A server object
+ * (lod_server_t) is internally synchronised.
+ */
+#ifndef LOD_H_
+#define LOD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+enum {
+  LOD_OK = 0,
+  LOD_NOT_READY = 1,       /* lod_poll: the request has not finished yet      */
+  LOD_ERR_INVALID_ARG = 2, /* bad pointer, size, alignment or parameter       */
+  LOD_ERR_OOM = 3,         /* device allocation failed                        */
+  LOD_ERR_BUDGET = 4,      /* request can never fit the server's HBM budget   */
+  LOD_ERR_CUDA = 5,        /* a CUDA call or kernel launch failed             */
+  LOD_ERR_TIMEOUT = 6,     /* lod_wait: timed out                             */
+  LOD_ERR_INTERNAL = 7     /* internal consistency check failed               */
+};
+
+/* ------------------------------------------------------------------ data */
+
+/* Input point, 16 bytes, array-of-structs.  rgba is RGBA8 with R in the low
+ * byte and A in the high byte.  Arrays of points must be 16-byte aligned
+ * (cudaMalloc and torch allocations are). */
+typedef struct lod_point {
+  int32_t x, y, z;
+  uint32_t rgba;
+} lod_point_t;
+
+enum { LOD_FILTER = 0, LOD_PICK = 1 };
+
+/* Keep the original input index of every leaf point (always kept in
+ * LOD_PICK mode, where the sampling rule needs it). */
+enum { LOD_FLAG_LEAF_INDEX = 1u };
+
+/* Build parameters.
+ *   leaf_threshold  T >= 1: a node with more than T points is split into its
+ *                   non-empty octants (Section 3; the paper uses T = 50k).
+ *   mode            LOD_FILTER or LOD_PICK.
+ *   max_depth       <= 32: nodes at this level are leaves even above T.
+ *                   Unit cubes (edge 1) are leaves too; such leaves may hold
+ *                   more than T points and are flagged LOD_NODE_OVERFULL.
+ *   flags           LOD_FLAG_* bits. */
+typedef struct lod_params {
+  uint32_t leaf_threshold;
+  uint32_t mode;
+  uint32_t max_depth;
+  uint32_t flags;
+} lod_params_t;
+
+enum { LOD_NODE_LEAF = 1u, LOD_NODE_OVERFULL = 2u };
+
+/* One octree node, 56 bytes.
+ *   min, log2_size  the node's cube [min, min + 2^log2_size)^3.  The root's
+ *                   min is the bounding-box minimum and its edge the smallest
+ *                   power of two strictly greater than the largest extent
+ *                   (N = 0: one empty leaf at the origin with edge 1).
+ *   level           0 for the root.
+ *   child_mask      bit k set if octant k has a child; octant
+ *                   k = 4*bx + 2*by + bz, b = upper half along x, y, z.
+ *   flags           LOD_NODE_LEAF / LOD_NODE_OVERFULL.
+ *   parent          node index, 0xFFFFFFFF for the root.
+ *   first_child     index of the child of the lowest set octant; the
+ *                   children follow contiguously in octant order;
+ *                   0xFFFFFFFF for leaves.
+ *   point_offset,   the node's subtree owns the contiguous leaf-point range
+ *   point_count     [point_offset, point_offset + point_count).
+ *   voxel_offset,   inner nodes: their voxels (index into the view's voxel
+ *   voxel_count     array); leaves: 0, 0.
+ * Nodes are ordered breadth first; within a level by parent, then octant. */
+typedef struct lod_node {
+  int32_t min[3];
+  uint8_t level, log2_size, child_mask, flags;
+  uint32_t parent, first_child;
+  uint64_t point_offset, point_count;
+  uint64_t voxel_offset;
+  uint32_t voxel_count, reserved;
+} lod_node_t;
+
+/* One voxel of an inner node, 16 bytes (Section 3.2).
+ *   cell        x | y << 7 | z << 14, the 128^3 grid cell relative to the
+ *               node's cube (cell edge 2^log2_size / 128).
+ *   rgba        LOD_FILTER: rounded-half-up mean RGB, A = 255;
+ *               LOD_PICK: colour of the picked input point.
+ *   count       number of original points inside the cell.
+ *   pick_index  LOD_PICK: input index of the picked point (splitmix64-min);
+ *               LOD_FILTER: 0xFFFFFFFF.
+ * Voxel order within a node is unspecified. */
+typedef struct lod_voxel {
+  uint32_t cell, rgba, count, pick_index;
+} lod_voxel_t;
+
+/* Read-only view of a result.  All pointers are device pointers owned by
+ * the result.
+ *   points      n_points leaf points in layout order: leaves are laid out
+ *               depth first in octant order (every subtree is contiguous);
+ *               order inside a leaf is unspecified.
+ *   point_index original input index of each leaf point, or NULL if not kept.
+ *   voxels      base of the voxel array that nodes[i].voxel_offset indexes;
+ *               n_voxels is the number of voxels of this result.  Results of
+ *               one lod_build_batched call share one voxel array. */
+typedef struct lod_view {
+  const lod_node_t* nodes;
+  uint32_t n_nodes;
+  uint32_t n_levels;
+  const lod_point_t* points;
+  const uint32_t* point_index;
+  uint64_t n_points;
+  const lod_voxel_t* voxels;
+  uint64_t n_voxels;
+  uint32_t mode;
+  uint32_t reserved;
+} lod_view_t;
+
+typedef struct lod_result lod_result_t;
+
+/* ------------------------------------------------------------------- API */
+
+/* Fill *p with the defaults: T = 50000, LOD_FILTER, max_depth 21, flags 0. */
+int lod_params_init(lod_params_t* p);
+
+/* Build the LOD octree of n device points (Sections 3.1 and 3.2).
+ *   d_points  device, 16-byte aligned, n records; read only.  n < 2^32.
+ *   params    host; NULL selects the defaults.
+ *   stream    cudaStream_t as void*; all device work is ordered on it.
+ *   out       host; receives a new result on LOD_OK (untouched otherwise).
+ * Blocks the calling host thread until the build has completed on the
+ * stream.  Errors: LOD_ERR_INVALID_ARG, LOD_ERR_OOM, LOD_ERR_CUDA. */
+int lod_build(const lod_point_t* d_points, uint64_t n, const lod_params_t* params, void* stream,
+              lod_result_t** out);
+
+/* Same, with the points in host memory: they are copied to the device on
+ * the stream first (pinned memory makes the copy asynchronous). */
+int lod_build_from_host(const lod_point_t* h_points, uint64_t n, const lod_params_t* params,
+                        void* stream, lod_result_t** out);
+
+/* Build n_tiles independent octrees in one batched pass: every stage runs
+ * as one launch over the work of all tiles (one device work list).
+ *   d_tiles   host array of n_tiles device pointers (each 16-byte aligned).
+ *   n         host array of n_tiles point counts (each < 2^32).
+ *   out       host array of n_tiles result pointers, filled on LOD_OK.
+ * Each result is freed separately; they share device buffers internally,
+ * which are released when the last of them is freed.  Results are
+ * identical to n_tiles separate lod_build calls. */
+int lod_build_batched(const lod_point_t* const* d_tiles, const uint64_t* n, uint32_t n_tiles,
+                      const lod_params_t* params, void* stream, lod_result_t** out);
+
+/* Fill *view (host) with the device pointers and sizes of result r. */
+int lod_result_view(const lod_result_t* r, lod_view_t* view);
+
+/* Copy a result to host memory (stream-ordered; synchronises before
+ * returning).  Any output pointer may be NULL to skip that part.
+ *   nodes   n_nodes records; voxel_offset is rewritten to index `voxels`.
+ *   points  n_points leaf points;  index  n_points indices (needs a kept
+ *           index, else LOD_ERR_INVALID_ARG);
+ *   voxels  n_voxels records, grouped per node in node order. */
+int lod_result_copy_to_host(const lod_result_t* r, lod_node_t* nodes, lod_point_t* points,
+                            uint32_t* index, lod_voxel_t* voxels, void* stream);
+
+/* Device bytes held by a result (its share of shared buffers included). */
+uint64_t lod_result_device_bytes(const lod_result_t* r);
+
+/* Release a result; NULL is a no-op. */
+void lod_free(lod_result_t* r);
+
+/* Static description of a status code. */
+const char* lod_error_string(int status);
+
+/* -------------------------------------------------------------- serving */
+
+/* A server admits tile-build requests as they arrive and runs them
+ * concurrently on the device (continuous batching): a request is started as
+ * soon as a slot is free and its estimated device footprint fits in what
+ * the HBM budget has left after the resident results of earlier requests;
+ * results stay resident (counted against the budget) until lod_free().
+ *   hbm_budget_bytes  device bytes for in-flight builds + resident results.
+ *   max_inflight      concurrent builds (streams), >= 1.
+ * Results are bit-identical to lod_build of the same request alone. */
+typedef struct lod_server_config {
+  uint64_t hbm_budget_bytes;
+  uint32_t max_inflight;
+  uint32_t reserved;
+} lod_server_config_t;
+
+typedef struct lod_server lod_server_t;
+
+int lod_server_create(const lod_server_config_t* cfg, lod_server_t** out);
+
+/* Enqueue a build of n device points (kept valid by the caller until the
+ * result is returned).  *ticket identifies the request.  Returns
+ * LOD_ERR_BUDGET if the request alone exceeds the budget. */
+int lod_submit(lod_server_t* s, const lod_point_t* d_points, uint64_t n, const lod_params_t* params,
+               uint64_t* ticket);
+
+/* Non-blocking: LOD_OK and *out set when the request has finished (the
+ * ticket is then consumed), LOD_NOT_READY otherwise, or the build's error. */
+int lod_poll(lod_server_t* s, uint64_t ticket, lod_result_t** out);
+
+/* Blocking variant of lod_poll with a timeout in milliseconds. */
+int lod_wait(lod_server_t* s, uint64_t ticket, uint32_t timeout_ms, lod_result_t** out);
+
+/* Device bytes currently counted against the budget. */
+uint64_t lod_server_bytes_in_use(const lod_server_t* s);
+
+/* Finish all queued requests, release the worker threads and the server.
+ * Results already returned stay valid. */
+int lod_server_destroy(lod_server_t* s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LOD_H_ */

@@ -1,0 +1,426 @@
+// C ABI of the LOD builder (declared in include/lod.h): argument checks,
+// result objects, host copies and the serving loop.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "engine.h"
+#include "kernels.h"
+
+static_assert(sizeof(lod_point_t) == 16, "point record is 16 bytes");
+static_assert(sizeof(lod_node_t) == 56, "node record is 56 bytes");
+static_assert(sizeof(lod_voxel_t) == 16, "voxel record is 16 bytes");
+static_assert(sizeof(lod_view_t) == 64, "view is 64 bytes");
+static_assert(sizeof(lod_params_t) == 16, "params are 16 bytes");
+
+namespace {
+
+// Budget accounting shared between a server and the results it returned
+// (results may outlive the server).
+struct Budget {
+  std::mutex mu;
+  std::condition_variable cv;
+  uint64_t limit = 0;
+  uint64_t in_use = 0;
+  void release(uint64_t b) {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      in_use = b > in_use ? 0 : in_use - b;
+    }
+    cv.notify_all();
+  }
+};
+
+int to_status(cudaError_t e) {
+  if (e == cudaSuccess) return LOD_OK;
+  return e == cudaErrorMemoryAllocation ? LOD_ERR_OOM : LOD_ERR_CUDA;
+}
+
+lod_params_t defaults() {
+  lod_params_t p;
+  p.leaf_threshold = 50000;
+  p.mode = LOD_FILTER;
+  p.max_depth = 21;
+  p.flags = 0;
+  return p;
+}
+
+}  // namespace
+
+struct lod_result {
+  std::shared_ptr<lodk::SharedBuffers> sh;
+  lodk::TileResult tr;
+  uint32_t mode = 0;
+  uint64_t bytes = 0;
+  std::shared_ptr<Budget> budget;  // set when a server accounts for this result
+};
+
+static lod_result_t* make_result(const std::shared_ptr<lodk::SharedBuffers>& sh, const lodk::TileResult& tr,
+                                 uint32_t mode, uint64_t share) {
+  lod_result_t* r = new (std::nothrow) lod_result_t();
+  if (!r) return nullptr;
+  r->sh = sh;
+  r->tr = tr;
+  r->mode = mode;
+  r->bytes = share;
+  return r;
+}
+
+extern "C" {
+
+int lod_params_init(lod_params_t* p) {
+  if (!p) return LOD_ERR_INVALID_ARG;
+  *p = defaults();
+  return LOD_OK;
+}
+
+int lod_build(const lod_point_t* d_points, uint64_t n, const lod_params_t* params, void* stream,
+              lod_result_t** out) {
+  if (!out) return LOD_ERR_INVALID_ARG;
+  const lod_params_t p = params ? *params : defaults();
+  lodk::TileInput ti{d_points, n};
+  std::shared_ptr<lodk::SharedBuffers> sh;
+  std::vector<lodk::TileResult> tr;
+  const int rc = lodk::run_build(&ti, 1, p, static_cast<cudaStream_t>(stream), &sh, &tr, nullptr);
+  if (rc != LOD_OK) return rc;
+  lod_result_t* r = make_result(sh, tr[0], p.mode, sh->bytes);
+  if (!r) return LOD_ERR_OOM;
+  *out = r;
+  return LOD_OK;
+}
+
+int lod_build_from_host(const lod_point_t* h_points, uint64_t n, const lod_params_t* params, void* stream,
+                        lod_result_t** out) {
+  if (!out || (n && !h_points) || n > 0xFFFFFFFFull) return LOD_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void* d = nullptr;
+  if (n) {
+    cudaError_t e = cudaMallocAsync(&d, n * sizeof(lod_point_t), st);
+    if (e != cudaSuccess) return to_status(e);
+    e = cudaMemcpyAsync(d, h_points, n * sizeof(lod_point_t), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+      cudaFreeAsync(d, st);
+      return to_status(e);
+    }
+  }
+  const int rc = lod_build(static_cast<const lod_point_t*>(d), n, params, stream, out);
+  if (d) cudaFreeAsync(d, st);
+  return rc;
+}
+
+int lod_build_batched(const lod_point_t* const* d_tiles, const uint64_t* n, uint32_t n_tiles,
+                      const lod_params_t* params, void* stream, lod_result_t** out) {
+  if (!d_tiles || !n || !out || n_tiles == 0) return LOD_ERR_INVALID_ARG;
+  const lod_params_t p = params ? *params : defaults();
+  std::vector<lodk::TileInput> ti(n_tiles);
+  uint64_t total = 0;
+  for (uint32_t t = 0; t < n_tiles; ++t) {
+    ti[t] = {d_tiles[t], n[t]};
+    total += n[t];
+  }
+  std::shared_ptr<lodk::SharedBuffers> sh;
+  std::vector<lodk::TileResult> tr;
+  const int rc = lodk::run_build(ti.data(), n_tiles, p, static_cast<cudaStream_t>(stream), &sh, &tr, nullptr);
+  if (rc != LOD_OK) return rc;
+  std::vector<lod_result_t*> rs(n_tiles, nullptr);
+  for (uint32_t t = 0; t < n_tiles; ++t) {
+    const uint64_t share = total ? (uint64_t)((double)sh->bytes * (double)n[t] / (double)total) : 0;
+    rs[t] = make_result(sh, tr[t], p.mode, share);
+    if (!rs[t]) {
+      for (auto* q : rs) delete q;
+      return LOD_ERR_OOM;
+    }
+  }
+  for (uint32_t t = 0; t < n_tiles; ++t) out[t] = rs[t];
+  return LOD_OK;
+}
+
+int lod_result_view(const lod_result_t* r, lod_view_t* v) {
+  if (!r || !v) return LOD_ERR_INVALID_ARG;
+  std::memset(v, 0, sizeof(*v));
+  v->nodes = static_cast<const lod_node_t*>(r->sh->nodes) + r->tr.node_base;
+  v->n_nodes = r->tr.n_nodes;
+  v->n_levels = r->tr.n_levels;
+  v->points = static_cast<const lod_point_t*>(r->sh->points) + r->tr.pt_base;
+  v->point_index = r->sh->index ? static_cast<const uint32_t*>(r->sh->index) + r->tr.pt_base : nullptr;
+  v->n_points = r->tr.n_points;
+  v->voxels = static_cast<const lod_voxel_t*>(r->sh->voxels);
+  v->n_voxels = r->tr.n_voxels;
+  v->mode = r->mode;
+  return LOD_OK;
+}
+
+int lod_result_copy_to_host(const lod_result_t* r, lod_node_t* nodes, lod_point_t* points, uint32_t* index,
+                            lod_voxel_t* voxels, void* stream) {
+  if (!r) return LOD_ERR_INVALID_ARG;
+  if (index && !r->sh->index) return LOD_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  lod_view_t v;
+  lod_result_view(r, &v);
+  cudaError_t e = cudaSuccess;
+  if (points && v.n_points)
+    e = cudaMemcpyAsync(points, v.points, v.n_points * sizeof(lod_point_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && index && v.n_points)
+    e = cudaMemcpyAsync(index, v.point_index, v.n_points * 4, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return to_status(e);
+  if (!nodes && !voxels) return to_status(cudaStreamSynchronize(st));
+  std::vector<lod_node_t> hn(v.n_nodes);
+  e = cudaMemcpyAsync(hn.data(), v.nodes, v.n_nodes * sizeof(lod_node_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return to_status(e);
+  std::vector<uint64_t> off(v.n_nodes);
+  uint64_t acc = 0;
+  for (uint32_t i = 0; i < v.n_nodes; ++i) {
+    off[i] = acc;
+    acc += hn[i].voxel_count;
+  }
+  if (voxels && acc) {
+    void *d_off = nullptr, *d_tmp = nullptr;
+    e = cudaMallocAsync(&d_off, v.n_nodes * 8, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_tmp, acc * 16, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, off.data(), v.n_nodes * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = lodk::launch_gather_voxels(v.nodes, v.n_nodes, static_cast<const uint64_t*>(d_off),
+                                     reinterpret_cast<const int4*>(v.voxels), static_cast<int4*>(d_tmp), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(voxels, d_tmp, acc * 16, cudaMemcpyDeviceToHost, st);
+    if (d_off) cudaFreeAsync(d_off, st);
+    if (d_tmp) cudaFreeAsync(d_tmp, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return to_status(e);
+  }
+  if (nodes) {
+    for (uint32_t i = 0; i < v.n_nodes; ++i) hn[i].voxel_offset = off[i];
+    std::memcpy(nodes, hn.data(), hn.size() * sizeof(lod_node_t));
+  }
+  return LOD_OK;
+}
+
+uint64_t lod_result_device_bytes(const lod_result_t* r) { return r ? r->bytes : 0; }
+
+void lod_free(lod_result_t* r) {
+  if (!r) return;
+  if (r->budget) r->budget->release(r->bytes);
+  delete r;
+}
+
+const char* lod_error_string(int status) {
+  switch (status) {
+    case LOD_OK: return "ok";
+    case LOD_NOT_READY: return "not ready";
+    case LOD_ERR_INVALID_ARG: return "invalid argument";
+    case LOD_ERR_OOM: return "device out of memory";
+    case LOD_ERR_BUDGET: return "request exceeds the HBM budget";
+    case LOD_ERR_CUDA: return "CUDA error";
+    case LOD_ERR_TIMEOUT: return "timed out";
+    case LOD_ERR_INTERNAL: return "internal consistency check failed";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ serving
+
+namespace {
+
+struct Request {
+  uint64_t ticket = 0;
+  const lod_point_t* d_points = nullptr;
+  uint64_t n = 0;
+  lod_params_t params;
+  uint64_t est = 0;
+  bool done = false;
+  int status = LOD_NOT_READY;
+  lod_result_t* result = nullptr;
+};
+
+}  // namespace
+
+struct lod_server {
+  lod_server_config_t cfg;
+  int device = 0;
+  std::shared_ptr<Budget> budget = std::make_shared<Budget>();
+  std::mutex mu;  // queue + table
+  std::condition_variable cv_done;
+  std::deque<std::shared_ptr<Request>> queue;
+  std::unordered_map<uint64_t, std::shared_ptr<Request>> table;
+  std::vector<std::thread> workers;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+
+  void worker_main() {
+    cudaSetDevice(device);
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return;
+    for (;;) {
+      std::shared_ptr<Request> rq;
+      {
+        // admission: FIFO head, once it fits into what the budget has left
+        std::unique_lock<std::mutex> lk(budget->mu);
+        for (;;) {
+          {
+            std::lock_guard<std::mutex> qk(mu);
+            if (!queue.empty()) {
+              auto& h = queue.front();
+              if (budget->in_use + h->est <= budget->limit) {
+                rq = h;
+                queue.pop_front();
+                budget->in_use += rq->est;
+              } else if (stop) {
+                // shutting down and the budget is held by resident results
+                h->status = LOD_ERR_BUDGET;
+                h->done = true;
+                queue.pop_front();
+                cv_done.notify_all();
+                continue;
+              }
+            } else if (stop) {
+              break;
+            }
+          }
+          if (rq) break;
+          budget->cv.wait_for(lk, std::chrono::milliseconds(50));
+        }
+      }
+      if (!rq) break;
+      lodk::TileInput ti{rq->d_points, rq->n};
+      std::shared_ptr<lodk::SharedBuffers> sh;
+      std::vector<lodk::TileResult> tr;
+      int rc = lodk::run_build(&ti, 1, rq->params, st, &sh, &tr, nullptr);
+      lod_result_t* res = nullptr;
+      if (rc == LOD_OK) {
+        res = make_result(sh, tr[0], rq->params.mode, sh->bytes);
+        if (!res) rc = LOD_ERR_OOM;
+      }
+      // the build's transient footprint is returned, the result stays counted
+      {
+        std::lock_guard<std::mutex> lk(budget->mu);
+        budget->in_use -= std::min(budget->in_use, rq->est);
+        if (res) {
+          budget->in_use += res->bytes;
+          res->budget = budget;
+        }
+      }
+      budget->cv.notify_all();
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        rq->status = rc;
+        rq->result = res;
+        rq->done = true;
+      }
+      cv_done.notify_all();
+    }
+    cudaStreamDestroy(st);
+  }
+};
+
+extern "C" {
+
+int lod_server_create(const lod_server_config_t* cfg, lod_server_t** out) {
+  if (!cfg || !out || cfg->max_inflight == 0 || cfg->hbm_budget_bytes == 0) return LOD_ERR_INVALID_ARG;
+  lod_server_t* s = new (std::nothrow) lod_server_t();
+  if (!s) return LOD_ERR_OOM;
+  s->cfg = *cfg;
+  cudaGetDevice(&s->device);
+  s->budget->limit = cfg->hbm_budget_bytes;
+  try {
+    for (uint32_t i = 0; i < cfg->max_inflight; ++i) s->workers.emplace_back(&lod_server::worker_main, s);
+  } catch (...) {
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->stop = true;
+    }
+    for (auto& w : s->workers) w.join();
+    delete s;
+    return LOD_ERR_OOM;
+  }
+  *out = s;
+  return LOD_OK;
+}
+
+int lod_submit(lod_server_t* s, const lod_point_t* d_points, uint64_t n, const lod_params_t* params,
+               uint64_t* ticket) {
+  if (!s || !ticket || (n && !d_points) || n > 0xFFFFFFFFull) return LOD_ERR_INVALID_ARG;
+  auto rq = std::make_shared<Request>();
+  rq->d_points = d_points;
+  rq->n = n;
+  rq->params = params ? *params : defaults();
+  if (rq->params.leaf_threshold == 0 || rq->params.mode > 1 || rq->params.max_depth > 32)
+    return LOD_ERR_INVALID_ARG;
+  rq->est = lodk::estimate_build_bytes(n, rq->params);
+  if (rq->est > s->budget->limit) return LOD_ERR_BUDGET;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) return LOD_ERR_INVALID_ARG;
+    rq->ticket = s->next_ticket++;
+    s->table[rq->ticket] = rq;
+    s->queue.push_back(rq);
+  }
+  s->budget->cv.notify_all();
+  *ticket = rq->ticket;
+  return LOD_OK;
+}
+
+static int take_if_done(lod_server_t* s, uint64_t ticket, lod_result_t** out, bool* found) {
+  auto it = s->table.find(ticket);
+  *found = it != s->table.end();
+  if (!*found) return LOD_ERR_INVALID_ARG;
+  if (!it->second->done) return LOD_NOT_READY;
+  const int rc = it->second->status;
+  if (rc == LOD_OK) *out = it->second->result;
+  s->table.erase(it);
+  return rc;
+}
+
+int lod_poll(lod_server_t* s, uint64_t ticket, lod_result_t** out) {
+  if (!s || !out) return LOD_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  bool found;
+  return take_if_done(s, ticket, out, &found);
+}
+
+int lod_wait(lod_server_t* s, uint64_t ticket, uint32_t timeout_ms, lod_result_t** out) {
+  if (!s || !out) return LOD_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+  for (;;) {
+    bool found;
+    const int rc = take_if_done(s, ticket, out, &found);
+    if (rc != LOD_NOT_READY) return rc;
+    if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
+      const int rc2 = take_if_done(s, ticket, out, &found);
+      return rc2 == LOD_NOT_READY ? LOD_ERR_TIMEOUT : rc2;
+    }
+  }
+}
+
+uint64_t lod_server_bytes_in_use(const lod_server_t* s) {
+  if (!s) return 0;
+  std::lock_guard<std::mutex> lk(s->budget->mu);
+  return s->budget->in_use;
+}
+
+int lod_server_destroy(lod_server_t* s) {
+  if (!s) return LOD_ERR_INVALID_ARG;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->budget->cv.notify_all();
+  for (auto& w : s->workers) w.join();
+  // requests finished but never polled: release their results
+  for (auto& kv : s->table)
+    if (kv.second->done && kv.second->result) lod_free(kv.second->result);
+  delete s;
+  return LOD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,168 @@
+// Internal definitions shared by the kernels and the host orchestrator of the
+// GB300 LOD builder.  Nothing here is part of the public C ABI (include/lod.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lod.h"
+
+namespace lodk {
+
+// ----------------------------------------------------------------- constants
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint32_t kChunk = 4096;      // points per work chunk of the streaming kernels
+constexpr uint32_t kChunkLog2 = 12;
+constexpr uint32_t kMaxLevels = 34;    // levels 0..32 plus one sentinel slot
+constexpr uint32_t kRootMaxD = 8;      // depth of the largest first counting grid (256^3 cells)
+constexpr uint32_t kSegMaxD = 4;       // depth of a refinement grid (16^3 cells, as in Section 3.1.5)
+constexpr uint32_t kSmemBins = 4096;   // grids up to 8^4 bins are counted in shared memory
+constexpr uint32_t kOctCells = 1u << 18;  // 64^3 cells of one child octant (Section 3.2.1)
+constexpr uint32_t kBlock = 1024;
+
+// Offset of level j inside a count/start pyramid stored level by level
+// (level j holds 8^j cells in Morton order), and the pyramid's total size.
+__host__ __device__ __forceinline__ uint64_t pyr_off(uint32_t j) {
+  return ((uint64_t(1) << (3 * j)) - 1) / 7;
+}
+__host__ __device__ __forceinline__ uint64_t pyr_size(uint32_t d) { return pyr_off(d + 1); }
+
+// ------------------------------------------------------------- descriptors
+
+// One independent problem (a whole cloud for lod_build, one tile for the
+// batched and serving paths).  Positions are tile-relative unless noted.
+struct TileDesc {
+  const int4* in;      // caller's input points (16-byte records)
+  uint32_t n;          // points
+  uint32_t log2S;      // root cube edge 2^log2S
+  int32_t min[3];      // root cube min corner (bounding-box minimum)
+  uint32_t node_cap;   // capacity of this tile's node region
+  uint64_t pt_base;    // absolute base of the tile in the shared point buffers
+  uint64_t node_base;  // absolute first node of the tile in the node buffer
+};
+
+// A counting grid ("source"): 8^d cells under one cube, the whole root for
+// the first grid of a tile, or an overflowing cell for a refinement grid
+// (Section 3.1.5).  Its points occupy [pt_off, pt_off + n) of the tile.
+struct SrcDesc {
+  uint32_t* cnt;       // count pyramid, levels 0..d (level j: 8^j cells)
+  uint32_t* start;     // start pyramid (tile-relative positions); its
+                       // bottom level is the scatter cursor
+  uint32_t* map;       // bottom cells: child source id where overflowing
+  uint32_t* ovf;       // bottom cells: overflow bit mask
+  int32_t min[3];
+  uint32_t tile;
+  uint32_t level;      // octree level of the source's root cell
+  uint32_t log2size;   // edge of the source's root cell
+  uint32_t d;          // grid depth (0..8)
+  uint32_t buf;        // where its points are: 0 tile input, 1 tmpA, 2 tmpB
+  uint32_t pt_off;
+  uint32_t n;
+  uint64_t chunk0;     // first chunk of this source in its round's chunk space
+};
+
+// Build-wide settings shared by every kernel of one build.
+struct BuildArgs {
+  const TileDesc* tiles;
+  SrcDesc* srcs;
+  uint32_t n_tiles;
+  uint32_t T;
+  uint32_t max_depth;
+  uint32_t mode;
+  int4* out;           // leaf points, all tiles, absolute positions
+  uint32_t* out_idx;   // original input index per leaf point (or null)
+  int4* tmp[2];        // refinement ping-pong buffers (absolute positions)
+  uint32_t* tmp_idx[2];
+};
+
+// Per-node internal bookkeeping of the voxel pass, indexed by absolute node.
+struct NodeAux {
+  uint32_t src, j, c;  // counting grid, local level, Morton cell (split pass)
+  uint32_t occ;        // voxels this node contributes to its parent's grid
+  uint64_t stage;      // first staging record of that contribution
+  uint64_t dense;      // absolute position of that contribution in the voxel array
+};
+
+// Counters written by kernels and read back by the host.
+struct DevCounters {
+  unsigned long long new_srcs;        // refinement grids created this round
+  unsigned long long new_points;      // points inside them
+  unsigned long long stage_used[2];   // staging records bump allocators
+  unsigned long long level_voxels;    // voxels of the level just scanned
+  unsigned long long next_cap;        // staging bound of the next level
+  unsigned int error;                 // nonzero: a kernel detected a problem
+  unsigned int pad;
+};
+
+enum : uint32_t {
+  kErrNodeCap = 1u,      // node capacity of a tile exceeded
+  kErrStageCap = 2u,     // staging capacity exceeded
+  kErrSrcCap = 4u,       // source table capacity exceeded
+  kErrInternal = 8u,
+};
+
+// ----------------------------------------------------------- device helpers
+
+__host__ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+
+// Spread the low 10 bits of v so that bit b lands on bit 3b.
+__host__ __device__ __forceinline__ uint32_t spread3(uint32_t v) {
+  v &= 0x3FFu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+// Morton index of a cell; within every bit triple x is the most significant,
+// so the low triple is the octant index k = 4*bx + 2*by + bz.
+__host__ __device__ __forceinline__ uint32_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+  return (spread3(x) << 2) | (spread3(y) << 1) | spread3(z);
+}
+
+// splitmix64 (Steele, Lea & Flood, OOPSLA 2014): first output of a generator
+// whose state is x.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Multiplicative inverse of an odd a modulo 2^64 by Newton's iteration
+// x <- x (2 - a x), which doubles the number of correct low bits each step.
+__host__ __device__ constexpr uint64_t inv_mod64(uint64_t a) {
+  uint64_t x = a;  // correct to 3 bits for odd a
+  for (int i = 0; i < 6; ++i) x *= 2 - a * x;
+  return x;
+}
+
+// Inverse of y = x ^ (x >> s) on 64 bits.
+__host__ __device__ __forceinline__ uint64_t unxorshift(uint64_t y, int s) {
+  uint64_t x = y;
+  for (int i = s; i < 64; i += s) x = y ^ (x >> s);
+  return x;
+}
+
+// splitmix64 is a bijection; this undoes it, step by step in reverse.
+__host__ __device__ __forceinline__ uint64_t splitmix64_inverse(uint64_t h) {
+  constexpr uint64_t i2 = inv_mod64(0x94D049BB133111EBull);
+  constexpr uint64_t i1 = inv_mod64(0xBF58476D1CE4E5B9ull);
+  uint64_t z = unxorshift(h, 31);
+  z *= i2;
+  z = unxorshift(z, 27);
+  z *= i1;
+  z = unxorshift(z, 30);
+  return z - 0x9E3779B97F4A7C15ull;
+}
+
+// 128^3 grid coordinate of an offset d (0 <= d < 2^L) inside a cube of edge
+// 2^L (Section 3.2: every node samples onto a 128^3 grid).
+__device__ __forceinline__ uint32_t grid_coord(uint32_t d, uint32_t L) {
+  return L >= 7 ? (uint32_t)((uint64_t)d >> (L - 7)) : (d << (7 - L));
+}
+
+__device__ __forceinline__ int4 ldg_stream(const int4* p) { return __ldcs(p); }
+
+}  // namespace lodk

@@ -1,0 +1,651 @@
+// Host orchestration of a (batched) LOD build.
+//
+// The device work of all tiles of a batch runs in the same launches: one
+// bounding-box pass, then counting rounds (first grid per tile, then the
+// refinement grids of overflowing cells), the node tables (one CTA per
+// tile), and the bottom-up voxel levels.  The host only reads back small
+// counters between phases to size the next allocations: once after the
+// bounding box, once per counting round, once after the node tables and
+// once per voxel level.
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <mutex>
+
+#include "engine.h"
+#include "kernels.h"
+
+namespace lodk {
+
+namespace {
+
+#define LOD_CK(x)                                                           \
+  do {                                                                      \
+    cudaError_t e_ = (x);                                                   \
+    if (e_ != cudaSuccess) {                                                \
+      return e_ == cudaErrorMemoryAllocation ? LOD_ERR_OOM : LOD_ERR_CUDA;  \
+    }                                                                       \
+  } while (0)
+
+int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+// Stream-ordered device buffer released on destruction.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaStream_t st;
+  explicit DevBuf(cudaStream_t s) : st(s) {}
+  DevBuf(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  cudaError_t alloc(size_t b) {
+    release();
+    if (b == 0) b = 16;
+    bytes = b;
+    return cudaMallocAsync(&p, b, st);
+  }
+  // grow keeping the first `keep` bytes
+  cudaError_t grow(size_t b, size_t keep) {
+    if (b <= bytes) return cudaSuccess;
+    void* q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, b, st);
+    if (e != cudaSuccess) return e;
+    if (p && keep) {
+      e = cudaMemcpyAsync(q, p, std::min(keep, bytes), cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return e;
+    }
+    release();
+    p = q;
+    bytes = b;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) cudaFreeAsync(p, st);
+    p = nullptr;
+    bytes = 0;
+  }
+  void* take() {
+    void* q = p;
+    p = nullptr;
+    bytes = 0;
+    return q;
+  }
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+// Pinned host staging for read-backs, one per host thread.
+struct HostStage {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~HostStage() {
+    if (p) cudaFreeHost(p);
+  }
+  void* get(size_t b) {
+    if (b > bytes) {
+      if (p) cudaFreeHost(p);
+      bytes = std::max<size_t>(b, 1 << 16);
+      if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+        p = nullptr;
+        bytes = 0;
+      }
+    }
+    return p;
+  }
+};
+thread_local HostStage tl_stage;
+
+// Pinned host arena for small uploads: cudaMemcpyAsync from pageable memory
+// synchronises the stream, from pinned memory it does not.  The arena is
+// recycled at every host synchronisation of the build (all earlier copies
+// have completed by then).
+struct Uploader {
+  cudaStream_t st;
+  char* base = nullptr;
+  size_t cap = 0, used = 0;
+  std::vector<char*> retired;
+  explicit Uploader(cudaStream_t s) : st(s) {}
+  ~Uploader() {
+    cudaStreamSynchronize(st);
+    for (char* r : retired) cudaFreeHost(r);
+    if (base) cudaFreeHost(base);
+  }
+  cudaError_t put(void* dst, const void* src, size_t bytes) {
+    if (!bytes) return cudaSuccess;
+    const size_t need = (bytes + 255) & ~size_t(255);
+    if (used + need > cap) {
+      if (base) retired.push_back(base);
+      cap = std::max<size_t>(need, std::max<size_t>(cap * 2, 1 << 20));
+      void* q = nullptr;
+      cudaError_t e = cudaMallocHost(&q, cap);
+      if (e != cudaSuccess) {
+        base = nullptr;
+        cap = used = 0;
+        return e;
+      }
+      base = static_cast<char*>(q);
+      used = 0;
+    }
+    std::memcpy(base + used, src, bytes);
+    cudaError_t e = cudaMemcpyAsync(dst, base + used, bytes, cudaMemcpyHostToDevice, st);
+    used += need;
+    return e;
+  }
+  // call right after a stream synchronisation
+  void recycle() {
+    used = 0;
+    for (char* r : retired) cudaFreeHost(r);
+    retired.clear();
+  }
+};
+
+uint32_t ceil_log4(double x) {
+  uint32_t d = 0;
+  double v = 1.0;
+  while (v < x && d < 32) {
+    v *= 4.0;
+    ++d;
+  }
+  return d;
+}
+
+// Depth of a tile's first counting grid: deep enough that surface-like
+// clouds reach leaf size without refinement (about 4x fewer points per
+// level), capped at 256^3 cells, the cube's own size and max_depth.
+uint32_t choose_root_depth(uint64_t n, uint32_t T, uint32_t log2S, uint32_t max_depth) {
+  if (n <= T || log2S == 0 || max_depth == 0) return 0;
+  uint32_t d = ceil_log4((double)n / (double)T) + 1;
+  d = std::min(d, kRootMaxD);
+  d = std::min(d, log2S);
+  d = std::min(d, max_depth);
+  return std::max(d, 1u);
+}
+
+uint64_t ipow8(uint32_t d) { return uint64_t(1) << (3 * d); }
+
+// Shared-memory pool layout of a set of sources (all ovf words, then all
+// count pyramids, start pyramids and maps), so that the parts that must
+// start at zero (ovf, counts) are one contiguous range.
+struct PoolLayout {
+  uint64_t ovf = 0, cnt = 0, start = 0, map = 0, total = 0, zero = 0;  // in u32 units
+};
+
+PoolLayout layout_pool(const std::vector<SrcDesc>& v, size_t first, size_t n, std::vector<uint64_t>* offs) {
+  PoolLayout L;
+  uint64_t o_ovf = 0, o_cnt = 0, o_map = 0;
+  offs->assign(4 * n, 0);
+  for (size_t i = 0; i < n; ++i) {
+    const uint32_t d = v[first + i].d;
+    (*offs)[4 * i + 0] = o_ovf;
+    o_ovf += (ipow8(d) + 31) / 32;
+    (*offs)[4 * i + 1] = o_cnt;
+    (*offs)[4 * i + 2] = o_cnt;  // same offset inside the start region
+    o_cnt += pyr_size(d);
+    (*offs)[4 * i + 3] = o_map;
+    o_map += ipow8(d);
+  }
+  L.ovf = 0;
+  L.cnt = o_ovf;
+  L.start = L.cnt + o_cnt;
+  L.map = L.start + o_cnt;
+  L.total = L.map + o_map;
+  L.zero = L.start;  // ovf + cnt
+  return L;
+}
+
+}  // namespace
+
+static std::mutex g_free_mu;
+static cudaStream_t g_free_streams[64] = {};
+
+cudaStream_t free_stream() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_free_mu);
+  if (dev < 0 || dev >= 64) return nullptr;
+  if (!g_free_streams[dev]) cudaStreamCreateWithFlags(&g_free_streams[dev], cudaStreamNonBlocking);
+  return g_free_streams[dev];
+}
+
+SharedBuffers::~SharedBuffers() {
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess) return;
+  cudaSetDevice(device);
+  cudaStream_t fs = free_stream();
+  for (void* q : {points, index, nodes, voxels, input})
+    if (q) cudaFreeAsync(q, fs);
+  cudaSetDevice(prev);
+}
+
+uint64_t estimate_result_bytes(uint64_t n, const lod_params_t& p) {
+  const bool idx = p.mode == LOD_PICK || (p.flags & LOD_FLAG_LEAF_INDEX);
+  const uint64_t T = std::max<uint32_t>(p.leaf_threshold, 1);
+  const uint64_t nodes = 64 + 16 * ((n + T - 1) / T);
+  return n * 16 + (idx ? n * 4 : 0) + (n / 2 + 1024) * 16 + nodes * sizeof(lod_node_t);
+}
+
+uint64_t estimate_build_bytes(uint64_t n, const lod_params_t& p) {
+  const uint64_t T = std::max<uint32_t>(p.leaf_threshold, 1);
+  const uint32_t d = choose_root_depth(n, (uint32_t)T, 32, 32);
+  const uint64_t pool = (2 * pyr_size(d) + ipow8(d) + ipow8(d) / 32 + 1) * 4;
+  const uint64_t nodes = 64 + 16 * ((n + T - 1) / T);
+  // result + one refinement buffer + two staging levels + node aux + pool
+  return estimate_result_bytes(n, p) + n * 20 + n * 40 + nodes * sizeof(NodeAux) + pool + (16u << 20);
+}
+
+int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaStream_t st,
+              std::shared_ptr<SharedBuffers>* shared_out, std::vector<TileResult>* tiles_out, BuildStats* stats) {
+  BuildStats S;
+  if (nt == 0 || !tin) return LOD_ERR_INVALID_ARG;
+  if (prm.leaf_threshold == 0 || prm.mode > 1 || prm.max_depth > 32) return LOD_ERR_INVALID_ARG;
+  const bool want_idx = prm.mode == LOD_PICK || (prm.flags & LOD_FLAG_LEAF_INDEX);
+  const uint32_t T = prm.leaf_threshold;
+
+  // ---- tile table and round-0 chunk space
+  std::vector<TileDesc> td(nt);
+  std::vector<uint64_t> chunk0(nt + 1, 0);
+  uint64_t M = 0;
+  for (uint32_t t = 0; t < nt; ++t) {
+    const uint64_t n = tin[t].n;
+    if (n > 0xFFFFFFFFull) return LOD_ERR_INVALID_ARG;
+    if (n > 0 && (!tin[t].d_points || (reinterpret_cast<uintptr_t>(tin[t].d_points) & 15u)))
+      return LOD_ERR_INVALID_ARG;
+    std::memset(&td[t], 0, sizeof(TileDesc));
+    td[t].in = reinterpret_cast<const int4*>(tin[t].d_points);
+    td[t].n = (uint32_t)n;
+    td[t].pt_base = M;
+    M += n;
+    chunk0[t + 1] = chunk0[t] + (n + kChunk - 1) / kChunk;
+  }
+  const uint64_t n_chunks0 = chunk0[nt];
+  std::vector<uint32_t> chunk_tile(n_chunks0);
+  for (uint32_t t = 0; t < nt; ++t)
+    for (uint64_t c = chunk0[t]; c < chunk0[t + 1]; ++c) chunk_tile[c] = t;
+
+  auto sh = std::make_shared<SharedBuffers>();
+  LOD_CK(cudaGetDevice(&sh->device));
+  const int grid = 2 * sm_count();
+  Uploader up_(st);
+
+  DevBuf d_points(st), d_index(st), d_tiles(st), d_chunk0(st), d_chunk_src(st), d_bbox(st), d_ctr(st),
+      d_nchunks(st);
+  LOD_CK(d_points.alloc(M * 16));
+  if (want_idx) LOD_CK(d_index.alloc(M * 4));
+  LOD_CK(d_tiles.alloc(nt * sizeof(TileDesc)));
+  LOD_CK(d_chunk0.alloc((nt + 1) * sizeof(uint64_t)));
+  LOD_CK(d_chunk_src.alloc(std::max<uint64_t>(n_chunks0, 1) * 4));
+  LOD_CK(d_bbox.alloc(nt * 6 * sizeof(int)));
+  LOD_CK(d_ctr.alloc(sizeof(DevCounters)));
+  LOD_CK(d_nchunks.alloc(sizeof(unsigned long long)));
+  LOD_CK(cudaMemsetAsync(d_ctr.p, 0, sizeof(DevCounters), st));
+  LOD_CK(up_.put(d_tiles.p, td.data(), nt * sizeof(TileDesc)));
+  LOD_CK(up_.put(d_chunk0.p, chunk0.data(), (nt + 1) * sizeof(uint64_t)));
+  if (n_chunks0)
+    LOD_CK(up_.put(d_chunk_src.p, chunk_tile.data(), n_chunks0 * 4));
+  {
+    std::vector<int> init(6 * nt);
+    for (uint32_t t = 0; t < nt; ++t)
+      for (int i = 0; i < 3; ++i) {
+        init[6 * t + i] = INT_MAX;
+        init[6 * t + 3 + i] = INT_MIN;
+      }
+    LOD_CK(up_.put(d_bbox.p, init.data(), init.size() * sizeof(int)));
+  }
+
+  // ---- bounding box (root cube)
+  LOD_CK(launch_bbox(d_tiles.as<TileDesc>(), d_chunk_src.as<uint32_t>(), n_chunks0, d_chunk0.as<uint64_t>(),
+                     d_bbox.as<int>(), grid, st));
+  ++S.launches;
+  std::vector<int> bbox(6 * nt);
+  LOD_CK(cudaMemcpyAsync(bbox.data(), d_bbox.p, bbox.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+  LOD_CK(cudaStreamSynchronize(st));
+  up_.recycle();
+  ++S.host_syncs;
+
+  std::vector<SrcDesc> srcs(nt);
+  uint64_t src_bound0 = 0;
+  for (uint32_t t = 0; t < nt; ++t) {
+    if (td[t].n == 0) {
+      td[t].min[0] = td[t].min[1] = td[t].min[2] = 0;
+      td[t].log2S = 0;
+    } else {
+      int64_t ext = 0;
+      for (int a = 0; a < 3; ++a) {
+        td[t].min[a] = bbox[6 * t + a];
+        ext = std::max<int64_t>(ext, (int64_t)bbox[6 * t + 3 + a] - (int64_t)bbox[6 * t + a]);
+      }
+      uint32_t L = 0;
+      while ((int64_t(1) << L) <= ext) ++L;  // smallest power of two > extent
+      td[t].log2S = L;
+    }
+    SrcDesc& s = srcs[t];
+    std::memset(&s, 0, sizeof(SrcDesc));
+    for (int a = 0; a < 3; ++a) s.min[a] = td[t].min[a];
+    s.tile = t;
+    s.level = 0;
+    s.log2size = td[t].log2S;
+    s.d = choose_root_depth(td[t].n, T, td[t].log2S, prm.max_depth);
+    s.buf = 0;
+    s.pt_off = 0;
+    s.n = td[t].n;
+    s.chunk0 = chunk0[t];
+    src_bound0 += td[t].n / (T + 1ull);
+  }
+
+  // ---- counting rounds
+  DevBuf d_srcs(st), d_jobs(st), d_tmp0(st), d_tmp1(st), d_tmpi0(st), d_tmpi1(st);
+  std::vector<std::unique_ptr<DevBuf>> pools;
+  uint64_t src_cap = nt + src_bound0 + 16;
+  LOD_CK(d_srcs.alloc(src_cap * sizeof(SrcDesc)));
+
+  BuildArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.n_tiles = nt;
+  A.T = T;
+  A.max_depth = prm.max_depth;
+  A.mode = prm.mode;
+  A.out = d_points.as<int4>();
+  A.out_idx = want_idx ? d_index.as<uint32_t>() : nullptr;
+
+  uint32_t round_first = 0, round_n = nt, n_src = nt;
+  uint64_t round_chunks = n_chunks0;
+  for (uint32_t round = 0;; ++round) {
+    ++S.rounds;
+    // pool for this round's grids
+    std::vector<uint64_t> offs;
+    const PoolLayout L = layout_pool(srcs, round_first, round_n, &offs);
+    pools.emplace_back(new DevBuf(st));
+    DevBuf& pool = *pools.back();
+    LOD_CK(pool.alloc(L.total * 4));
+    LOD_CK(cudaMemsetAsync(pool.p, 0, L.zero * 4, st));
+    uint32_t* pb = pool.as<uint32_t>();
+    for (uint32_t i = 0; i < round_n; ++i) {
+      SrcDesc& s = srcs[round_first + i];
+      s.ovf = pb + L.ovf + offs[4 * i + 0];
+      s.cnt = pb + L.cnt + offs[4 * i + 1];
+      s.start = pb + L.start + offs[4 * i + 2];
+      s.map = pb + L.map + offs[4 * i + 3];
+    }
+    LOD_CK(up_.put(d_srcs.as<SrcDesc>() + round_first, srcs.data() + round_first,
+                           round_n * sizeof(SrcDesc)));
+    LOD_CK(up_.put(d_nchunks.p, &round_chunks, sizeof(round_chunks)));
+    A.tiles = d_tiles.as<TileDesc>();
+    A.srcs = d_srcs.as<SrcDesc>();
+    A.tmp[0] = d_tmp0.as<int4>();
+    A.tmp[1] = d_tmp1.as<int4>();
+    A.tmp_idx[0] = d_tmpi0.as<uint32_t>();
+    A.tmp_idx[1] = d_tmpi1.as<uint32_t>();
+
+    const int cgrid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)grid, round_chunks));
+    LOD_CK(launch_count(A, d_chunk_src.as<uint32_t>(), d_nchunks.as<unsigned long long>(), cgrid, st));
+    ++S.launches;
+
+    // pyramid jobs: up passes (bottom levels d, d-4, ...), down passes (tops 0, 4, ...)
+    std::vector<std::vector<PyrJob>> up, down;
+    for (uint32_t i = 0; i < round_n; ++i) {
+      const uint32_t sid = round_first + i;
+      const uint32_t d = srcs[sid].d;
+      uint32_t pass = 0;
+      for (int jb = (int)d; jb > 0; jb -= 4, ++pass) {
+        if (up.size() <= pass) up.emplace_back();
+        const uint32_t k = std::min<uint32_t>(4, jb);
+        const uint64_t blocks = ipow8(jb - k);
+        for (uint64_t b = 0; b < blocks; ++b) up[pass].push_back({sid, (uint32_t)jb, (uint32_t)b});
+      }
+      pass = 0;
+      for (uint32_t jt = 0; jt < d || (d == 0 && jt == 0); jt += 4, ++pass) {
+        if (down.size() <= pass) down.emplace_back();
+        const uint64_t blocks = ipow8(jt);
+        for (uint64_t b = 0; b < blocks; ++b) down[pass].push_back({sid, jt, (uint32_t)b});
+        if (d == 0) break;
+      }
+    }
+    size_t n_jobs = 0;
+    for (auto& v : up) n_jobs += v.size();
+    for (auto& v : down) n_jobs += v.size();
+    std::vector<PyrJob> all;
+    all.reserve(n_jobs);
+    for (auto& v : up) all.insert(all.end(), v.begin(), v.end());
+    for (auto& v : down) all.insert(all.end(), v.begin(), v.end());
+    LOD_CK(d_jobs.alloc(std::max<size_t>(all.size(), 1) * sizeof(PyrJob)));
+    LOD_CK(up_.put(d_jobs.p, all.data(), all.size() * sizeof(PyrJob)));
+    size_t jo = 0;
+    for (auto& v : up) {
+      LOD_CK(launch_pyr_up(A, d_jobs.as<PyrJob>() + jo, (uint32_t)v.size(), st));
+      ++S.launches;
+      jo += v.size();
+    }
+    // capacity of the source table for grids created by this round
+    uint64_t round_points = 0;
+    for (uint32_t i = 0; i < round_n; ++i) round_points += srcs[round_first + i].n;
+    const uint64_t need = (uint64_t)n_src + round_points / (T + 1ull) + 16;
+    if (need > src_cap) {
+      LOD_CK(d_srcs.grow(need * sizeof(SrcDesc), (size_t)n_src * sizeof(SrcDesc)));
+      src_cap = need;
+      A.srcs = d_srcs.as<SrcDesc>();
+    }
+    LOD_CK(cudaMemsetAsync(d_ctr.p, 0, sizeof(DevCounters), st));
+    const uint32_t next_buf = 1 + (round & 1);
+    for (auto& v : down) {
+      LOD_CK(launch_pyr_down(A, d_jobs.as<PyrJob>() + jo, (uint32_t)v.size(), n_src, (uint32_t)(src_cap - n_src),
+                             next_buf, d_ctr.as<DevCounters>(), st));
+      ++S.launches;
+      jo += v.size();
+    }
+    DevCounters* hc = static_cast<DevCounters*>(tl_stage.get(sizeof(DevCounters)));
+    if (!hc) return LOD_ERR_OOM;
+    LOD_CK(cudaMemcpyAsync(hc, d_ctr.p, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+    LOD_CK(cudaStreamSynchronize(st));
+    up_.recycle();
+    ++S.host_syncs;
+    if (hc->error) return LOD_ERR_INTERNAL;
+    const uint32_t new_srcs = (uint32_t)hc->new_srcs;
+    const uint64_t new_points = hc->new_points;
+    if (new_srcs) {
+      DevBuf& tb = (round & 1) ? d_tmp1 : d_tmp0;
+      DevBuf& ti = (round & 1) ? d_tmpi1 : d_tmpi0;
+      if (!tb.p) {
+        LOD_CK(tb.alloc(M * 16));
+        if (want_idx) LOD_CK(ti.alloc(M * 4));
+      }
+      A.tmp[0] = d_tmp0.as<int4>();
+      A.tmp[1] = d_tmp1.as<int4>();
+      A.tmp_idx[0] = d_tmpi0.as<uint32_t>();
+      A.tmp_idx[1] = d_tmpi1.as<uint32_t>();
+    }
+    LOD_CK(launch_scatter(A, d_chunk_src.as<uint32_t>(), d_nchunks.as<unsigned long long>(), round, cgrid, st));
+    ++S.launches;
+    if (!new_srcs) break;
+
+    // next round: the new grids, their chunk space
+    srcs.resize(n_src + new_srcs);
+    LOD_CK(cudaMemcpyAsync(srcs.data() + n_src, d_srcs.as<SrcDesc>() + n_src, new_srcs * sizeof(SrcDesc),
+                           cudaMemcpyDeviceToHost, st));
+    LOD_CK(cudaStreamSynchronize(st));
+    up_.recycle();
+    ++S.host_syncs;
+    round_first = n_src;
+    round_n = new_srcs;
+    n_src += new_srcs;
+    round_chunks = 0;
+    for (uint32_t i = 0; i < round_n; ++i) {
+      SrcDesc& s = srcs[round_first + i];
+      s.chunk0 = round_chunks;
+      round_chunks += (s.n + kChunk - 1) / kChunk;
+    }
+    std::vector<uint32_t> cs(round_chunks);
+    for (uint32_t i = 0; i < round_n; ++i) {
+      const SrcDesc& s = srcs[round_first + i];
+      const uint64_t nc = (s.n + kChunk - 1) / kChunk;
+      for (uint64_t c = 0; c < nc; ++c) cs[s.chunk0 + c] = round_first + i;
+    }
+    (void)new_points;
+    LOD_CK(d_chunk_src.alloc(std::max<uint64_t>(round_chunks, 1) * 4));
+    LOD_CK(up_.put(d_chunk_src.p, cs.data(), round_chunks * 4));
+  }
+
+  // ---- node tables
+  std::vector<uint32_t> node_cap(nt);
+  for (uint32_t t = 0; t < nt; ++t) node_cap[t] = (uint32_t)std::min<uint64_t>(64 + 16 * ((td[t].n + T - 1) / T), 0x7FFFFFFFull);
+  DevBuf d_nodes(st), d_aux(st), d_lvl(st), d_nn(st), d_leafcap(st);
+  std::vector<uint32_t> n_nodes(nt), lvl((size_t)nt * (kMaxLevels + 1));
+  std::vector<unsigned long long> leaf_cap(kMaxLevels + 1);
+  uint64_t total_cap = 0;
+  for (int attempt = 0;; ++attempt) {
+    total_cap = 0;
+    for (uint32_t t = 0; t < nt; ++t) {
+      td[t].node_base = total_cap;
+      td[t].node_cap = node_cap[t];
+      total_cap += node_cap[t];
+    }
+    LOD_CK(up_.put(d_tiles.p, td.data(), nt * sizeof(TileDesc)));
+    LOD_CK(d_nodes.alloc(total_cap * sizeof(lod_node_t)));
+    LOD_CK(d_aux.alloc(total_cap * sizeof(NodeAux)));
+    LOD_CK(d_lvl.alloc(lvl.size() * 4));
+    LOD_CK(d_nn.alloc(nt * 4));
+    LOD_CK(d_leafcap.alloc(leaf_cap.size() * 8));
+    LOD_CK(cudaMemsetAsync(d_leafcap.p, 0, leaf_cap.size() * 8, st));
+    LOD_CK(cudaMemsetAsync(d_ctr.p, 0, sizeof(DevCounters), st));
+    LOD_CK(launch_nodes(A, d_nodes.as<lod_node_t>(), d_aux.as<NodeAux>(), d_lvl.as<uint32_t>(), d_nn.as<uint32_t>(),
+                        d_leafcap.as<unsigned long long>(), d_ctr.as<DevCounters>(), st));
+    ++S.launches;
+    LOD_CK(cudaMemcpyAsync(n_nodes.data(), d_nn.p, nt * 4, cudaMemcpyDeviceToHost, st));
+    LOD_CK(cudaMemcpyAsync(lvl.data(), d_lvl.p, lvl.size() * 4, cudaMemcpyDeviceToHost, st));
+    LOD_CK(cudaMemcpyAsync(leaf_cap.data(), d_leafcap.p, leaf_cap.size() * 8, cudaMemcpyDeviceToHost, st));
+    LOD_CK(cudaStreamSynchronize(st));
+    up_.recycle();
+    ++S.host_syncs;
+    bool retry = false;
+    for (uint32_t t = 0; t < nt; ++t)
+      if (n_nodes[t] == kNone) {
+        node_cap[t] = (uint32_t)std::min<uint64_t>(uint64_t(node_cap[t]) * 4, 0x7FFFFFFFull);
+        retry = true;
+      }
+    if (!retry) break;
+    if (attempt > 8) return LOD_ERR_INTERNAL;
+  }
+  std::vector<uint32_t> n_levels(nt);
+  uint32_t max_levels = 0;
+  for (uint32_t t = 0; t < nt; ++t) {
+    uint32_t l = 0;
+    while (l < kMaxLevels && lvl[(size_t)t * (kMaxLevels + 1) + l] < n_nodes[t]) ++l;
+    n_levels[t] = l;
+    max_levels = std::max(max_levels, l);
+    S.nodes += n_nodes[t];
+  }
+  pools.clear();
+  d_tmp0.release();
+  d_tmp1.release();
+  d_tmpi0.release();
+  d_tmpi1.release();
+
+  // ---- voxel levels, bottom-up
+  DevBuf d_dense(st), d_stage0(st), d_stage1(st), d_sum0(st), d_sum1(st), d_itemp(st), d_parp(st), d_tvox(st);
+  const bool filt = prm.mode == LOD_FILTER;
+  uint64_t dense_cap = std::max<uint64_t>(M / 2, 1024);
+  LOD_CK(d_dense.alloc(dense_cap * 16));
+  LOD_CK(d_tvox.alloc(nt * 8));
+  LOD_CK(cudaMemsetAsync(d_tvox.p, 0, nt * 8, st));
+  LOD_CK(d_itemp.alloc((nt + 1) * 4));
+  LOD_CK(d_parp.alloc((nt + 1) * 4));
+  uint64_t V = 0, inner_cap = 0;
+  uint64_t stage_cap[2] = {0, 0};
+  VoxLevel vl;
+  std::memset(&vl, 0, sizeof(vl));
+  bool have_top = false;
+  std::vector<uint32_t> item_prefix(nt + 1), parent_prefix(nt + 1);
+  for (int l = (int)max_levels - 2; l >= 0; --l) {
+    // items: nodes at level l + 1; parents: nodes at level l
+    item_prefix[0] = parent_prefix[0] = 0;
+    for (uint32_t t = 0; t < nt; ++t) {
+      const uint32_t* ls = &lvl[(size_t)t * (kMaxLevels + 1)];
+      item_prefix[t + 1] = item_prefix[t] + (ls[l + 2] - ls[l + 1]);
+      parent_prefix[t + 1] = parent_prefix[t] + (ls[l + 1] - ls[l]);
+    }
+    const uint32_t n_items = item_prefix[nt], n_par = parent_prefix[nt];
+    const int par = (l + 1) & 1;
+    DevBuf& stg = par ? d_stage1 : d_stage0;
+    DevBuf& sum = par ? d_sum1 : d_sum0;
+    const uint64_t bound = leaf_cap[l + 1] + inner_cap + 1;
+    if (bound > stage_cap[par]) {
+      LOD_CK(stg.alloc(bound * 16));
+      if (filt) LOD_CK(sum.alloc(bound * 16));
+      stage_cap[par] = bound;
+    }
+    LOD_CK(up_.put(d_itemp.p, item_prefix.data(), (nt + 1) * 4));
+    LOD_CK(up_.put(d_parp.p, parent_prefix.data(), (nt + 1) * 4));
+    LOD_CK(cudaMemsetAsync(d_ctr.p, 0, sizeof(DevCounters), st));
+    vl.level = (uint32_t)l;
+    vl.n_items = n_items;
+    vl.item_prefix = d_itemp.as<uint32_t>();
+    vl.lvl_start = d_lvl.as<uint32_t>();
+    vl.nodes = d_nodes.as<lod_node_t>();
+    vl.aux = d_aux.as<NodeAux>();
+    vl.stage_out = stg.as<int4>();
+    vl.stage_out_sum = filt ? sum.as<ulonglong2>() : nullptr;
+    vl.stage_cap = stage_cap[par];
+    vl.stage_in = (par ? d_stage0 : d_stage1).as<int4>();
+    vl.stage_in_sum = filt ? (par ? d_sum0 : d_sum1).as<ulonglong2>() : nullptr;
+    vl.dense = d_dense.as<int4>();
+    vl.stage_used = &d_ctr.as<DevCounters>()->stage_used[par];
+    A.tiles = d_tiles.as<TileDesc>();
+    LOD_CK(launch_vox(A, vl, d_ctr.as<DevCounters>(), st));
+    LOD_CK(launch_level_scan(A, vl, d_parp.as<uint32_t>(), n_par, V, d_tvox.as<unsigned long long>(),
+                             d_ctr.as<DevCounters>(), st));
+    S.launches += 2;
+    DevCounters* hc = static_cast<DevCounters*>(tl_stage.get(sizeof(DevCounters)));
+    if (!hc) return LOD_ERR_OOM;
+    LOD_CK(cudaMemcpyAsync(hc, d_ctr.p, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+    LOD_CK(cudaStreamSynchronize(st));
+    up_.recycle();
+    ++S.host_syncs;
+    if (hc->error) return LOD_ERR_INTERNAL;
+    V += hc->level_voxels;
+    inner_cap = hc->next_cap;
+    if (V > dense_cap) {
+      const uint64_t nc = std::max<uint64_t>(V, dense_cap * 2);
+      LOD_CK(d_dense.grow(nc * 16, (V - hc->level_voxels) * 16));
+      dense_cap = nc;
+    }
+    have_top = true;
+  }
+  if (have_top) {
+    vl.dense = d_dense.as<int4>();
+    LOD_CK(launch_copy_items(A, vl, st));
+    ++S.launches;
+  }
+  std::vector<unsigned long long> tvox(nt);
+  LOD_CK(cudaMemcpyAsync(tvox.data(), d_tvox.p, nt * 8, cudaMemcpyDeviceToHost, st));
+  LOD_CK(cudaStreamSynchronize(st));
+  up_.recycle();
+  ++S.host_syncs;
+
+  // ---- results
+  tiles_out->assign(nt, TileResult());
+  for (uint32_t t = 0; t < nt; ++t) {
+    TileResult& r = (*tiles_out)[t];
+    r.pt_base = td[t].pt_base;
+    r.n_points = td[t].n;
+    r.node_base = td[t].node_base;
+    r.n_nodes = n_nodes[t];
+    r.n_levels = n_levels[t];
+    r.n_voxels = tvox[t];
+  }
+  sh->bytes = M * 16 + (want_idx ? M * 4 : 0) + total_cap * sizeof(lod_node_t) + dense_cap * 16;
+  sh->points = d_points.take();
+  sh->index = want_idx ? d_index.take() : nullptr;
+  sh->nodes = d_nodes.take();
+  sh->voxels = d_dense.take();
+  *shared_out = sh;
+  S.voxels = V;
+  if (stats) *stats = S;
+  return LOD_OK;
+}
+
+}  // namespace lodk

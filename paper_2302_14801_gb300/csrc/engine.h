@@ -1,0 +1,60 @@
+// Host orchestration of one (batched) LOD build — internal.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <memory>
+#include <vector>
+
+#include "lod.h"
+
+namespace lodk {
+
+// Device buffers produced by one build and shared by its results.
+struct SharedBuffers {
+  int device = 0;
+  void* points = nullptr;   // leaf points of all tiles
+  void* index = nullptr;    // original indices (or null)
+  void* nodes = nullptr;    // node tables of all tiles
+  void* voxels = nullptr;   // voxels of all tiles
+  void* input = nullptr;    // owned copy of host input (lod_build_from_host), or null
+  uint64_t bytes = 0;
+  ~SharedBuffers();
+};
+
+struct TileResult {
+  uint64_t pt_base = 0, n_points = 0;
+  uint64_t node_base = 0;
+  uint32_t n_nodes = 0, n_levels = 0;
+  uint64_t n_voxels = 0;
+};
+
+struct BuildStats {
+  uint32_t rounds = 0;       // counting rounds (1 + refinement rounds)
+  uint32_t host_syncs = 0;
+  uint32_t launches = 0;
+  uint64_t voxels = 0;
+  uint64_t nodes = 0;
+};
+
+struct TileInput {
+  const lod_point_t* d_points;
+  uint64_t n;
+};
+
+// Runs the complete build of n_tiles independent tiles on stream st.
+// On LOD_OK fills *shared and tiles_out (one entry per tile).
+int run_build(const TileInput* tiles, uint32_t n_tiles, const lod_params_t& params, cudaStream_t st,
+              std::shared_ptr<SharedBuffers>* shared, std::vector<TileResult>* tiles_out, BuildStats* stats);
+
+// Rough device footprint (bytes) of building n points (result + temporaries).
+uint64_t estimate_build_bytes(uint64_t n, const lod_params_t& params);
+// Rough device footprint of a finished result of n points.
+uint64_t estimate_result_bytes(uint64_t n, const lod_params_t& params);
+
+// A library-owned non-blocking stream of the current device used to
+// release buffers asynchronously.
+cudaStream_t free_stream();
+
+}  // namespace lodk

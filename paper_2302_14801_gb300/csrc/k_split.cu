@@ -1,0 +1,610 @@
+// Split of the input into octree leaves (Section 3.1 of the paper):
+// bounding box, hierarchical counting sort with recursive refinement of
+// overflowing cells, and the breadth-first node table.
+//
+// GB300 design: every pass streams the 16-byte AoS points with coalesced
+// 128-bit loads in 4096-point chunks; each CTA owns a contiguous run of
+// chunks so that per-source state (a shared-memory histogram, a reduction)
+// is flushed only when the source changes.  Counting grids of up to 8^4
+// cells are privatised in shared memory; larger first grids (up to 256^3,
+// which stays resident in the 129 MB L2) use warp-aggregated global
+// atomics.  Grid pyramids (per-level sums and exclusive-scan starts) are
+// built in 4-level blocks in shared memory.  No kernel ever waits on
+// another CTA.
+#include <climits>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace lodk {
+
+namespace {
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+// Morton cell of point p inside a source grid (8^d cells under a cube of
+// edge 2^log2size with min corner mn).
+__device__ __forceinline__ uint32_t src_bin(const int4& p, const int32_t mn[3], uint32_t log2size,
+                                            uint32_t d) {
+  if (d == 0) return 0;
+  const uint32_t sh = log2size - d;
+  const uint32_t ux = (uint32_t)((uint64_t)((uint32_t)p.x - (uint32_t)mn[0]) >> sh);
+  const uint32_t uy = (uint32_t)((uint64_t)((uint32_t)p.y - (uint32_t)mn[1]) >> sh);
+  const uint32_t uz = (uint32_t)((uint64_t)((uint32_t)p.z - (uint32_t)mn[2]) >> sh);
+  return morton3(ux, uy, uz);
+}
+
+// Compact every third bit (inverse of spread3) for 8 output bits.
+__device__ __forceinline__ uint32_t compact3(uint32_t v) {
+  v &= 0x09249249u;
+  v = (v | (v >> 2)) & 0x030C30C3u;
+  v = (v | (v >> 4)) & 0x0300F00Fu;
+  v = (v | (v >> 8)) & 0x030000FFu;
+  v = (v | (v >> 16)) & 0x000003FFu;
+  return v;
+}
+
+// Pointer to the points of a source and the tile-absolute base of its range.
+__device__ __forceinline__ const int4* src_points(const BuildArgs& a, const SrcDesc& s, const TileDesc& t) {
+  if (s.buf == 0) return t.in;  // round 0 reads the caller's input, index = input index
+  return a.tmp[s.buf - 1] + t.pt_base + s.pt_off;
+}
+
+// Depth of a refinement grid for a cell of n points (surfaces shrink by
+// about 4x per level): enough levels to reach T, capped at 4 (16^3 cells).
+__device__ __forceinline__ uint32_t choose_seg_depth(uint64_t n, uint32_t T, uint32_t level,
+                                                     uint32_t log2size, uint32_t max_depth) {
+  uint32_t d = 1;
+  while (d < kSegMaxD && (n >> (2 * d)) > T) ++d;
+  d = min(d, max_depth - level);
+  d = min(d, log2size);
+  return d;
+}
+
+}  // namespace
+
+// --------------------------------------------------------------- bounding box
+
+__global__ void __launch_bounds__(kBlock) k_bbox(const TileDesc* __restrict__ tiles,
+                                                 const uint32_t* __restrict__ chunk_tile, uint64_t n_chunks,
+                                                 const uint64_t* __restrict__ tile_chunk0,
+                                                 int* __restrict__ bbox) {
+  __shared__ int red[32][6];
+  const uint64_t per = (n_chunks + gridDim.x - 1) / gridDim.x;
+  const uint64_t c0 = (uint64_t)blockIdx.x * per;
+  const uint64_t c1 = min(c0 + per, n_chunks);
+  uint32_t cur = kNone;
+  int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {INT_MIN, INT_MIN, INT_MIN};
+
+  auto flush = [&](uint32_t t) {
+    const uint32_t w = threadIdx.x >> 5;
+    int v[6] = {mn[0], mn[1], mn[2], mx[0], mx[1], mx[2]};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      v[i] = __reduce_min_sync(0xFFFFFFFFu, v[i]);
+      v[i + 3] = __reduce_max_sync(0xFFFFFFFFu, v[i + 3]);
+    }
+    if (lane_id() == 0)
+#pragma unroll
+      for (int i = 0; i < 6; ++i) red[w][i] = v[i];
+    __syncthreads();
+    if (w == 0) {
+      const bool ok = lane_id() < (blockDim.x >> 5);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        int a = ok ? red[lane_id()][i] : INT_MAX;
+        int b = ok ? red[lane_id()][i + 3] : INT_MIN;
+        a = __reduce_min_sync(0xFFFFFFFFu, a);
+        b = __reduce_max_sync(0xFFFFFFFFu, b);
+        if (lane_id() == 0) {
+          atomicMin(&bbox[6 * t + i], a);
+          atomicMax(&bbox[6 * t + 3 + i], b);
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      mn[i] = INT_MAX;
+      mx[i] = INT_MIN;
+    }
+  };
+
+  for (uint64_t c = c0; c < c1; ++c) {
+    const uint32_t t = chunk_tile[c];
+    if (t != cur) {
+      if (cur != kNone) flush(cur);
+      cur = t;
+    }
+    const TileDesc& td = tiles[t];
+    const uint64_t first = (c - tile_chunk0[t]) << kChunkLog2;
+    const uint64_t end = min(first + kChunk, (uint64_t)td.n);
+    int4 p[kChunk / kBlock];
+#pragma unroll
+    for (int k = 0; k < (int)(kChunk / kBlock); ++k) {
+      const uint64_t i = first + threadIdx.x + (uint64_t)k * kBlock;
+      if (i < end) p[k] = ldg_stream(td.in + i);
+    }
+#pragma unroll
+    for (int k = 0; k < (int)(kChunk / kBlock); ++k) {
+      const uint64_t i = first + threadIdx.x + (uint64_t)k * kBlock;
+      if (i < end) {
+        mn[0] = min(mn[0], p[k].x);
+        mn[1] = min(mn[1], p[k].y);
+        mn[2] = min(mn[2], p[k].z);
+        mx[0] = max(mx[0], p[k].x);
+        mx[1] = max(mx[1], p[k].y);
+        mx[2] = max(mx[2], p[k].z);
+      }
+    }
+  }
+  if (cur != kNone) flush(cur);
+}
+
+cudaError_t launch_bbox(const TileDesc* tiles, const uint32_t* chunk_tile, uint64_t n_chunks,
+                        const uint64_t* tile_chunk0, int* bbox, int grid, cudaStream_t st) {
+  if (n_chunks == 0) return cudaSuccess;
+  grid = (int)umin64((uint64_t)grid, n_chunks);
+  k_bbox<<<grid, kBlock, 0, st>>>(tiles, chunk_tile, n_chunks, tile_chunk0, bbox);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------- counting
+// Section 3.1.1 (count per cell of the grid) and 3.1.5 (count again inside
+// the extended grids of overflowing cells): one histogram per source.
+
+__global__ void __launch_bounds__(kBlock) k_count(BuildArgs a, const uint32_t* __restrict__ chunk_src,
+                                                  const unsigned long long* __restrict__ n_chunks_p) {
+  __shared__ uint32_t hist[kSmemBins];
+  __shared__ SrcDesc s;
+  const uint64_t n_chunks = *n_chunks_p;
+  const uint64_t per = (n_chunks + gridDim.x - 1) / gridDim.x;
+  const uint64_t c0 = (uint64_t)blockIdx.x * per;
+  const uint64_t c1 = min(c0 + per, n_chunks);
+  uint32_t cur = kNone;
+  bool smem = false;
+  uint32_t nbins = 0;
+
+  auto flush = [&]() {
+    if (smem) {
+      uint32_t* dst = s.cnt + pyr_off(s.d);
+      for (uint32_t b = threadIdx.x; b < nbins; b += blockDim.x)
+        if (hist[b]) atomicAdd(dst + b, hist[b]);
+    }
+    __syncthreads();
+  };
+
+  for (uint64_t c = c0; c < c1; ++c) {
+    const uint32_t sid = chunk_src[c];
+    if (sid != cur) {
+      if (cur != kNone) flush();
+      if (threadIdx.x == 0) s = a.srcs[sid];
+      __syncthreads();
+      cur = sid;
+      nbins = 1u << (3 * s.d);
+      smem = nbins <= kSmemBins;
+      if (smem)
+        for (uint32_t b = threadIdx.x; b < nbins; b += blockDim.x) hist[b] = 0;
+      __syncthreads();
+    }
+    const TileDesc& td = a.tiles[s.tile];
+    const int4* pts = src_points(a, s, td);
+    const uint64_t first = (c - s.chunk0) << kChunkLog2;
+    const uint64_t end = min(first + kChunk, (uint64_t)s.n);
+    uint32_t* gcnt = s.cnt + pyr_off(s.d);
+    int4 p[kChunk / kBlock];
+#pragma unroll
+    for (int k = 0; k < (int)(kChunk / kBlock); ++k) {
+      const uint64_t i = first + threadIdx.x + (uint64_t)k * kBlock;
+      if (i < end) p[k] = ldg_stream(pts + i);
+    }
+#pragma unroll
+    for (int k = 0; k < (int)(kChunk / kBlock); ++k) {
+      const uint64_t i = first + threadIdx.x + (uint64_t)k * kBlock;
+      const bool v = i < end;
+      const uint32_t bin = v ? src_bin(p[k], s.min, s.log2size, s.d) : 0u;
+      if (smem) {
+        if (v) atomicAdd(&hist[bin], 1u);
+      } else {
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, v);
+        if (v) {
+          const unsigned peers = __match_any_sync(m, bin);
+          if ((int)lane_id() == __ffs(peers) - 1) atomicAdd(gcnt + bin, (uint32_t)__popc(peers));
+        }
+      }
+    }
+  }
+  if (cur != kNone) flush();
+}
+
+cudaError_t launch_count(const BuildArgs& a, const uint32_t* chunk_src, const unsigned long long* n_chunks,
+                         int grid, cudaStream_t st) {
+  k_count<<<grid, kBlock, 0, st>>>(a, chunk_src, n_chunks);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ pyramid: up-sweep
+// Per-level counts (the counting-grid pyramid of Section 3.1.2) from the
+// bottom histogram, 4 levels per CTA in shared memory.
+
+__global__ void __launch_bounds__(512) k_pyr_up(BuildArgs a, const PyrJob* __restrict__ jobs) {
+  __shared__ uint32_t sm[4096 + 512 + 64 + 8];
+  const PyrJob job = jobs[blockIdx.x];
+  const SrcDesc& s = a.srcs[job.src];
+  const uint32_t jb = job.lvl;
+  const uint32_t k = min(4u, jb);
+  const uint32_t nb = 1u << (3 * k);
+  const uint32_t* bottom = s.cnt + pyr_off(jb) + (uint64_t)job.block * nb;
+  for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) sm[i] = bottom[i];
+  __syncthreads();
+  uint32_t in_off = 0, n_in = nb, out_off = nb;
+  for (uint32_t l = 1; l <= k; ++l) {
+    const uint32_t n_out = n_in >> 3;
+    uint32_t* dst = s.cnt + pyr_off(jb - l) + (uint64_t)job.block * n_out;
+    for (uint32_t q = threadIdx.x; q < n_out; q += blockDim.x) {
+      uint32_t sum = 0;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) sum += sm[in_off + 8 * q + c];
+      sm[out_off + q] = sum;
+      dst[q] = sum;
+    }
+    __syncthreads();
+    in_off = out_off;
+    out_off += n_out;
+    n_in = n_out;
+  }
+}
+
+cudaError_t launch_pyr_up(const BuildArgs& a, const PyrJob* jobs, uint32_t n_jobs, cudaStream_t st) {
+  if (!n_jobs) return cudaSuccess;
+  k_pyr_up<<<n_jobs, 512, 0, st>>>(a, jobs);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------- pyramid: down-sweep
+// Exclusive-scan starts of every cell (the "target pointers" of Section
+// 3.1.3: where each node's points go), top-down 4 levels per CTA.  At the
+// bottom level the starts become the scatter cursors, and every cell with
+// more than T points that can still be split becomes a refinement grid
+// for the next round (Section 3.1.5, extended to any depth).
+
+__global__ void __launch_bounds__(512) k_pyr_down(BuildArgs a, const PyrJob* __restrict__ jobs,
+                                                  uint32_t next_base, uint32_t next_cap, uint32_t next_buf,
+                                                  DevCounters* __restrict__ ctr) {
+  __shared__ uint32_t cnt[8 + 64 + 512 + 4096];
+  __shared__ uint32_t sta[1 + 8 + 64 + 512 + 4096];
+  const PyrJob job = jobs[blockIdx.x];
+  const uint32_t sid = job.src;
+  const SrcDesc s = a.srcs[sid];
+  const uint32_t jt = job.lvl;
+  const uint32_t k = min(4u, s.d - jt);
+  // shared layout: level i (1..k) of the block subtree at offset (8^i - 8)/7
+  uint32_t lo[5], lsz[5];
+  lo[0] = 0;
+  lsz[0] = 1;
+  for (uint32_t i = 1; i <= 4; ++i) {
+    lsz[i] = 1u << (3 * i);
+    lo[i] = (uint32_t)((lsz[i] - 8) / 7);
+  }
+  for (uint32_t i = 1; i <= k; ++i) {
+    const uint32_t* src = s.cnt + pyr_off(jt + i) + (uint64_t)job.block * lsz[i];
+    for (uint32_t q = threadIdx.x; q < lsz[i]; q += blockDim.x) cnt[lo[i] + q] = src[q];
+  }
+  if (threadIdx.x == 0) {
+    uint32_t top;
+    if (jt == 0) {
+      top = s.pt_off;
+      s.start[0] = top;
+    } else {
+      top = s.start[pyr_off(jt) + job.block];
+    }
+    sta[0] = top;
+  }
+  __syncthreads();
+  if (k == 0) return;  // a one-cell grid (d == 0) never overflows: its start is set above
+  // sta layout: level 0 at [0], level i at 1 + lo[i]
+  for (uint32_t i = 1; i <= k; ++i) {
+    const uint32_t n_par = lsz[i - 1];
+    const uint32_t par_off = (i == 1) ? 0 : 1 + lo[i - 1];
+    uint32_t* gdst = s.start + pyr_off(jt + i) + (uint64_t)job.block * lsz[i];
+    for (uint32_t q = threadIdx.x; q < n_par; q += blockDim.x) {
+      uint32_t acc = sta[par_off + q];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        sta[1 + lo[i] + 8 * q + c] = acc;
+        gdst[8 * q + c] = acc;
+        acc += cnt[lo[i] + 8 * q + c];
+      }
+    }
+    __syncthreads();
+  }
+  if (jt + k != s.d) return;
+  // bottom level of the source: detect cells to refine
+  const uint32_t level_b = s.level + s.d;
+  const uint32_t log2_b = s.log2size - s.d;
+  if (!(level_b < a.max_depth && log2_b > 0)) return;
+  const uint32_t nbot = lsz[k];
+  for (uint32_t q = threadIdx.x; q < nbot; q += blockDim.x) {
+    const uint32_t n = cnt[lo[k] + q];
+    if (n <= a.T) continue;
+    const uint32_t c = job.block * nbot + q;  // Morton cell at the bottom level
+    const unsigned long long id = atomicAdd(&ctr->new_srcs, 1ull);
+    if (id >= next_cap) {
+      atomicOr(&ctr->error, kErrSrcCap);
+      continue;
+    }
+    atomicAdd(&ctr->new_points, (unsigned long long)n);
+    const uint32_t g = next_base + (uint32_t)id;
+    SrcDesc ns;
+    ns.cnt = ns.start = ns.map = ns.ovf = nullptr;
+    const uint32_t cx = compact3(c >> 2), cy = compact3(c >> 1), cz = compact3(c);
+    ns.min[0] = (int32_t)((uint32_t)s.min[0] + (cx << log2_b));
+    ns.min[1] = (int32_t)((uint32_t)s.min[1] + (cy << log2_b));
+    ns.min[2] = (int32_t)((uint32_t)s.min[2] + (cz << log2_b));
+    ns.tile = s.tile;
+    ns.level = level_b;
+    ns.log2size = log2_b;
+    ns.d = choose_seg_depth(n, a.T, level_b, log2_b, a.max_depth);
+    ns.buf = next_buf;
+    ns.pt_off = sta[1 + lo[k] + q];
+    ns.n = n;
+    ns.chunk0 = 0;
+    a.srcs[g] = ns;
+    s.map[c] = g;
+    atomicOr(&s.ovf[c >> 5], 1u << (c & 31));
+  }
+}
+
+cudaError_t launch_pyr_down(const BuildArgs& a, const PyrJob* jobs, uint32_t n_jobs, uint32_t next_base,
+                            uint32_t next_cap, uint32_t next_buf, DevCounters* ctr, cudaStream_t st) {
+  if (!n_jobs) return cudaSuccess;
+  k_pyr_down<<<n_jobs, 512, 0, st>>>(a, jobs, next_base, next_cap, next_buf, ctr);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------- scatter
+// Section 3.1.4 (insert): every point goes to its cell's cursor; points of
+// cells that will be refined go to the ping-pong buffer of the next round,
+// all others to their final place in the leaf-point array.  Cursors are
+// claimed with warp-aggregated atomics.
+
+__global__ void __launch_bounds__(kBlock) k_scatter(BuildArgs a, const uint32_t* __restrict__ chunk_src,
+                                                    const unsigned long long* __restrict__ n_chunks_p,
+                                                    uint32_t round) {
+  __shared__ SrcDesc s;
+  const uint64_t n_chunks = *n_chunks_p;
+  const uint64_t per = (n_chunks + gridDim.x - 1) / gridDim.x;
+  const uint64_t c0 = (uint64_t)blockIdx.x * per;
+  const uint64_t c1 = min(c0 + per, n_chunks);
+  uint32_t cur = kNone;
+  int4* ovf_dst = a.tmp[round & 1];
+  uint32_t* ovf_idx = a.tmp_idx[round & 1];
+  const uint32_t lane = lane_id();
+
+  for (uint64_t c = c0; c < c1; ++c) {
+    const uint32_t sid = chunk_src[c];
+    if (sid != cur) {
+      __syncthreads();
+      if (threadIdx.x == 0) s = a.srcs[sid];
+      __syncthreads();
+      cur = sid;
+    }
+    const TileDesc& td = a.tiles[s.tile];
+    const int4* pts = src_points(a, s, td);
+    const uint32_t* src_idx = s.buf == 0 ? nullptr : a.tmp_idx[s.buf - 1] + td.pt_base + s.pt_off;
+    const uint64_t first = (c - s.chunk0) << kChunkLog2;
+    const uint64_t end = min(first + kChunk, (uint64_t)s.n);
+    uint32_t* cursor = s.start + pyr_off(s.d);
+    int4 p[kChunk / kBlock];
+#pragma unroll
+    for (int k = 0; k < (int)(kChunk / kBlock); ++k) {
+      const uint64_t i = first + threadIdx.x + (uint64_t)k * kBlock;
+      if (i < end) p[k] = ldg_stream(pts + i);
+    }
+#pragma unroll
+    for (int k = 0; k < (int)(kChunk / kBlock); ++k) {
+      const uint64_t i = first + threadIdx.x + (uint64_t)k * kBlock;
+      const bool v = i < end;
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, v);
+      if (!v) continue;
+      const uint32_t bin = src_bin(p[k], s.min, s.log2size, s.d);
+      const unsigned peers = __match_any_sync(m, bin);
+      const int leader = __ffs(peers) - 1;
+      uint32_t base = 0;
+      if ((int)lane == leader) base = atomicAdd(cursor + bin, (uint32_t)__popc(peers));
+      base = __shfl_sync(peers, base, leader);
+      const uint32_t pos = base + __popc(peers & ((1u << lane) - 1u));
+      const bool ovf = (s.ovf[bin >> 5] >> (bin & 31)) & 1u;
+      const uint64_t dst = td.pt_base + pos;
+      if (ovf) {
+        __stcs(ovf_dst + dst, p[k]);
+      } else {
+        __stcs(a.out + dst, p[k]);
+      }
+      if (a.out_idx) {
+        const uint32_t idx = src_idx ? src_idx[i] : (uint32_t)i;
+        (ovf ? ovf_idx : a.out_idx)[dst] = idx;
+      }
+    }
+  }
+}
+
+cudaError_t launch_scatter(const BuildArgs& a, const uint32_t* chunk_src, const unsigned long long* n_chunks,
+                           uint32_t round, int grid, cudaStream_t st) {
+  k_scatter<<<grid, kBlock, 0, st>>>(a, chunk_src, n_chunks, round);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- node table
+// Breadth-first node list (Section 3.1.3 creates the node list from the
+// count pyramid): one CTA per tile walks the levels; a node is split iff it
+// holds more than T points, is above max_depth and larger than a unit cube.
+// Children are the non-empty octants in octant order, their counts read
+// from the pyramid of the grid that covers them (switching to the
+// refinement grid of a cell at the bottom of a grid).
+
+__global__ void __launch_bounds__(kBlock) k_nodes(BuildArgs a, lod_node_t* __restrict__ nodes,
+                                                  NodeAux* __restrict__ aux, uint32_t* __restrict__ lvl_start,
+                                                  uint32_t* __restrict__ n_nodes,
+                                                  unsigned long long* __restrict__ leaf_cap,
+                                                  DevCounters* __restrict__ ctr) {
+  __shared__ uint32_t warp_sum[32];
+  __shared__ uint32_t s_total;
+  __shared__ int s_fail;
+  const uint32_t t = blockIdx.x;
+  const TileDesc td = a.tiles[t];
+  lod_node_t* nd = nodes + td.node_base;
+  NodeAux* ax = aux + td.node_base;
+  uint32_t* ls = lvl_start + (uint64_t)t * (kMaxLevels + 1);
+  if (threadIdx.x == 0) {
+    lod_node_t r;
+    r.min[0] = td.min[0];
+    r.min[1] = td.min[1];
+    r.min[2] = td.min[2];
+    r.level = 0;
+    r.log2_size = (uint8_t)td.log2S;
+    r.child_mask = 0;
+    r.flags = 0;
+    r.parent = kNone;
+    r.first_child = kNone;
+    r.point_offset = 0;
+    r.point_count = td.n;
+    r.voxel_offset = 0;
+    r.voxel_count = 0;
+    r.reserved = 0;
+    nd[0] = r;
+    ax[0].src = t;
+    ax[0].j = 0;
+    ax[0].c = 0;
+    s_fail = 0;
+  }
+  __syncthreads();
+  uint32_t begin = 0, end = 1, level = 0;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  while (begin < end) {
+    if (threadIdx.x == 0) ls[level] = begin;
+    uint32_t next = end;
+    for (uint32_t chunk = begin; chunk < end; chunk += blockDim.x) {
+      const uint32_t i = chunk + threadIdx.x;
+      const bool valid = i < end;
+      uint32_t mask = 0, cc[8];
+      uint32_t sid = 0, j = 0, c = 0;
+      uint64_t cnt = 0;
+      uint32_t lvl = 0, lg = 0;
+      bool split = false;
+      if (valid) {
+        cnt = nd[i].point_count;
+        lvl = nd[i].level;
+        lg = nd[i].log2_size;
+        sid = ax[i].src;
+        j = ax[i].j;
+        c = ax[i].c;
+        split = cnt > a.T && lvl < a.max_depth && lg > 0;
+        if (split && j == a.srcs[sid].d) {
+          // bottom cell of its grid: continue in the cell's refinement grid
+          sid = a.srcs[sid].map[c];
+          j = 0;
+          c = 0;
+          ax[i].src = sid;
+          ax[i].j = 0;
+          ax[i].c = 0;
+        }
+        if (split) {
+          const uint32_t* ch = a.srcs[sid].cnt + pyr_off(j + 1) + 8ull * c;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            cc[k] = ch[k];
+            mask |= (cc[k] ? 1u : 0u) << k;
+          }
+        }
+      }
+      const uint32_t nch = __popc(mask);
+      // block exclusive scan of nch
+      uint32_t incl = nch;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if ((int)lane >= o) incl += y;
+      }
+      if (lane == 31) warp_sum[warp] = incl;
+      __syncthreads();
+      if (warp == 0) {
+        const uint32_t nw = blockDim.x >> 5;
+        uint32_t w = lane < nw ? warp_sum[lane] : 0;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+          if ((int)lane >= o) wi += y;
+        }
+        if (lane < nw) warp_sum[lane] = wi - w;
+        if (lane == nw - 1) s_total = wi;
+      }
+      __syncthreads();
+      const uint32_t pos = warp_sum[warp] + incl - nch;
+      const uint32_t total = s_total;
+      const bool fits = (uint64_t)next + total <= td.node_cap;
+      if (valid && fits) {
+        const SrcDesc& sd = a.srcs[sid];
+        const uint32_t st = sd.start[pyr_off(j) + c];
+        // bottom cells: the start array was advanced by the scatter (cursor)
+        nd[i].point_offset = (j < sd.d) ? st : st - (uint32_t)cnt;
+        nd[i].child_mask = (uint8_t)mask;
+        nd[i].flags = split ? 0 : (LOD_NODE_LEAF | (cnt > a.T ? LOD_NODE_OVERFULL : 0));
+        nd[i].first_child = split ? next + pos : kNone;
+        if (!split) atomicAdd(&leaf_cap[lvl], (unsigned long long)umin64(cnt, kOctCells));
+        if (split) {
+          const uint32_t half = lg - 1;
+          uint32_t r = 0;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            if (!(mask >> k & 1u)) continue;
+            const uint32_t id = next + pos + r++;
+            lod_node_t q;
+            q.min[0] = (int32_t)((uint32_t)nd[i].min[0] + ((uint32_t)((k >> 2) & 1) << half));
+            q.min[1] = (int32_t)((uint32_t)nd[i].min[1] + ((uint32_t)((k >> 1) & 1) << half));
+            q.min[2] = (int32_t)((uint32_t)nd[i].min[2] + ((uint32_t)(k & 1) << half));
+            q.level = (uint8_t)(lvl + 1);
+            q.log2_size = (uint8_t)half;
+            q.child_mask = 0;
+            q.flags = 0;
+            q.parent = i;
+            q.first_child = kNone;
+            q.point_offset = 0;
+            q.point_count = cc[k];
+            q.voxel_offset = 0;
+            q.voxel_count = 0;
+            q.reserved = 0;
+            nd[id] = q;
+            ax[id].src = sid;
+            ax[id].j = j + 1;
+            ax[id].c = 8 * c + k;
+            ax[id].occ = 0;
+          }
+        }
+      }
+      if (!fits && threadIdx.x == 0) s_fail = 1;
+      next += total;
+      __syncthreads();
+      if (s_fail) break;
+    }
+    if (s_fail) break;
+    begin = end;
+    end = next;
+    ++level;
+  }
+  if (threadIdx.x == 0) {
+    ls[level] = begin;
+    for (uint32_t l = level + 1; l <= kMaxLevels; ++l) ls[l] = begin;
+    n_nodes[t] = s_fail ? kNone : end;
+    if (s_fail) atomicOr(&ctr->error, kErrNodeCap);
+  }
+}
+
+cudaError_t launch_nodes(const BuildArgs& a, lod_node_t* nodes, NodeAux* aux, uint32_t* lvl_start,
+                         uint32_t* n_nodes, unsigned long long* leaf_cap, DevCounters* ctr, cudaStream_t st) {
+  k_nodes<<<a.n_tiles, kBlock, 0, st>>>(a, nodes, aux, lvl_start, n_nodes, leaf_cap, ctr);
+  return cudaGetLastError();
+}
+
+}  // namespace lodk

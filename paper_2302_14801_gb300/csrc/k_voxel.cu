@@ -1,0 +1,470 @@
+// Bottom-up voxel sampling (Section 3.2 of the paper).
+//
+// The paper processes one node per workgroup with one 128^3 grid per SM in
+// global memory (8 MB / 33 MB per workgroup, Sections 3.2.2-3.2.3).  Here a
+// CTA handles one (parent, child octant) pair: the child's samples (its
+// leaf points, or the voxels the child itself received one level below)
+// all fall into one 64^3 octant of the parent's 128^3 grid (the observation
+// of Section 3.2.1), and their cells are accumulated in a ~200 KB
+// shared-memory open-addressing hash table instead of a dense grid.  An
+// octant whose occupied cells exceed the table is processed in several
+// hash-partitioned passes.  Colour sums are exact integers (32-bit lanes
+// while they provably cannot overflow, 64-bit otherwise); the pick keeps the
+// minimal splitmix64(input index) with a 64-bit atomicMin.
+//
+// Every octant's voxels go to a staging area; a level scan then assigns
+// each parent one contiguous voxel range (children are consecutive in node
+// order), and the next level up copies the records to that range while it
+// reads them (so each record is read once).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace lodk {
+
+namespace {
+
+constexpr int kSmemBytes = 200 * 1024;
+constexpr uint32_t kHn = kSmemBytes / 20;  // filtered, 32-bit sums: key + 2 x u64
+constexpr uint32_t kHw = kSmemBytes / 32;  // filtered, 64-bit sums: key + 3 x u64 + count
+constexpr uint32_t kHp = kSmemBytes / 16;  // pick: key + u64 hash + count
+constexpr uint64_t kNarrowMaxSamples = 0xFFFFFFFFull / 255;  // 32-bit channel sums cannot overflow
+constexpr uint64_t kMask40 = (1ull << 40) - 1;
+
+__device__ __forceinline__ uint32_t table_limit(uint32_t H) { return min(H / 4 * 3, H - kBlock - 1); }
+
+__device__ __forceinline__ uint32_t part_of(uint32_t key1, uint32_t mlog) {
+  return mlog ? (key1 * 0x85EBCA6Bu) >> (32 - mlog) : 0u;
+}
+
+// Find the slot of key1 (= local cell + 1), inserting it if absent.
+// Returns -1 when the table has reached its fill limit.
+__device__ __forceinline__ int find_or_insert(uint32_t* keys, uint32_t H, uint32_t key1, uint32_t* used,
+                                              uint32_t limit) {
+  uint32_t slot = __umulhi(key1 * 0x9E3779B1u, H);
+  while (true) {
+    const uint32_t k = ((volatile uint32_t*)keys)[slot];
+    if (k == key1) return (int)slot;
+    if (k == 0u) {
+      if (*((volatile uint32_t*)used) >= limit) return -1;
+      const uint32_t old = atomicCAS(&keys[slot], 0u, key1);
+      if (old == 0u) {
+        atomicAdd(used, 1u);
+        return (int)slot;
+      }
+      if (old == key1) return (int)slot;
+    }
+    slot = (slot + 1 == H) ? 0u : slot + 1;
+  }
+}
+
+struct ItemInfo {
+  uint32_t tile;
+  uint64_t g;        // absolute node id of the item (the child)
+  uint32_t kx, ky, kz;
+  uint32_t Lp;       // parent log2 edge
+  int32_t pmin[3];
+  bool leaf;
+  uint64_t n;        // samples
+};
+
+__device__ __forceinline__ uint32_t find_tile(const uint32_t* prefix, uint32_t n_tiles, uint32_t it) {
+  uint32_t lo = 0, hi = n_tiles;  // largest t with prefix[t] <= it
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (prefix[mid] <= it) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint32_t point_key1(const int4& q, const ItemInfo& I) {
+  const uint32_t qx = grid_coord((uint32_t)q.x - (uint32_t)I.pmin[0], I.Lp) & 63u;
+  const uint32_t qy = grid_coord((uint32_t)q.y - (uint32_t)I.pmin[1], I.Lp) & 63u;
+  const uint32_t qz = grid_coord((uint32_t)q.z - (uint32_t)I.pmin[2], I.Lp) & 63u;
+  return (qx | (qy << 6) | (qz << 12)) + 1u;
+}
+
+__device__ __forceinline__ uint32_t voxel_key1(uint32_t cell) {
+  const uint32_t x = (cell & 127u) >> 1, y = ((cell >> 7) & 127u) >> 1, z = (cell >> 14) >> 1;
+  return (x | (y << 6) | (z << 12)) + 1u;
+}
+
+__device__ __forceinline__ uint32_t key_to_cell(uint32_t key1, const ItemInfo& I) {
+  const uint32_t l = key1 - 1u;
+  return ((I.kx << 6) | (l & 63u)) | (((I.ky << 6) | ((l >> 6) & 63u)) << 7) |
+         (((I.kz << 6) | (l >> 12)) << 14);
+}
+
+__device__ __forceinline__ uint32_t mean_rgba(uint64_t r, uint64_t g, uint64_t b, uint64_t n) {
+  const uint64_t h = n >> 1;
+  return (uint32_t)((r + h) / n) | ((uint32_t)((g + h) / n) << 8) | ((uint32_t)((b + h) / n) << 16) |
+         0xFF000000u;
+}
+
+}  // namespace
+
+int vox_smem_bytes() { return kSmemBytes; }
+
+// One CTA per item (a child node c of an inner node p at level v.level).
+template <int MODE>
+__global__ void __launch_bounds__(kBlock, 1) k_vox(BuildArgs a, VoxLevel v, DevCounters* __restrict__ ctr) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t s_used, s_out, s_fail;
+  __shared__ unsigned long long s_stage;
+  __shared__ ItemInfo I;
+
+  if (threadIdx.x == 0) {
+    const uint32_t it = blockIdx.x;
+    const uint32_t t = find_tile(v.item_prefix, a.n_tiles, it);
+    const uint32_t* ls = v.lvl_start + (uint64_t)t * (kMaxLevels + 1);
+    const TileDesc& td = a.tiles[t];
+    const uint64_t g = td.node_base + ls[v.level + 1] + (it - v.item_prefix[t]);
+    const lod_node_t c = v.nodes[g];
+    const lod_node_t p = v.nodes[td.node_base + c.parent];
+    I.tile = t;
+    I.g = g;
+    I.Lp = p.log2_size;
+    I.pmin[0] = p.min[0];
+    I.pmin[1] = p.min[1];
+    I.pmin[2] = p.min[2];
+    I.kx = c.min[0] != p.min[0];
+    I.ky = c.min[1] != p.min[1];
+    I.kz = c.min[2] != p.min[2];
+    I.leaf = (c.flags & LOD_NODE_LEAF) != 0;
+    I.n = I.leaf ? c.point_count : c.voxel_count;
+    s_stage = ~0ull;
+  }
+  __syncthreads();
+  const TileDesc& td = a.tiles[I.tile];
+  const lod_node_t& c = v.nodes[I.g];
+  const bool narrow = MODE == LOD_FILTER && I.leaf && I.n <= kNarrowMaxSamples;
+  const uint32_t H = MODE == LOD_PICK ? kHp : (narrow ? kHn : kHw);
+  const uint32_t limit = table_limit(H);
+  // shared-memory carve-up (u64 arrays first)
+  unsigned long long* A0 = reinterpret_cast<unsigned long long*>(smem);
+  unsigned long long* A1 = A0 + H;
+  unsigned long long* A2 = A1 + H;  // wide only
+  uint32_t* keys;
+  uint32_t* cnt32;
+  if (MODE == LOD_PICK) {
+    keys = reinterpret_cast<uint32_t*>(A0 + H);
+    cnt32 = keys + H;
+  } else if (narrow) {
+    keys = reinterpret_cast<uint32_t*>(A0 + 2 * H);
+    cnt32 = nullptr;
+  } else {
+    keys = reinterpret_cast<uint32_t*>(A0 + 3 * H);
+    cnt32 = keys + H;
+  }
+
+  const uint64_t cap = umin64(I.n, kOctCells);
+  uint32_t mlog = 0;
+  uint64_t out_total = 0;
+  const int4* pts = a.out + td.pt_base + c.point_offset;
+  const uint32_t* pidx = (MODE == LOD_PICK) ? a.out_idx + td.pt_base + c.point_offset : nullptr;
+  const uint32_t nch = __popc(c.child_mask);
+  const uint64_t fc = td.node_base + (c.first_child == kNone ? 0 : c.first_child);
+
+  for (;;) {  // attempts with more partitions after an overflow
+    const uint32_t P = 1u << mlog;
+    out_total = 0;
+    bool failed = false;
+    if (mlog > 0 && threadIdx.x == 0 && s_stage == ~0ull) {
+      s_stage = atomicAdd(v.stage_used, (unsigned long long)cap);
+      if (s_stage + cap > v.stage_cap) atomicOr(&ctr->error, kErrStageCap);
+    }
+    for (uint32_t part = 0; part < P; ++part) {
+      for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) {
+        keys[i] = 0u;
+        if (MODE == LOD_PICK) {
+          A0[i] = ~0ull;
+          cnt32[i] = 0u;
+        } else {
+          A0[i] = 0ull;
+          A1[i] = 0ull;
+          if (!narrow) {
+            A2[i] = 0ull;
+            cnt32[i] = 0u;
+          }
+        }
+      }
+      if (threadIdx.x == 0) {
+        s_used = 0;
+        s_fail = 0;
+      }
+      __syncthreads();
+
+      if (I.leaf) {
+        const uint64_t n = I.n;
+        for (uint64_t base = 0; base < n; base += 4ull * blockDim.x) {
+          if (*((volatile uint32_t*)&s_fail)) break;
+          int4 q[4];
+          uint32_t ix[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const uint64_t i = base + threadIdx.x + (uint64_t)u * blockDim.x;
+            if (i < n) {
+              q[u] = __ldcs(pts + i);
+              if (MODE == LOD_PICK) ix[u] = __ldcs(pidx + i);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const uint64_t i = base + threadIdx.x + (uint64_t)u * blockDim.x;
+            if (i >= n) continue;
+            const uint32_t key1 = point_key1(q[u], I);
+            if (part_of(key1, mlog) != part) continue;
+            const int slot = find_or_insert(keys, H, key1, &s_used, limit);
+            if (slot < 0) {
+              s_fail = 1;
+              continue;
+            }
+            const uint32_t rgba = (uint32_t)q[u].w;
+            const uint64_t r = rgba & 255u, g = (rgba >> 8) & 255u, b = (rgba >> 16) & 255u;
+            if (MODE == LOD_PICK) {
+              atomicMin(&A0[slot], splitmix64(ix[u]));
+              atomicAdd(&cnt32[slot], 1u);
+            } else if (narrow) {
+              atomicAdd(&A0[slot], r | (g << 32));
+              atomicAdd(&A1[slot], b | (1ull << 32));
+            } else {
+              atomicAdd(&A0[slot], r);
+              atomicAdd(&A1[slot], g);
+              atomicAdd(&A2[slot], b);
+              atomicAdd(&cnt32[slot], 1u);
+            }
+          }
+        }
+      } else {
+        // inner child: its voxels are the staged records of its own children
+        for (uint32_t r = 0; r < nch; ++r) {
+          const NodeAux& ca = v.aux[fc + r];
+          const int4* rec = v.stage_in + ca.stage;
+          const ulonglong2* sums = (MODE == LOD_FILTER) ? v.stage_in_sum + ca.stage : nullptr;
+          int4* dst = v.dense + ca.dense;
+          const uint32_t m = ca.occ;
+          for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+            if (*((volatile uint32_t*)&s_fail)) break;
+            const int4 vr = rec[i];
+            if (part == 0) dst[i] = vr;  // publish the child's voxel (idempotent)
+            const uint32_t key1 = voxel_key1((uint32_t)vr.x);
+            if (part_of(key1, mlog) != part) continue;
+            const int slot = find_or_insert(keys, H, key1, &s_used, limit);
+            if (slot < 0) {
+              s_fail = 1;
+              continue;
+            }
+            if (MODE == LOD_PICK) {
+              atomicMin(&A0[slot], splitmix64((uint32_t)vr.w));
+              atomicAdd(&cnt32[slot], (uint32_t)vr.z);
+            } else {
+              const ulonglong2 sm = sums[i];
+              atomicAdd(&A0[slot], sm.x & kMask40);
+              atomicAdd(&A1[slot], (sm.x >> 40) | ((sm.y & 0xFFFFull) << 24));
+              atomicAdd(&A2[slot], sm.y >> 16);
+              atomicAdd(&cnt32[slot], (uint32_t)vr.z);
+            }
+          }
+        }
+      }
+      __syncthreads();
+      if (s_fail) {
+        failed = true;
+        break;
+      }
+      // extract this partition's occupied cells into staging
+      const uint32_t used = s_used;
+      if (mlog == 0 && threadIdx.x == 0) {
+        s_stage = atomicAdd(v.stage_used, (unsigned long long)used);
+        if (s_stage + used > v.stage_cap) atomicOr(&ctr->error, kErrStageCap);
+      }
+      if (threadIdx.x == 0) s_out = 0;
+      __syncthreads();
+      const bool room = s_stage + out_total + used <= v.stage_cap;
+      const uint32_t lane = threadIdx.x & 31u;
+      for (uint32_t i0 = 0; i0 < H; i0 += blockDim.x) {
+        const uint32_t i = i0 + threadIdx.x;
+        const uint32_t key1 = i < H ? keys[i] : 0u;
+        const bool occ = key1 != 0u;
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, occ);
+        uint32_t wbase = 0;
+        if (lane == 0 && bal) wbase = atomicAdd(&s_out, (uint32_t)__popc(bal));
+        wbase = __shfl_sync(0xFFFFFFFFu, wbase, 0);
+        if (!occ || !room) continue;
+        const uint64_t o = s_stage + out_total + wbase + __popc(bal & ((1u << lane) - 1u));
+        const uint32_t cell = key_to_cell(key1, I);
+        int4 rec;
+        rec.x = (int)cell;
+        if (MODE == LOD_PICK) {
+          const uint32_t best = (uint32_t)splitmix64_inverse(A0[i]);
+          rec.y = (int)__ldg(reinterpret_cast<const uint32_t*>(td.in) + 4ull * best + 3);
+          rec.z = (int)cnt32[i];
+          rec.w = (int)best;
+        } else {
+          uint64_t sr, sg, sb, n;
+          if (narrow) {
+            sr = A0[i] & 0xFFFFFFFFull;
+            sg = A0[i] >> 32;
+            sb = A1[i] & 0xFFFFFFFFull;
+            n = A1[i] >> 32;
+          } else {
+            sr = A0[i];
+            sg = A1[i];
+            sb = A2[i];
+            n = cnt32[i];
+          }
+          rec.y = (int)mean_rgba(sr, sg, sb, n);
+          rec.z = (int)n;
+          rec.w = (int)kNone;
+          ulonglong2 sm;
+          sm.x = sr | (sg << 40);
+          sm.y = (sg >> 24) | (sb << 16);
+          v.stage_out_sum[o] = sm;
+        }
+        v.stage_out[o] = rec;
+      }
+      out_total += used;
+      __syncthreads();
+    }
+    if (!failed) break;
+    // more partitions: first try two, then enough for the worst case
+    const uint32_t need = (uint32_t)((cap + limit - 1) / limit);
+    uint32_t bound = 0;
+    while ((1u << bound) < need) ++bound;
+    mlog = mlog == 0 ? 1u : max(mlog + 1, bound);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    v.aux[I.g].stage = s_stage == ~0ull ? 0ull : s_stage;
+    v.aux[I.g].occ = (uint32_t)out_total;
+  }
+}
+
+cudaError_t launch_vox(const BuildArgs& a, const VoxLevel& v, DevCounters* ctr, cudaStream_t st) {
+  if (!v.n_items) return cudaSuccess;
+  if (a.mode == LOD_PICK) {
+    static bool once = [] {
+      cudaFuncSetAttribute(k_vox<LOD_PICK>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+      return true;
+    }();
+    (void)once;
+    k_vox<LOD_PICK><<<v.n_items, kBlock, kSmemBytes, st>>>(a, v, ctr);
+  } else {
+    static bool once = [] {
+      cudaFuncSetAttribute(k_vox<LOD_FILTER>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+      return true;
+    }();
+    (void)once;
+    k_vox<LOD_FILTER><<<v.n_items, kBlock, kSmemBytes, st>>>(a, v, ctr);
+  }
+  return cudaGetLastError();
+}
+
+// Assign every item its place in the level's contiguous voxel block
+// (exclusive scan of the occupied counts in node order), then give every
+// parent the range of its children's items.
+__global__ void __launch_bounds__(kBlock) k_level_scan(BuildArgs a, VoxLevel v, const uint32_t* __restrict__ parent_prefix,
+                                                       uint32_t n_parents, uint64_t level_base,
+                                                       unsigned long long* __restrict__ tile_voxels,
+                                                       DevCounters* __restrict__ ctr) {
+  __shared__ unsigned long long warp_sum[32];
+  __shared__ unsigned long long s_carry;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (uint32_t chunk = 0; chunk < v.n_items; chunk += blockDim.x) {
+    const uint32_t it = chunk + threadIdx.x;
+    uint64_t g = 0;
+    unsigned long long x = 0;
+    if (it < v.n_items) {
+      const uint32_t t = find_tile(v.item_prefix, a.n_tiles, it);
+      g = a.tiles[t].node_base + v.lvl_start[(uint64_t)t * (kMaxLevels + 1) + v.level + 1] + (it - v.item_prefix[t]);
+      x = v.aux[g].occ;
+    }
+    unsigned long long incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if ((int)lane >= o) incl += y;
+    }
+    if (lane == 31) warp_sum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t nw = blockDim.x >> 5;
+      unsigned long long w = lane < nw ? warp_sum[lane] : 0ull;
+      unsigned long long wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+        if ((int)lane >= o) wi += y;
+      }
+      if (lane < nw) warp_sum[lane] = wi - w;
+    }
+    __syncthreads();
+    const unsigned long long excl = s_carry + warp_sum[warp] + incl - x;
+    if (it < v.n_items) v.aux[g].dense = level_base + excl;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) s_carry = excl + x;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) ctr->level_voxels = s_carry;
+  __syncthreads();
+  for (uint32_t ip = threadIdx.x; ip < n_parents; ip += blockDim.x) {
+    const uint32_t t = find_tile(parent_prefix, a.n_tiles, ip);
+    const TileDesc& td = a.tiles[t];
+    const uint64_t pg = td.node_base + v.lvl_start[(uint64_t)t * (kMaxLevels + 1) + v.level] + (ip - parent_prefix[t]);
+    lod_node_t& p = v.nodes[pg];
+    if (p.flags & LOD_NODE_LEAF) continue;
+    const uint64_t f = td.node_base + p.first_child;
+    const uint64_t l = f + __popc(p.child_mask) - 1;
+    const uint64_t off = v.aux[f].dense;
+    const uint64_t cnt = v.aux[l].dense + v.aux[l].occ - off;
+    p.voxel_offset = off;
+    p.voxel_count = (uint32_t)cnt;
+    atomicAdd(&ctr->next_cap, (unsigned long long)umin64(cnt, kOctCells));
+    atomicAdd(&tile_voxels[t], (unsigned long long)cnt);
+  }
+}
+
+cudaError_t launch_level_scan(const BuildArgs& a, const VoxLevel& v, const uint32_t* parent_prefix,
+                              uint32_t n_parents, uint64_t level_base, unsigned long long* tile_voxels,
+                              DevCounters* ctr, cudaStream_t st) {
+  k_level_scan<<<1, kBlock, 0, st>>>(a, v, parent_prefix, n_parents, level_base, tile_voxels, ctr);
+  return cudaGetLastError();
+}
+
+// Publish the staged voxels of the items of the topmost processed level
+// (their parents, the roots, have no parent pass that would copy them).
+__global__ void __launch_bounds__(256) k_copy_items(BuildArgs a, VoxLevel v) {
+  const uint32_t it = blockIdx.x;
+  const uint32_t t = find_tile(v.item_prefix, a.n_tiles, it);
+  const uint64_t g = a.tiles[t].node_base + v.lvl_start[(uint64_t)t * (kMaxLevels + 1) + v.level + 1] +
+                     (it - v.item_prefix[t]);
+  const NodeAux ca = v.aux[g];
+  for (uint32_t i = threadIdx.x; i < ca.occ; i += blockDim.x) v.dense[ca.dense + i] = v.stage_out[ca.stage + i];
+}
+
+cudaError_t launch_copy_items(const BuildArgs& a, const VoxLevel& v, cudaStream_t st) {
+  if (!v.n_items) return cudaSuccess;
+  k_copy_items<<<v.n_items, 256, 0, st>>>(a, v);
+  return cudaGetLastError();
+}
+
+// Gather each node's voxels to a new offset (compact per-result copies).
+__global__ void __launch_bounds__(256) k_gather_voxels(const lod_node_t* __restrict__ nodes,
+                                                       const uint64_t* __restrict__ new_off,
+                                                       const int4* __restrict__ src, int4* __restrict__ dst) {
+  const lod_node_t nd = nodes[blockIdx.x];
+  const int4* s = src + nd.voxel_offset;
+  int4* d = dst + new_off[blockIdx.x];
+  for (uint32_t i = threadIdx.x; i < nd.voxel_count; i += blockDim.x) d[i] = s[i];
+}
+
+cudaError_t launch_gather_voxels(const lod_node_t* nodes, uint32_t n_nodes, const uint64_t* new_off,
+                                 const int4* src, int4* dst, cudaStream_t st) {
+  if (!n_nodes) return cudaSuccess;
+  k_gather_voxels<<<n_nodes, 256, 0, st>>>(nodes, new_off, src, dst);
+  return cudaGetLastError();
+}
+
+}  // namespace lodk

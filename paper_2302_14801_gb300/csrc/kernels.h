@@ -1,0 +1,53 @@
+// Host-side launch wrappers of the LOD kernels (internal).
+#pragma once
+
+#include "common.cuh"
+
+namespace lodk {
+
+struct PyrJob {
+  uint32_t src;    // source id
+  uint32_t lvl;    // up: bottom level of the block; down: top level of the block
+  uint32_t block;  // block index (cell index at the block's top level)
+};
+
+// ----- split (Section 3.1) -----
+cudaError_t launch_bbox(const TileDesc* tiles, const uint32_t* chunk_tile, uint64_t n_chunks,
+                        const uint64_t* tile_chunk0, int* bbox, int grid, cudaStream_t st);
+cudaError_t launch_count(const BuildArgs& a, const uint32_t* chunk_src, const unsigned long long* n_chunks,
+                         int grid, cudaStream_t st);
+cudaError_t launch_pyr_up(const BuildArgs& a, const PyrJob* jobs, uint32_t n_jobs, cudaStream_t st);
+cudaError_t launch_pyr_down(const BuildArgs& a, const PyrJob* jobs, uint32_t n_jobs, uint32_t next_base,
+                            uint32_t next_cap, uint32_t next_buf, DevCounters* ctr, cudaStream_t st);
+cudaError_t launch_scatter(const BuildArgs& a, const uint32_t* chunk_src, const unsigned long long* n_chunks,
+                           uint32_t round, int grid, cudaStream_t st);
+cudaError_t launch_nodes(const BuildArgs& a, lod_node_t* nodes, NodeAux* aux, uint32_t* lvl_start,
+                         uint32_t* n_nodes, unsigned long long* leaf_cap, DevCounters* ctr, cudaStream_t st);
+
+// ----- voxel sampling (Section 3.2) -----
+struct VoxLevel {
+  uint32_t level;              // parent level l; items are the nodes at level l + 1
+  uint32_t n_items;
+  const uint32_t* item_prefix; // n_tiles + 1 prefix of items per tile
+  const uint32_t* lvl_start;   // n_tiles x (kMaxLevels + 1)
+  lod_node_t* nodes;
+  NodeAux* aux;
+  int4* stage_out;             // staging records written by this level
+  ulonglong2* stage_out_sum;   // filtered mode: exact sums, parallel to stage_out
+  uint64_t stage_cap;
+  const int4* stage_in;        // staging of the level below (items at level l + 2)
+  const ulonglong2* stage_in_sum;
+  int4* dense;                 // public voxel array
+  unsigned long long* stage_used;
+};
+cudaError_t launch_vox(const BuildArgs& a, const VoxLevel& v, DevCounters* ctr, cudaStream_t st);
+cudaError_t launch_level_scan(const BuildArgs& a, const VoxLevel& v, const uint32_t* parent_prefix,
+                              uint32_t n_parents, uint64_t level_base, unsigned long long* tile_voxels,
+                              DevCounters* ctr, cudaStream_t st);
+cudaError_t launch_copy_items(const BuildArgs& a, const VoxLevel& v, cudaStream_t st);
+cudaError_t launch_gather_voxels(const lod_node_t* nodes, uint32_t n_nodes, const uint64_t* new_off,
+                                 const int4* src, int4* dst, cudaStream_t st);
+
+int vox_smem_bytes();
+
+}  // namespace lodk

@@ -1,0 +1,65 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every
+entry point declared in include/lod.h; host-side argument validation works
+without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lodmod():
+    from paper_2302_14801_gb300 import _build_ext
+    _build_ext.build()
+    from paper_2302_14801_gb300 import lod
+    return lod
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "lod.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lod_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("lod_build", "lod_build_batched", "lod_submit", "lod_poll", "lod_free", "lod_result_view"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lodmod):
+    lib = ctypes.CDLL(lodmod.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert sorted(lodmod.EXPORTED) == declared_functions()
+
+
+def test_struct_layouts(lodmod):
+    assert ctypes.sizeof(lodmod.Node) == 56
+    assert ctypes.sizeof(lodmod.Params) == 16
+    assert ctypes.sizeof(lodmod.View) == 64
+
+
+def test_params_defaults_and_error_strings(lodmod):
+    p = lodmod.Params()
+    assert lodmod.lib().lod_params_init(ctypes.byref(p)) == 0
+    assert (p.leaf_threshold, p.mode, p.max_depth, p.flags) == (50000, 0, 21, 0)
+    assert lodmod.error_string(0) == "ok"
+    assert "budget" in lodmod.error_string(lodmod.LOD_ERR_BUDGET)
+
+
+def test_invalid_arguments_rejected_on_host(lodmod):
+    L = lodmod.lib()
+    h = ctypes.c_void_p()
+    p = lodmod.make_params()
+    assert L.lod_build(None, 10, ctypes.byref(p), None, None) == lodmod.LOD_ERR_INVALID_ARG
+    assert L.lod_build_batched(None, None, 0, None, None, None) == lodmod.LOD_ERR_INVALID_ARG
+    bad = lodmod.make_params(leaf_threshold=0)
+    assert L.lod_build_from_host(None, 0, ctypes.byref(bad), None, ctypes.byref(h)) == lodmod.LOD_ERR_INVALID_ARG
+    assert L.lod_result_view(None, None) == lodmod.LOD_ERR_INVALID_ARG
+    L.lod_free(None)  # no-op
+    cfg = lodmod.ServerConfig(0, 1, 0)
+    assert L.lod_server_create(ctypes.byref(cfg), ctypes.byref(h)) == lodmod.LOD_ERR_INVALID_ARG

@@ -1,0 +1,215 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle,
+bit-exact, on seeded synthetic inputs spanning many chunks and ragged
+tails, the edge cases of the method, and the batched / host-input /
+serving entry points."""
+import numpy as np
+import pytest
+
+import oracle
+from bruteforce import check
+from compare import compare
+from paper_2302_14801_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lod():
+    import torch
+    from paper_2302_14801_gb300 import _build_ext
+    _build_ext.build()
+    from paper_2302_14801_gb300 import lod as m
+    torch.cuda.set_device(0)
+    return m
+
+
+def gpu_build(lod, pts, T, mode, max_depth=21, keep_index=False):
+    import torch
+    d = torch.from_numpy(np.ascontiguousarray(pts, dtype=np.int32)).cuda()
+    r = lod.build(d, T, mode, max_depth, keep_index)
+    got = r.to_host()
+    r.free()
+    return got
+
+
+def parity(lod, pts, T, mode, max_depth=21, keep_index=False):
+    got = gpu_build(lod, pts, T, mode, max_depth, keep_index)
+    want = oracle.build(pts, T, mode, max_depth)
+    compare(got, want, inp=pts)
+    return got
+
+
+def P(rows):
+    a = np.asarray(rows, dtype=np.int64).reshape(-1, 6)
+    out = np.empty((len(a), 4), np.int32)
+    out[:, :3] = a[:, :3]
+    out[:, 3] = synth.pack_rgba(a[:, 3], a[:, 4], a[:, 5])
+    return out
+
+
+# ------------------------------------------------------------- edge cases
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_empty(lod, mode):
+    got = gpu_build(lod, np.zeros((0, 4), np.int32), 10, mode)
+    assert len(got["level"]) == 1 and got["flags"][0] == 1 and got["point_count"][0] == 0
+    assert list(got["min"][0]) == [0, 0, 0] and got["log2_size"][0] == 0
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_single_point_and_leaf_root(lod, mode):
+    parity(lod, P([(5, -7, 9, 1, 2, 3)]), 1, mode)
+    parity(lod, synth.sphere(3000, seed=3), 3000, mode)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_identical_points_and_chains(lod, mode):
+    parity(lod, P([(5, 5, 5, 1, 2, 3)] * 1000), 3, mode)
+    pts = P([(0, 0, 0, 1, 1, 1)] * 9 + [(1023, 0, 0, 2, 2, 2)])
+    for md in (21, 5, 1, 0):
+        parity(lod, pts, 3, mode, md)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_full_int32_extent(lod, mode):
+    rng = np.random.default_rng(5)
+    xyz = rng.integers(-(2**31), 2**31, size=(5000, 3))
+    xyz[0] = [-(2**31)] * 3
+    xyz[1] = [2**31 - 1] * 3
+    pts = np.empty((5000, 4), np.int32)
+    pts[:, :3] = xyz
+    pts[:, 3] = rng.integers(-(2**31), 2**31, size=5000)
+    got = parity(lod, pts, 40, mode)
+    assert got["log2_size"][0] == 32
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_lattices(lod, mode):
+    g = np.stack(np.meshgrid(np.arange(8), np.arange(8), np.arange(8), indexing="ij"), -1).reshape(-1, 3)
+    rows = np.concatenate([g, np.full((512, 3), 9)], axis=1)
+    for T in (7, 8, 64):
+        parity(lod, P(rows), T, mode)
+    parity(lod, P([(i, 0, 0, i % 256, 0, 0) for i in range(1024)]), 100, mode)
+
+
+@pytest.mark.parametrize("n", [4095, 4096, 4097, 3 * 4096 + 1])
+def test_chunk_boundaries(lod, n):
+    pts = synth.sphere(n, seed=n)
+    parity(lod, pts, 200, 0)
+    parity(lod, pts, 200, 1)
+
+
+def _random_cloud(rng, n, spread_log2):
+    kind = rng.integers(0, 3)
+    if kind == 0:
+        xyz = rng.integers(-(2**spread_log2), 2**spread_log2, size=(n, 3))
+    elif kind == 1:
+        c = rng.integers(0, 2**spread_log2, size=(4, 3))
+        xyz = c[rng.integers(0, 4, size=n)] + rng.integers(0, 3, size=(n, 3))
+    else:
+        xyz = rng.integers(0, 2**spread_log2, size=(n, 3))
+        xyz[:, 2] = 77
+    out = np.empty((n, 4), np.int32)
+    out[:, :3] = xyz
+    out[:, 3] = rng.integers(-(2**31), 2**31, size=n)
+    return out
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_random_tiny_deep_trees(lod, seed):
+    rng = np.random.default_rng(7000 + seed)
+    n = int(rng.integers(1, 2000))
+    T = int(rng.integers(1, 17))
+    max_depth = int(rng.choice([21, 3, 1, 6, 32]))
+    pts = _random_cloud(rng, n, int(rng.integers(1, 31)))
+    for mode in (0, 1):
+        got = parity(lod, pts, T, mode, max_depth)
+        if n <= 600:
+            check(pts, got, T, mode, max_depth)
+
+
+# --------------------------------------------------- workload-shaped inputs
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_sphere_1m_default_T(lod, mode):
+    parity(lod, synth.sphere(1_000_000, seed=1), 50000, mode)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("T", [50000, 3000])
+def test_aerial_2m(lod, mode, T):
+    parity(lod, synth.aerial(2_000_000, seed=2, n_buildings=80), T, mode)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("T", [50000, 2000])
+def test_indoor_dense_clusters_refinement(lod, mode, T):
+    # log-normal densities put millions of points into single first-grid
+    # cells: exercises several refinement rounds
+    parity(lod, synth.indoor(3_000_000, seed=3, n_prims=256), T, mode)
+
+
+def test_keep_index_filtered(lod):
+    pts = synth.sphere(200_000, seed=12)
+    got = gpu_build(lod, pts, 5000, 0, keep_index=True)
+    assert got["index"] is not None
+    want = oracle.build(pts, 5000, 0)
+    compare(got, want, inp=pts)
+
+
+# ----------------------------------------------------------- other entry points
+
+def test_build_from_host(lod):
+    pts = synth.aerial(300_000, seed=21, n_buildings=10)
+    r = lod.build_from_host(pts, 4000, 1)
+    got = r.to_host()
+    r.free()
+    compare(got, oracle.build(pts, 4000, 1, 21), inp=pts)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batched_equals_single(lod, mode):
+    import torch
+    sizes = [0, 1, 17, 4096, 4097, 30_000, 250_000, 1_000_000, 60_000, 5]
+    tiles = [synth.sphere_tile(int(n), seed=100 + i) for i, n in enumerate(sizes)]
+    dts = [torch.from_numpy(t).cuda() for t in tiles]
+    rs = lod.build_batched(dts, 20000, mode)
+    for t, r in zip(tiles, rs):
+        got = r.to_host()
+        compare(got, oracle.build(t, 20000, mode, 21), inp=t)
+    for r in rs:
+        r.free()
+
+
+def test_server_alone_and_in_mix_identical(lod):
+    import torch
+    tiles = [synth.sphere_tile(int(n), seed=500 + i) for i, n in
+             enumerate([300_000, 20_000, 1_200_000, 5_000, 700_000, 90_000])]
+    dts = [torch.from_numpy(t).cuda() for t in tiles]
+    torch.cuda.synchronize()
+    srv = lod.Server(hbm_budget_bytes=8 << 30, max_inflight=4)
+    try:
+        tickets = [srv.submit(d, 30000, 1) for d in dts]
+        mixed = [srv.wait(tk).to_host() for tk in tickets]
+        alone = []
+        for d in dts:
+            tk = srv.submit(d, 30000, 1)
+            alone.append(srv.wait(tk).to_host())
+    finally:
+        srv.close()
+    for t, a, b in zip(tiles, alone, mixed):
+        want = oracle.build(t, 30000, 1, 21)
+        compare(a, want, inp=t)
+        compare(b, want, inp=t)
+
+
+def test_server_budget_rejects_oversized(lod):
+    import torch
+    srv = lod.Server(hbm_budget_bytes=1 << 20, max_inflight=1)
+    try:
+        d = torch.from_numpy(synth.sphere(100_000, seed=2)).cuda()
+        with pytest.raises(lod.LodError) as e:
+            srv.submit(d, 1000, 0)
+        assert e.value.status == lod.LOD_ERR_BUDGET
+    finally:
+        srv.close()
