@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(kBlock) k_count(BuildArgs a, const uint32_t* _
   uint32_t nbins = 0;
 
   auto flush = [&]() {
+    __syncthreads();  // every thread's shared-memory increments are done
     if (smem) {
       uint32_t* dst = s.cnt + pyr_off(s.d);
       for (uint32_t b = threadIdx.x; b < nbins; b += blockDim.x)
