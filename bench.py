@@ -1,0 +1,388 @@
+#!/usr/bin/env python3
+"""LOD build benchmark (one JSON line on stdout).
+
+Workload: the 50M-point aerial-LiDAR-like cloud (x, y uniform over a 2^24
+square, 6-octave fBm heightfield, 10 % building walls/roofs, int32 xyz +
+RGBA8), leaf threshold T = 50k, 128^3 voxel grid.  One step = one
+colour-filtered build plus one sample-pick build of that cloud, with the
+input resident in HBM; ``value`` is points built per second over both
+builds (M points/s).  Inputs (800 MB) are larger than L2, so no flush is
+needed between steps.
+
+Reported beside it: per-build latency p50/p99, the build's fraction of the
+HBM roofline (algorithmic bytes 64 N + 16 V + 16 (V - V_root)), the
+dominant kernel's live roofline (CUDA events on the launching stream), an
+end-to-end figure through the host-buffer C-ABI call (input H2D and the
+whole octree D2H inside the timed region), SM clocks sampled during the
+timed region, and the CPU oracle timed on a bounded sample.
+
+``--impl reference`` times the CPU oracle (the plain restatement of the
+method in oracle/) on the same workload and metric instead.
+Multi-GPU (torchrun): every rank builds its own replica (the method has no
+exchange step); ``value`` is all ranks' points over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    # name: (generator, n, seed, T)
+    "aerial50m": ("aerial", 50_000_000, 2, 50000),
+    "sphere1m": ("sphere", 1_000_000, 1, 50000),
+    "indoor100m": ("indoor", 100_000_000, 3, 50000),
+}
+METRIC = "LOD build M points/s (filtered & sample-pick), % HBM roofline; tile p50/p99 ms"
+
+
+def gen(name: str, seed_offset: int = 0) -> np.ndarray:
+    """Seeded workload; LOD_BENCH_CACHE=<dir> keeps a copy between runs
+    (generation is outside every timed region)."""
+    cache = os.environ.get("LOD_BENCH_CACHE")
+    if cache:
+        path = os.path.join(cache, f"{name}_{seed_offset}.npy")
+        if os.path.exists(path):
+            return np.load(path)
+        pts = _gen(name, seed_offset)
+        os.makedirs(cache, exist_ok=True)
+        np.save(path, pts)
+        return pts
+    return _gen(name, seed_offset)
+
+
+def _gen(name: str, seed_offset: int) -> np.ndarray:
+    from paper_2302_14801_gb300 import synth
+    g, n, seed, _ = WORKLOADS[name]
+    if g == "aerial":
+        return synth.aerial(n, seed=seed + seed_offset)
+    if g == "sphere":
+        return synth.sphere(n, seed=seed + seed_offset)
+    return synth.indoor(n, seed=seed + seed_offset)
+
+
+def peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(", ") for r in open(self.f.name).read().strip().splitlines() if r.count(",") >= 9]
+        os.unlink(self.f.name)
+        if self.uuid:
+            mine = [r for r in rows if self.uuid in r[1]]
+            rows = mine or rows
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[6 + j].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def b_alg(n_points: int, n_voxels: int, root_voxels: int) -> float:
+    """Algorithmic bytes of one build: 64 B per point (bounding box read,
+    one counting read, scatter read + write) + 16 B per voxel written + 16 B
+    per non-root voxel read by its parent."""
+    return 64.0 * n_points + 16.0 * n_voxels + 16.0 * (n_voxels - root_voxels)
+
+
+def cpu_oracle_sample(pts: np.ndarray, T: int, budget_s: float = 12.0, seed: int = 11) -> dict:
+    """The oracle (as it stands) on a bounded spatial sample of the workload:
+    the points inside a square x-y window (same density as the full cloud),
+    grown until one filtered + one pick build take about budget_s seconds."""
+    import oracle
+    lo = pts[:, :2].min(axis=0).astype(np.int64)
+    hi = pts[:, :2].max(axis=0).astype(np.int64)
+    frac = 1.0 / 256
+    best = None
+    while True:
+        side = np.sqrt(frac) * (hi - lo)
+        sel = np.all((pts[:, :2] >= lo) & (pts[:, :2] < lo + side), axis=1)
+        sample = np.ascontiguousarray(pts[sel])
+        t0 = time.perf_counter()
+        oracle.build(sample, T, 0, 21)
+        oracle.build(sample, T, 1, 21)
+        dt = time.perf_counter() - t0
+        best = (len(sample), dt, frac)
+        if dt >= budget_s / 4 or frac >= 1.0:
+            break
+        frac = min(1.0, frac * 4)
+    n, dt, frac = best
+    return {"value": 2.0 * n / dt / 1e6, "unit": "M points/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} points in an x-y window covering {frac * 100:.3g}% of the cloud's area; "
+                      f"one filtered + one pick build, single-threaded, {dt:.2f} s"}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.compile_oracle()
+    name = args.workload
+    _, n, _, T = WORKLOADS[name]
+    pts = gen(name)
+    # each step: one filtered + one pick oracle build on a bounded spatial sample
+    lo = pts[:, :2].min(axis=0).astype(np.int64)
+    hi = pts[:, :2].max(axis=0).astype(np.int64)
+    frac = args.ref_fraction
+    side = np.sqrt(frac) * (hi - lo)
+    sel = np.all((pts[:, :2] >= lo) & (pts[:, :2] < lo + side), axis=1)
+    sample = np.ascontiguousarray(pts[sel])
+    ns = len(sample)
+    for _ in range(args.warmup):
+        oracle.build(sample, T, 0, 21)
+        oracle.build(sample, T, 1, 21)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.build(sample, T, 0, 21)
+        oracle.build(sample, T, 1, 21)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    value = 2.0 * ns / t / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "M points/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32/u64", "data": "synthetic",
+        "config": {"workload": f"{name}: {n} points, T={T}, 128^3 grid, filtered + pick; "
+                               f"oracle on a {ns}-point x-y window sample ({frac * 100:.3g}% of the area)"},
+        "cpu_baseline": {"value": value, "unit": "M points/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{ns} points (x-y window, {frac * 100:.3g}% of the area) per step"},
+        "e2e": {"value": value, "unit": "M points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="aerial50m", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-fraction", type=float, default=1.0 / 64)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2302_14801_gb300 import lod
+
+    name = args.workload
+    _, n, _, T = WORKLOADS[name]
+    pts = gen(name, seed_offset=rank)
+    d = torch.from_numpy(pts).cuda()
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+
+    def step(timings=None):
+        rs = []
+        for mode in (lod.FILTER, lod.PICK):
+            if timings is not None:
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+            r = lod.build(d, T, mode, 21, stream=stream)
+            if timings is not None:
+                b.record(stream)
+                timings[mode].append((a, b))
+            rs.append(r)
+        return rs
+
+    # warm-up (also yields the voxel counts for the algorithmic bytes)
+    info = {}
+    for _ in range(args.warmup):
+        rs = step()
+        for mode, r in zip((lod.FILTER, lod.PICK), rs):
+            v = r.view()
+            h = r.to_host() if mode not in info else None
+            if h is not None:
+                root_vox = int(h["voxel_count"][0])
+                info[mode] = {"voxels": int(v.n_voxels), "root_voxels": root_vox, "nodes": int(v.n_nodes),
+                              "levels": int(v.n_levels)}
+            r.free()
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    lod.profile_reset()
+    lod.profile_enable(True)
+    timings = {lod.FILTER: [], lod.PICK: []}
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = lod.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        for r in step(timings):
+            r.free()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = lod.launch_count() - launches0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    lod.profile_enable(False)
+    prof = lod.profile_read()
+    ms_step = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * 2.0 * n / (ms_step * 1e-3) / 1e6
+
+    pk = peaks()
+    per_mode = {}
+    for mode, key in ((lod.FILTER, "filtered"), (lod.PICK, "pick")):
+        lat = sorted(a.elapsed_time(b) for a, b in timings[mode])
+        med = statistics.median(lat)
+        p99 = lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))]
+        ba = b_alg(n, info[mode]["voxels"], info[mode]["root_voxels"])
+        per_mode[key] = {"ms_p50": med, "ms_p99": p99, "mpts_per_s": n / (med * 1e-3) / 1e6,
+                         "voxels": info[mode]["voxels"], "nodes": info[mode]["nodes"],
+                         "levels": info[mode]["levels"], "alg_bytes": ba,
+                         "hbm_frac": (ba / (med * 1e-3) / 1e9) / pk["hbm_gbs"]}
+
+    # dominant kernel (largest total time) and its live roofline
+    kern = {}
+    for k, s in prof.items():
+        if s["launches"]:
+            kern[k] = {"launches": s["launches"], "avg_ms": s["total_ms"] / s["launches"],
+                       "share": None, "alg_gbs": (s["alg_bytes"] / (s["total_ms"] * 1e-3) / 1e9) if s["total_ms"] else 0}
+    tot = sum(s["total_ms"] for s in prof.values()) or 1.0
+    for k in kern:
+        kern[k]["share"] = prof[k]["total_ms"] / tot
+    dom = max(prof, key=lambda k: prof[k]["total_ms"]) if prof else None
+    roof = None
+    if dom:
+        s = prof[dom]
+        ach = s["alg_bytes"] / (s["total_ms"] * 1e-3) / 1e9
+        traffic = None
+        tp = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tp):
+            traffic = json.load(open(tp)).get(f"{name}:{dom}")
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "traffic": traffic, "peak_source": pk["source"],
+                "avg_launch_ms": s["total_ms"] / s["launches"], "alg_bytes_per_launch": s["alg_bytes"] / s["launches"]}
+
+    # end to end through the host-buffer call: H2D of the input + build + D2H of the octree
+    e2e = None
+    if not args.no_e2e:
+        hp = torch.from_numpy(pts).pin_memory()
+        h2d = d2h = 0
+        t_e2e = []
+        for it in range(args.warmup + max(1, args.steps // 2)):
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            bytes_out = 0
+            for mode in (lod.FILTER, lod.PICK):
+                r = lod.build_from_host(hp, T, mode, 21, stream=stream)
+                h = r.to_host(stream=stream)
+                bytes_out += sum(x.nbytes for x in (h["points"], h["voxels"]) if x is not None)
+                bytes_out += (h["index"].nbytes if h["index"] is not None else 0) + len(h["level"]) * 56
+                r.free()
+            b.record(stream)
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                t_e2e.append(a.elapsed_time(b))
+                h2d, d2h = 2 * n * 16, bytes_out
+        me = statistics.median(t_e2e)
+        e2e = {"value": world * 2.0 * n / (me * 1e-3) / 1e6, "unit": "M points/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": me}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(pts, T)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "M points/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32/u64", "data": "synthetic",
+            "config": {"workload": f"{name}: {n} points (seeded synthetic), T={T}, 128^3 grid; "
+                                   "step = 1 filtered + 1 pick build, input resident in HBM",
+                       "l2": "inputs (800 MB) larger than L2; no flush", "replicas": world},
+            "modes": per_mode, "roofline": roof, "kernels": kern, "gpu_launches": launches,
+            "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -203,6 +203,31 @@ void lod_free(lod_result_t* r);
 /* Static description of a status code. */
 const char* lod_error_string(int status);
 
+/* ------------------------------------------------------------ profiling */
+
+/* Per-kernel statistics accumulated by the library while profiling is on:
+ * every kernel launch is bracketed by CUDA events recorded on the stream it
+ * is launched on, and its elapsed time and algorithmic bytes (the bytes the
+ * method itself has to move for that launch: 16 B per point read, 16 B per
+ * point or voxel record written or read) are added to its entry. */
+typedef struct lod_kernel_stat {
+  char name[32];
+  uint64_t launches;
+  double total_ms;
+  double alg_bytes;
+} lod_kernel_stat_t;
+
+/* Switch event timing on (1) or off (0); process-wide, off by default. */
+int lod_profile_enable(int on);
+/* Clear the accumulated statistics and the launch counter. */
+int lod_profile_reset(void);
+/* Copy up to `capacity` entries into stats (host); *n_stats receives the
+ * number of distinct kernels recorded. */
+int lod_profile_read(lod_kernel_stat_t* stats, uint32_t capacity, uint32_t* n_stats);
+/* Number of kernels this library has launched since the last reset
+ * (counted whether or not profiling is on). */
+uint64_t lod_launch_count(void);
+
 /* -------------------------------------------------------------- serving */
 
 /* A server admits tile-build requests as they arrive and runs them

@@ -211,6 +211,14 @@ void lod_free(lod_result_t* r) {
   delete r;
 }
 
+int lod_profile_enable(int on) { return lodk::profile_enable(on != 0); }
+int lod_profile_reset(void) { return lodk::profile_reset(); }
+int lod_profile_read(lod_kernel_stat_t* stats, uint32_t capacity, uint32_t* n_stats) {
+  if (!n_stats) return LOD_ERR_INVALID_ARG;
+  return lodk::profile_read(stats, capacity, n_stats);
+}
+uint64_t lod_launch_count(void) { return lodk::launch_count(); }
+
 const char* lod_error_string(int status) {
   switch (status) {
     case LOD_OK: return "ok";

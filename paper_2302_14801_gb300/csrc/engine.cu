@@ -8,9 +8,12 @@
 // bounding box, once per counting round, once after the node tables and
 // once per voxel level.
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <string>
 
 #include "engine.h"
 #include "kernels.h"
@@ -199,7 +202,117 @@ PoolLayout layout_pool(const std::vector<SrcDesc>& v, size_t first, size_t n, st
   return L;
 }
 
+// ------------------------------------------------------------ profiling
+struct KStat {
+  uint64_t launches = 0;
+  double ms = 0.0, bytes = 0.0;
+};
+std::mutex g_prof_mu;
+std::map<std::string, KStat> g_prof;
+std::vector<cudaEvent_t> g_event_pool;
+std::atomic<bool> g_prof_on{false};
+std::atomic<uint64_t> g_launches{0};
+
+cudaEvent_t pool_event() {
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_event_pool.empty()) {
+      cudaEvent_t e = g_event_pool.back();
+      g_event_pool.pop_back();
+      return e;
+    }
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets every launch of one build with events on the build stream when
+// profiling is on; resolves them after the build's host synchronisations.
+struct Prof {
+  struct Rec {
+    const char* name;
+    cudaEvent_t a, b;
+    double bytes;
+  };
+  cudaStream_t st;
+  bool on;
+  cudaEvent_t a = nullptr;
+  std::vector<Rec> recs;
+  explicit Prof(cudaStream_t s) : st(s), on(g_prof_on.load()) {}
+  ~Prof() {
+    // unresolved records (error paths): give the events back
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto& r : recs) {
+      g_event_pool.push_back(r.a);
+      g_event_pool.push_back(r.b);
+    }
+  }
+  void begin() {
+    if (!on) return;
+    a = pool_event();
+    if (a) cudaEventRecord(a, st);
+  }
+  void end(const char* name, double bytes) {
+    g_launches.fetch_add(1);
+    if (!on || !a) return;
+    cudaEvent_t b = pool_event();
+    if (!b) return;
+    cudaEventRecord(b, st);
+    recs.push_back({name, a, b, bytes});
+    a = nullptr;
+  }
+  // call after the stream has been synchronised
+  void resolve() {
+    if (recs.empty()) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto& r : recs) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+        KStat& k = g_prof[r.name];
+        k.launches += 1;
+        k.ms += ms;
+        k.bytes += r.bytes;
+      }
+      g_event_pool.push_back(r.a);
+      g_event_pool.push_back(r.b);
+    }
+    recs.clear();
+  }
+};
+
 }  // namespace
+
+int profile_enable(bool on) {
+  g_prof_on.store(on);
+  return LOD_OK;
+}
+
+int profile_reset() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof.clear();
+  g_launches.store(0);
+  return LOD_OK;
+}
+
+int profile_read(lod_kernel_stat_t* out, uint32_t cap, uint32_t* n) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  uint32_t i = 0;
+  for (auto& kv : g_prof) {
+    if (out && i < cap) {
+      std::memset(&out[i], 0, sizeof(lod_kernel_stat_t));
+      std::strncpy(out[i].name, kv.first.c_str(), sizeof(out[i].name) - 1);
+      out[i].launches = kv.second.launches;
+      out[i].total_ms = kv.second.ms;
+      out[i].alg_bytes = kv.second.bytes;
+    }
+    ++i;
+  }
+  if (n) *n = i;
+  return LOD_OK;
+}
+
+uint64_t launch_count() { return g_launches.load(); }
 
 static std::mutex g_free_mu;
 static cudaStream_t g_free_streams[64] = {};
@@ -239,10 +352,29 @@ uint64_t estimate_build_bytes(uint64_t n, const lod_params_t& p) {
   return estimate_result_bytes(n, p) + n * 20 + n * 40 + nodes * sizeof(NodeAux) + pool + (16u << 20);
 }
 
+// Keep freed blocks of the device's stream-ordered pool instead of returning
+// them to the driver at every synchronisation (the pool's default), so that
+// repeated builds reuse their buffers without re-mapping memory.
+static void retain_pool_memory() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  done[dev] = true;
+}
+
 int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaStream_t st,
               std::shared_ptr<SharedBuffers>* shared_out, std::vector<TileResult>* tiles_out, BuildStats* stats) {
   BuildStats S;
   if (nt == 0 || !tin) return LOD_ERR_INVALID_ARG;
+  retain_pool_memory();
   if (prm.leaf_threshold == 0 || prm.mode > 1 || prm.max_depth > 32) return LOD_ERR_INVALID_ARG;
   const bool want_idx = prm.mode == LOD_PICK || (prm.flags & LOD_FLAG_LEAF_INDEX);
   const uint32_t T = prm.leaf_threshold;
@@ -272,6 +404,14 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
   LOD_CK(cudaGetDevice(&sh->device));
   const int grid = 2 * sm_count();
   Uploader up_(st);
+  Prof prof(st);
+#define LOD_LAUNCH(name, bytes, call) \
+  do {                                \
+    prof.begin();                     \
+    LOD_CK(call);                     \
+    prof.end(name, (double)(bytes));  \
+    ++S.launches;                     \
+  } while (0)
 
   DevBuf d_points(st), d_index(st), d_tiles(st), d_chunk0(st), d_chunk_src(st), d_bbox(st), d_ctr(st),
       d_nchunks(st);
@@ -299,13 +439,14 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
   }
 
   // ---- bounding box (root cube)
-  LOD_CK(launch_bbox(d_tiles.as<TileDesc>(), d_chunk_src.as<uint32_t>(), n_chunks0, d_chunk0.as<uint64_t>(),
-                     d_bbox.as<int>(), grid, st));
-  ++S.launches;
+  LOD_LAUNCH("bbox", 16.0 * M,
+             launch_bbox(d_tiles.as<TileDesc>(), d_chunk_src.as<uint32_t>(), n_chunks0, d_chunk0.as<uint64_t>(),
+                         d_bbox.as<int>(), grid, st));
   std::vector<int> bbox(6 * nt);
   LOD_CK(cudaMemcpyAsync(bbox.data(), d_bbox.p, bbox.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
   LOD_CK(cudaStreamSynchronize(st));
   up_.recycle();
+  prof.resolve();
   ++S.host_syncs;
 
   std::vector<SrcDesc> srcs(nt);
@@ -383,8 +524,10 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
     A.tmp_idx[1] = d_tmpi1.as<uint32_t>();
 
     const int cgrid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)grid, round_chunks));
-    LOD_CK(launch_count(A, d_chunk_src.as<uint32_t>(), d_nchunks.as<unsigned long long>(), cgrid, st));
-    ++S.launches;
+    uint64_t round_points = 0;
+    for (uint32_t i = 0; i < round_n; ++i) round_points += srcs[round_first + i].n;
+    LOD_LAUNCH("count", 16.0 * round_points,
+               launch_count(A, d_chunk_src.as<uint32_t>(), d_nchunks.as<unsigned long long>(), cgrid, st));
 
     // pyramid jobs: up passes (bottom levels d, d-4, ...), down passes (tops 0, 4, ...)
     std::vector<std::vector<PyrJob>> up, down;
@@ -417,13 +560,10 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
     LOD_CK(up_.put(d_jobs.p, all.data(), all.size() * sizeof(PyrJob)));
     size_t jo = 0;
     for (auto& v : up) {
-      LOD_CK(launch_pyr_up(A, d_jobs.as<PyrJob>() + jo, (uint32_t)v.size(), st));
-      ++S.launches;
+      LOD_LAUNCH("pyramid_up", 0, launch_pyr_up(A, d_jobs.as<PyrJob>() + jo, (uint32_t)v.size(), st));
       jo += v.size();
     }
     // capacity of the source table for grids created by this round
-    uint64_t round_points = 0;
-    for (uint32_t i = 0; i < round_n; ++i) round_points += srcs[round_first + i].n;
     const uint64_t need = (uint64_t)n_src + round_points / (T + 1ull) + 16;
     if (need > src_cap) {
       LOD_CK(d_srcs.grow(need * sizeof(SrcDesc), (size_t)n_src * sizeof(SrcDesc)));
@@ -433,9 +573,9 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
     LOD_CK(cudaMemsetAsync(d_ctr.p, 0, sizeof(DevCounters), st));
     const uint32_t next_buf = 1 + (round & 1);
     for (auto& v : down) {
-      LOD_CK(launch_pyr_down(A, d_jobs.as<PyrJob>() + jo, (uint32_t)v.size(), n_src, (uint32_t)(src_cap - n_src),
-                             next_buf, d_ctr.as<DevCounters>(), st));
-      ++S.launches;
+      LOD_LAUNCH("pyramid_down", 0,
+                 launch_pyr_down(A, d_jobs.as<PyrJob>() + jo, (uint32_t)v.size(), n_src,
+                                 (uint32_t)(src_cap - n_src), next_buf, d_ctr.as<DevCounters>(), st));
       jo += v.size();
     }
     DevCounters* hc = static_cast<DevCounters*>(tl_stage.get(sizeof(DevCounters)));
@@ -443,6 +583,7 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
     LOD_CK(cudaMemcpyAsync(hc, d_ctr.p, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
     LOD_CK(cudaStreamSynchronize(st));
     up_.recycle();
+    prof.resolve();
     ++S.host_syncs;
     if (hc->error) return LOD_ERR_INTERNAL;
     const uint32_t new_srcs = (uint32_t)hc->new_srcs;
@@ -459,8 +600,8 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
       A.tmp_idx[0] = d_tmpi0.as<uint32_t>();
       A.tmp_idx[1] = d_tmpi1.as<uint32_t>();
     }
-    LOD_CK(launch_scatter(A, d_chunk_src.as<uint32_t>(), d_nchunks.as<unsigned long long>(), round, cgrid, st));
-    ++S.launches;
+    LOD_LAUNCH("scatter", 32.0 * round_points,
+               launch_scatter(A, d_chunk_src.as<uint32_t>(), d_nchunks.as<unsigned long long>(), round, cgrid, st));
     if (!new_srcs) break;
 
     // next round: the new grids, their chunk space
@@ -469,6 +610,7 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
                            cudaMemcpyDeviceToHost, st));
     LOD_CK(cudaStreamSynchronize(st));
     up_.recycle();
+    prof.resolve();
     ++S.host_syncs;
     round_first = n_src;
     round_n = new_srcs;
@@ -495,7 +637,8 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
   for (uint32_t t = 0; t < nt; ++t) node_cap[t] = (uint32_t)std::min<uint64_t>(64 + 16 * ((td[t].n + T - 1) / T), 0x7FFFFFFFull);
   DevBuf d_nodes(st), d_aux(st), d_lvl(st), d_nn(st), d_leafcap(st);
   std::vector<uint32_t> n_nodes(nt), lvl((size_t)nt * (kMaxLevels + 1));
-  std::vector<unsigned long long> leaf_cap(kMaxLevels + 1);
+  // [0, L): per level sum of min(leaf points, 64^3); [L, 2L): exact leaf points
+  std::vector<unsigned long long> leaf_cap(2 * (kMaxLevels + 1));
   uint64_t total_cap = 0;
   for (int attempt = 0;; ++attempt) {
     total_cap = 0;
@@ -512,14 +655,15 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
     LOD_CK(d_leafcap.alloc(leaf_cap.size() * 8));
     LOD_CK(cudaMemsetAsync(d_leafcap.p, 0, leaf_cap.size() * 8, st));
     LOD_CK(cudaMemsetAsync(d_ctr.p, 0, sizeof(DevCounters), st));
-    LOD_CK(launch_nodes(A, d_nodes.as<lod_node_t>(), d_aux.as<NodeAux>(), d_lvl.as<uint32_t>(), d_nn.as<uint32_t>(),
-                        d_leafcap.as<unsigned long long>(), d_ctr.as<DevCounters>(), st));
-    ++S.launches;
+    LOD_LAUNCH("nodes", 0,
+               launch_nodes(A, d_nodes.as<lod_node_t>(), d_aux.as<NodeAux>(), d_lvl.as<uint32_t>(),
+                            d_nn.as<uint32_t>(), d_leafcap.as<unsigned long long>(), d_ctr.as<DevCounters>(), st));
     LOD_CK(cudaMemcpyAsync(n_nodes.data(), d_nn.p, nt * 4, cudaMemcpyDeviceToHost, st));
     LOD_CK(cudaMemcpyAsync(lvl.data(), d_lvl.p, lvl.size() * 4, cudaMemcpyDeviceToHost, st));
     LOD_CK(cudaMemcpyAsync(leaf_cap.data(), d_leafcap.p, leaf_cap.size() * 8, cudaMemcpyDeviceToHost, st));
     LOD_CK(cudaStreamSynchronize(st));
     up_.recycle();
+    prof.resolve();
     ++S.host_syncs;
     bool retry = false;
     for (uint32_t t = 0; t < nt; ++t)
@@ -554,7 +698,7 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
   LOD_CK(cudaMemsetAsync(d_tvox.p, 0, nt * 8, st));
   LOD_CK(d_itemp.alloc((nt + 1) * 4));
   LOD_CK(d_parp.alloc((nt + 1) * 4));
-  uint64_t V = 0, inner_cap = 0;
+  uint64_t V = 0, inner_cap = 0, V_child = 0, V_top = 0;
   uint64_t stage_cap[2] = {0, 0};
   VoxLevel vl;
   std::memset(&vl, 0, sizeof(vl));
@@ -595,10 +739,11 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
     vl.dense = d_dense.as<int4>();
     vl.stage_used = &d_ctr.as<DevCounters>()->stage_used[par];
     A.tiles = d_tiles.as<TileDesc>();
-    LOD_CK(launch_vox(A, vl, d_ctr.as<DevCounters>(), st));
-    LOD_CK(launch_level_scan(A, vl, d_parp.as<uint32_t>(), n_par, V, d_tvox.as<unsigned long long>(),
-                             d_ctr.as<DevCounters>(), st));
-    S.launches += 2;
+    LOD_LAUNCH("voxelize", 0, launch_vox(A, vl, d_ctr.as<DevCounters>(), st));
+    const size_t vox_rec = prof.recs.size();
+    LOD_LAUNCH("level_scan", 0,
+               launch_level_scan(A, vl, d_parp.as<uint32_t>(), n_par, V, d_tvox.as<unsigned long long>(),
+                                 d_ctr.as<DevCounters>(), st));
     DevCounters* hc = static_cast<DevCounters*>(tl_stage.get(sizeof(DevCounters)));
     if (!hc) return LOD_ERR_OOM;
     LOD_CK(cudaMemcpyAsync(hc, d_ctr.p, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
@@ -608,6 +753,14 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
     if (hc->error) return LOD_ERR_INTERNAL;
     V += hc->level_voxels;
     inner_cap = hc->next_cap;
+    if (prof.on && vox_rec >= 1 && vox_rec <= prof.recs.size()) {
+      // reads: leaf points and the children's voxels; writes: this level's voxels
+      prof.recs[vox_rec - 1].bytes =
+          16.0 * (double)(leaf_cap[kMaxLevels + 1 + l + 1] + V_child + hc->level_voxels);
+    }
+    prof.resolve();
+    V_child = hc->level_voxels;
+    V_top = hc->level_voxels;
     if (V > dense_cap) {
       const uint64_t nc = std::max<uint64_t>(V, dense_cap * 2);
       LOD_CK(d_dense.grow(nc * 16, (V - hc->level_voxels) * 16));
@@ -617,13 +770,13 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
   }
   if (have_top) {
     vl.dense = d_dense.as<int4>();
-    LOD_CK(launch_copy_items(A, vl, st));
-    ++S.launches;
+    LOD_LAUNCH("publish_top", 32.0 * V_top, launch_copy_items(A, vl, st));
   }
   std::vector<unsigned long long> tvox(nt);
   LOD_CK(cudaMemcpyAsync(tvox.data(), d_tvox.p, nt * 8, cudaMemcpyDeviceToHost, st));
   LOD_CK(cudaStreamSynchronize(st));
   up_.recycle();
+  prof.resolve();
   ++S.host_syncs;
 
   // ---- results

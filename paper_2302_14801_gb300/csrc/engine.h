@@ -53,6 +53,12 @@ uint64_t estimate_build_bytes(uint64_t n, const lod_params_t& params);
 // Rough device footprint of a finished result of n points.
 uint64_t estimate_result_bytes(uint64_t n, const lod_params_t& params);
 
+// Process-wide kernel profiling (see lod_profile_* in lod.h).
+int profile_enable(bool on);
+int profile_reset();
+int profile_read(lod_kernel_stat_t* out, uint32_t cap, uint32_t* n);
+uint64_t launch_count();
+
 // A library-owned non-blocking stream of the current device used to
 // release buffers asynchronously.
 cudaStream_t free_stream();

@@ -33,7 +33,7 @@ EXPORTED = [
     "lod_params_init", "lod_build", "lod_build_from_host", "lod_build_batched", "lod_result_view",
     "lod_result_copy_to_host", "lod_result_device_bytes", "lod_free", "lod_error_string",
     "lod_server_create", "lod_submit", "lod_poll", "lod_wait", "lod_server_bytes_in_use",
-    "lod_server_destroy",
+    "lod_server_destroy", "lod_profile_enable", "lod_profile_reset", "lod_profile_read", "lod_launch_count",
 ]
 
 
@@ -60,6 +60,11 @@ class View(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double),
+                ("alg_bytes", ctypes.c_double)]
 
 
 NODE_DTYPE = np.dtype([("min", "<i4", (3,)), ("level", "u1"), ("log2_size", "u1"), ("child_mask", "u1"),
@@ -97,6 +102,10 @@ def _load():
         "lod_wait": (i, [vp, u64, u32, P(vp)]),
         "lod_server_bytes_in_use": (u64, [vp]),
         "lod_server_destroy": (i, [vp]),
+        "lod_profile_enable": (i, [i]),
+        "lod_profile_reset": (i, []),
+        "lod_profile_read": (i, [P(KernelStat), u32, P(u32)]),
+        "lod_launch_count": (u64, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -137,6 +146,28 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
+
+
+def profile_enable(on: bool = True) -> None:
+    _check(lib().lod_profile_enable(1 if on else 0), "lod_profile_enable")
+
+
+def profile_reset() -> None:
+    _check(lib().lod_profile_reset(), "lod_profile_reset")
+
+
+def profile_read() -> dict:
+    """{kernel name: {"launches", "total_ms", "alg_bytes"}} accumulated so far."""
+    n = ctypes.c_uint32()
+    _check(lib().lod_profile_read(None, 0, ctypes.byref(n)), "lod_profile_read")
+    arr = (KernelStat * max(n.value, 1))()
+    _check(lib().lod_profile_read(arr, n.value, ctypes.byref(n)), "lod_profile_read")
+    return {arr[i].name.decode(): {"launches": int(arr[i].launches), "total_ms": float(arr[i].total_ms),
+                                   "alg_bytes": float(arr[i].alg_bytes)} for i in range(n.value)}
+
+
+def launch_count() -> int:
+    return int(lib().lod_launch_count())
 
 
 class _DevArray:
