@@ -203,6 +203,31 @@ void lod_free(lod_result_t* r);
 /* Static description of a status code. */
 const char* lod_error_string(int status);
 
+/* ------------------------------------------------------- no allocation */
+
+/* Root cube of each of n_tiles point clouds, computed without allocating
+ * any device memory.  The paper has no counterpart to this call; it exists
+ * for callers that cannot call cudaMalloc (a plug-in whose host application
+ * owns all device memory, a render loop that must not let an allocation
+ * synchronise the device, code held to a fixed memory budget).
+ *   d_tiles  host array of n_tiles device pointers (16-byte aligned; may be
+ *            NULL where n[t] == 0).
+ *   n        host array of n_tiles point counts (each < 2^32).
+ *   n_tiles  1 .. 4096; larger batches return LOD_ERR_INVALID_ARG.
+ *   d_cubes  device, caller-owned, 4 int32 per tile: min x, y, z of the
+ *            root cube (the bounding-box minimum) and log2 of its edge (the
+ *            smallest power of two strictly greater than the largest
+ *            extent) — the root node lod_build produces; an empty tile
+ *            gives 0, 0, 0, 0.
+ *   stream   cudaStream_t as void*; the call is asynchronous on it.
+ * Scratch: a 160 KB array in static device memory, one per device that
+ * loads the library, held until the process exits.  The first call on a
+ * device looks up that array's device address; make that first call before
+ * any stream capture.  All calls share the array, so calls whose work
+ * overlaps on the GPU race with one another: issue them on one stream. */
+int lod_root_cubes_noalloc(const lod_point_t* const* d_tiles, const uint64_t* n, uint32_t n_tiles,
+                           int32_t* d_cubes, void* stream);
+
 /* ------------------------------------------------------------ profiling */
 
 /* Per-kernel statistics accumulated by the library while profiling is on:

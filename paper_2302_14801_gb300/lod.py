@@ -34,6 +34,7 @@ EXPORTED = [
     "lod_result_copy_to_host", "lod_result_device_bytes", "lod_free", "lod_error_string",
     "lod_server_create", "lod_submit", "lod_poll", "lod_wait", "lod_server_bytes_in_use",
     "lod_server_destroy", "lod_profile_enable", "lod_profile_reset", "lod_profile_read", "lod_launch_count",
+    "lod_root_cubes_noalloc",
 ]
 
 
@@ -106,6 +107,7 @@ def _load():
         "lod_profile_reset": (i, []),
         "lod_profile_read": (i, [P(KernelStat), u32, P(u32)]),
         "lod_launch_count": (u64, []),
+        "lod_root_cubes_noalloc": (i, [P(vp), P(u64), u32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -296,6 +298,26 @@ def build_batched(tiles, leaf_threshold=50000, mode=FILTER, max_depth=21, keep_i
     _check(lib().lod_build_batched(ptrs, ns, nt, ctypes.byref(p), _stream_handle(stream), outs),
            "lod_build_batched")
     return [Result(outs[t]) for t in range(nt)]
+
+
+def root_cubes_noalloc(tiles, out, stream=None) -> None:
+    """lod_root_cubes_noalloc: root cube (min x, y, z, log2 edge) of every
+    CUDA int32 (N_t, 4) tensor in ``tiles`` into the caller's CUDA int32
+    tensor ``out`` of shape (len(tiles), 4).  The library allocates no device
+    memory for this call (its scratch is a static device array)."""
+    import torch
+    nt = len(tiles)
+    if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.int32
+            and tuple(out.shape) == (nt, 4) and out.is_contiguous()):
+        raise TypeError("out must be a contiguous CUDA int32 tensor of shape (n_tiles, 4)")
+    ptrs = (ctypes.c_void_p * max(nt, 1))()
+    ns = (ctypes.c_uint64 * max(nt, 1))()
+    for t, x in enumerate(tiles):
+        ptr, n = _dev_ptr(x)
+        ptrs[t] = ptr if n else None
+        ns[t] = n
+    _check(lib().lod_root_cubes_noalloc(ptrs, ns, nt, out.data_ptr(), _stream_handle(stream)),
+           "lod_root_cubes_noalloc")
 
 
 class Server:
