@@ -228,6 +228,24 @@ const char* lod_error_string(int status);
 int lod_root_cubes_noalloc(const lod_point_t* const* d_tiles, const uint64_t* n, uint32_t n_tiles,
                            int32_t* d_cubes, void* stream);
 
+/* --------------------------------------------------------------- tuning */
+
+/* Launch and tiling parameters that change speed, never results.  They are
+ * process-wide; set them while no build is running.  Zero means "default".
+ *   root_depth      depth d of each tile's first counting grid (8^d cells,
+ *                   1..8, still capped by the cube and max_depth); default:
+ *                   one more level than a surface-like cloud needs to reach
+ *                   the leaf threshold.
+ *   stream_ctas_per_sm  CTAs per SM of the streaming passes (default 2). */
+typedef struct lod_tuning {
+  uint32_t root_depth;
+  uint32_t stream_ctas_per_sm;
+  uint32_t reserved[6];
+} lod_tuning_t;
+
+int lod_set_tuning(const lod_tuning_t* t);
+int lod_get_tuning(lod_tuning_t* t);
+
 /* ------------------------------------------------------------ profiling */
 
 /* Per-kernel statistics accumulated by the library while profiling is on:

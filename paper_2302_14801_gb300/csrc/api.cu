@@ -211,6 +211,9 @@ void lod_free(lod_result_t* r) {
   delete r;
 }
 
+int lod_set_tuning(const lod_tuning_t* t) { return t ? lodk::set_tuning(*t) : LOD_ERR_INVALID_ARG; }
+int lod_get_tuning(lod_tuning_t* t) { return t ? lodk::get_tuning(t) : LOD_ERR_INVALID_ARG; }
+
 int lod_profile_enable(int on) { return lodk::profile_enable(on != 0); }
 int lod_profile_reset(void) { return lodk::profile_reset(); }
 int lod_profile_read(lod_kernel_stat_t* stats, uint32_t capacity, uint32_t* n_stats) {

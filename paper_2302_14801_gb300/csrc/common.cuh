@@ -59,6 +59,9 @@ struct SrcDesc {
   uint32_t pt_off;
   uint32_t n;
   uint64_t chunk0;     // first chunk of this source in its round's chunk space
+  uint32_t priv;       // 1: counted through per-CTA shared-memory tables
+                       // (grids too large for a dense shared histogram)
+  uint32_t pad;
 };
 
 // Build-wide settings shared by every kernel of one build.
@@ -73,7 +76,17 @@ struct BuildArgs {
   uint32_t* out_idx;   // original input index per leaf point (or null)
   int4* tmp[2];        // refinement ping-pong buffers (absolute positions)
   uint32_t* tmp_idx[2];
+  // privatised counting of large grids: counters are keyed by their index
+  // relative to cnt_base; each CTA leaves its (key, count) list in lists
+  uint32_t* cnt_base;      // count region of the round's pool
+  uint64_t cursor_delta;   // start region - count region (u32 elements)
+  uint2* lists;            // kPrivSlots entries per CTA
+  uint32_t* list_len;      // per CTA
+  unsigned long long* diag;  // [0] points counted outside the tables, [1] table inserts
 };
+
+constexpr uint32_t kPrivSlots = 16384;  // per-CTA table of distinct cells (128 KB)
+constexpr uint32_t kPrivProbe = 32;     // longest probe sequence before a cell counts as not fitting
 
 // Per-node internal bookkeeping of the voxel pass, indexed by absolute node.
 struct NodeAux {
@@ -90,6 +103,8 @@ struct DevCounters {
   unsigned long long stage_used[2];   // staging records bump allocators
   unsigned long long level_voxels;    // voxels of the level just scanned
   unsigned long long next_cap;        // staging bound of the next level
+  unsigned long long vox_retries;     // voxel items that needed more table passes
+  unsigned long long vox_passes;      // table passes over all voxel items
   unsigned int error;                 // nonzero: a kernel detected a problem
   unsigned int pad;
 };

@@ -10,6 +10,8 @@
 #include <algorithm>
 #include <atomic>
 #include <climits>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -161,9 +163,13 @@ uint32_t ceil_log4(double x) {
 // Depth of a tile's first counting grid: deep enough that surface-like
 // clouds reach leaf size without refinement (about 4x fewer points per
 // level), capped at 256^3 cells, the cube's own size and max_depth.
+std::atomic<uint32_t> g_tune_root_depth{0};
+std::atomic<uint32_t> g_tune_ctas_per_sm{0};
+
 uint32_t choose_root_depth(uint64_t n, uint32_t T, uint32_t log2S, uint32_t max_depth) {
   if (n <= T || log2S == 0 || max_depth == 0) return 0;
-  uint32_t d = ceil_log4((double)n / (double)T) + 1;
+  const uint32_t forced = g_tune_root_depth.load();
+  uint32_t d = forced ? forced : ceil_log4((double)n / (double)T) + 1;
   d = std::min(d, kRootMaxD);
   d = std::min(d, log2S);
   d = std::min(d, max_depth);
@@ -281,7 +287,30 @@ struct Prof {
   }
 };
 
+// LOD_DEBUG_STATS=1 prints per-level voxel statistics of every build to stderr.
+bool debug_stats() {
+  static const bool on = [] {
+    const char* e = std::getenv("LOD_DEBUG_STATS");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
+
 }  // namespace
+
+int set_tuning(const lod_tuning_t& t) {
+  if (t.root_depth > kRootMaxD || t.stream_ctas_per_sm > 8) return LOD_ERR_INVALID_ARG;
+  g_tune_root_depth.store(t.root_depth);
+  g_tune_ctas_per_sm.store(t.stream_ctas_per_sm);
+  return LOD_OK;
+}
+
+int get_tuning(lod_tuning_t* t) {
+  std::memset(t, 0, sizeof(*t));
+  t->root_depth = g_tune_root_depth.load();
+  t->stream_ctas_per_sm = g_tune_ctas_per_sm.load();
+  return LOD_OK;
+}
 
 int profile_enable(bool on) {
   g_prof_on.store(on);
@@ -402,7 +431,8 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
 
   auto sh = std::make_shared<SharedBuffers>();
   LOD_CK(cudaGetDevice(&sh->device));
-  const int grid = 2 * sm_count();
+  const uint32_t cps = g_tune_ctas_per_sm.load();
+  const int grid = (int)(cps ? cps : 2) * sm_count();
   Uploader up_(st);
   Prof prof(st);
 #define LOD_LAUNCH(name, bytes, call) \
@@ -476,11 +506,14 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
     s.pt_off = 0;
     s.n = td[t].n;
     s.chunk0 = chunk0[t];
+    s.priv = ipow8(s.d) > kSmemBins ? 1u : 0u;  // too large for a dense shared histogram
     src_bound0 += td[t].n / (T + 1ull);
   }
 
   // ---- counting rounds
-  DevBuf d_srcs(st), d_jobs(st), d_tmp0(st), d_tmp1(st), d_tmpi0(st), d_tmpi1(st);
+  DevBuf d_srcs(st), d_jobs(st), d_tmp0(st), d_tmp1(st), d_tmpi0(st), d_tmpi1(st), d_lists(st), d_llen(st);
+  LOD_CK(d_lists.alloc((size_t)grid * kPrivSlots * sizeof(uint2)));
+  LOD_CK(d_llen.alloc((size_t)grid * sizeof(uint32_t)));
   std::vector<std::unique_ptr<DevBuf>> pools;
   uint64_t src_cap = nt + src_bound0 + 16;
   LOD_CK(d_srcs.alloc(src_cap * sizeof(SrcDesc)));
@@ -493,6 +526,14 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
   A.mode = prm.mode;
   A.out = d_points.as<int4>();
   A.out_idx = want_idx ? d_index.as<uint32_t>() : nullptr;
+  A.lists = d_lists.as<uint2>();
+  A.list_len = d_llen.as<uint32_t>();
+  DevBuf d_diag(st);
+  if (debug_stats()) {
+    LOD_CK(d_diag.alloc(4 * sizeof(unsigned long long)));
+    LOD_CK(cudaMemsetAsync(d_diag.p, 0, 4 * sizeof(unsigned long long), st));
+    A.diag = d_diag.as<unsigned long long>();
+  }
 
   uint32_t round_first = 0, round_n = nt, n_src = nt;
   uint64_t round_chunks = n_chunks0;
@@ -506,6 +547,8 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
     LOD_CK(pool.alloc(L.total * 4));
     LOD_CK(cudaMemsetAsync(pool.p, 0, L.zero * 4, st));
     uint32_t* pb = pool.as<uint32_t>();
+    A.cnt_base = pb + L.cnt;
+    A.cursor_delta = L.start - L.cnt;
     for (uint32_t i = 0; i < round_n; ++i) {
       SrcDesc& s = srcs[round_first + i];
       s.ovf = pb + L.ovf + offs[4 * i + 0];
@@ -586,6 +629,13 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
     prof.resolve();
     ++S.host_syncs;
     if (hc->error) return LOD_ERR_INTERNAL;
+    if (A.diag) {
+      unsigned long long dg[2] = {0, 0};
+      LOD_CK(cudaMemcpy(dg, A.diag, sizeof(dg), cudaMemcpyDeviceToHost));
+      std::fprintf(stderr, "[lod] round %u: %u grids, %llu points, root depth %u, %llu counted outside "
+                   "the CTA tables, %llu table inserts\n", round, round_n, (unsigned long long)round_points,
+                   srcs[round_first].d, dg[0], dg[1]);
+    }
     const uint32_t new_srcs = (uint32_t)hc->new_srcs;
     const uint64_t new_points = hc->new_points;
     if (new_srcs) {
@@ -739,7 +789,14 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
     vl.dense = d_dense.as<int4>();
     vl.stage_used = &d_ctr.as<DevCounters>()->stage_used[par];
     A.tiles = d_tiles.as<TileDesc>();
-    LOD_LAUNCH("voxelize", 0, launch_vox(A, vl, d_ctr.as<DevCounters>(), st));
+    static const char* kVoxLevelNames[kMaxLevels] = {
+        "voxelize_L00", "voxelize_L01", "voxelize_L02", "voxelize_L03", "voxelize_L04", "voxelize_L05",
+        "voxelize_L06", "voxelize_L07", "voxelize_L08", "voxelize_L09", "voxelize_L10", "voxelize_L11",
+        "voxelize_L12", "voxelize_L13", "voxelize_L14", "voxelize_L15", "voxelize_L16", "voxelize_L17",
+        "voxelize_L18", "voxelize_L19", "voxelize_L20", "voxelize_L21", "voxelize_L22", "voxelize_L23",
+        "voxelize_L24", "voxelize_L25", "voxelize_L26", "voxelize_L27", "voxelize_L28", "voxelize_L29",
+        "voxelize_L30", "voxelize_L31", "voxelize_L32", "voxelize_L33"};
+    LOD_LAUNCH(debug_stats() ? kVoxLevelNames[l] : "voxelize", 0, launch_vox(A, vl, d_ctr.as<DevCounters>(), st));
     const size_t vox_rec = prof.recs.size();
     LOD_LAUNCH("level_scan", 0,
                launch_level_scan(A, vl, d_parp.as<uint32_t>(), n_par, V, d_tvox.as<unsigned long long>(),
@@ -759,6 +816,12 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
           16.0 * (double)(leaf_cap[kMaxLevels + 1 + l + 1] + V_child + hc->level_voxels);
     }
     prof.resolve();
+    if (debug_stats())
+      std::fprintf(stderr, "[lod] level %d: items %u (leaf points %llu, child voxels %llu) -> voxels %llu, "
+                   "retried items %llu, table passes %llu\n", l, n_items,
+                   (unsigned long long)leaf_cap[kMaxLevels + 1 + l + 1], (unsigned long long)V_child,
+                   (unsigned long long)hc->level_voxels, (unsigned long long)hc->vox_retries,
+                   (unsigned long long)hc->vox_passes);
     V_child = hc->level_voxels;
     V_top = hc->level_voxels;
     if (V > dense_cap) {

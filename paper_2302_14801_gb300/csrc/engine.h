@@ -53,6 +53,10 @@ uint64_t estimate_build_bytes(uint64_t n, const lod_params_t& params);
 // Rough device footprint of a finished result of n points.
 uint64_t estimate_result_bytes(uint64_t n, const lod_params_t& params);
 
+// Process-wide tuning (see lod_set_tuning in lod.h).
+int set_tuning(const lod_tuning_t& t);
+int get_tuning(lod_tuning_t* t);
+
 // Process-wide kernel profiling (see lod_profile_* in lod.h).
 int profile_enable(bool on);
 int profile_reset();

@@ -24,13 +24,13 @@ __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
 // Morton cell of point p inside a source grid (8^d cells under a cube of
 // edge 2^log2size with min corner mn).
-__device__ __forceinline__ uint32_t src_bin(const int4& p, const int32_t mn[3], uint32_t log2size,
+__device__ __forceinline__ uint32_t src_bin(const int4& p, int32_t mx, int32_t my, int32_t mz, uint32_t log2size,
                                             uint32_t d) {
   if (d == 0) return 0;
   const uint32_t sh = log2size - d;
-  const uint32_t ux = (uint32_t)((uint64_t)((uint32_t)p.x - (uint32_t)mn[0]) >> sh);
-  const uint32_t uy = (uint32_t)((uint64_t)((uint32_t)p.y - (uint32_t)mn[1]) >> sh);
-  const uint32_t uz = (uint32_t)((uint64_t)((uint32_t)p.z - (uint32_t)mn[2]) >> sh);
+  const uint32_t ux = (uint32_t)((uint64_t)((uint32_t)p.x - (uint32_t)mx) >> sh);
+  const uint32_t uy = (uint32_t)((uint64_t)((uint32_t)p.y - (uint32_t)my) >> sh);
+  const uint32_t uz = (uint32_t)((uint64_t)((uint32_t)p.z - (uint32_t)mz) >> sh);
   return morton3(ux, uy, uz);
 }
 
@@ -47,7 +47,7 @@ __device__ __forceinline__ uint32_t compact3(uint32_t v) {
 // Pointer to the points of a source and the tile-absolute base of its range.
 __device__ __forceinline__ const int4* src_points(const BuildArgs& a, const SrcDesc& s, const TileDesc& t) {
   if (s.buf == 0) return t.in;  // round 0 reads the caller's input, index = input index
-  return a.tmp[s.buf - 1] + t.pt_base + s.pt_off;
+  return (s.buf == 1 ? a.tmp[0] : a.tmp[1]) + t.pt_base + s.pt_off;
 }
 
 // Depth of a refinement grid for a cell of n points (surfaces shrink by
@@ -152,15 +152,71 @@ cudaError_t launch_bbox(const TileDesc* tiles, const uint32_t* chunk_tile, uint6
 // ------------------------------------------------------------------- counting
 // Section 3.1.1 (count per cell of the grid) and 3.1.5 (count again inside
 // the extended grids of overflowing cells): one histogram per source.
+//
+// Grids of up to 8^4 cells are counted in a dense shared-memory histogram.
+// Larger first grids are counted through a per-CTA shared-memory hash table
+// keyed by the cell's counter index: a CTA's contiguous run of chunks only
+// touches the occupied cells of the cloud, each of which then costs one
+// global add per CTA instead of one per point.  The table's (cell, count)
+// list is kept for the scatter, which claims one block per cell.  Cells that
+// arrive after the table is full are counted with per-point global atomics.
+
+namespace {
+
+__device__ __forceinline__ uint32_t priv_home(uint32_t key1) { return __umulhi(key1 * 0x9E3779B1u, kPrivSlots); }
+
+// Slot of key1 (= counter index + 1) in a per-CTA table, inserting it if
+// absent; -1 when kPrivProbe consecutive slots hold other cells (the table
+// is then treated as full for this cell).  No shared fill counter is
+// touched: every insert stays independent of the other warps.
+__device__ __forceinline__ int priv_insert(uint32_t* keys, uint32_t key1) {
+  uint32_t slot = priv_home(key1);
+  for (uint32_t probe = 0; probe < kPrivProbe; ++probe) {
+    const uint32_t k = ((volatile uint32_t*)keys)[slot];
+    if (k == key1) return (int)slot;
+    if (k == 0u) {
+      const uint32_t old = atomicCAS(&keys[slot], 0u, key1);
+      if (old == 0u || old == key1) return (int)slot;
+    }
+    slot = (slot + 1 == kPrivSlots) ? 0u : slot + 1;
+  }
+  return -1;
+}
+
+// Slot of key1 if present, -1 otherwise (the table is read-only here; the
+// search ends at an empty slot or after visiting every slot).
+__device__ __forceinline__ int priv_find(const uint32_t* keys, uint32_t key1) {
+  uint32_t slot = priv_home(key1);
+  for (uint32_t probe = 0; probe < kPrivSlots; ++probe) {
+    const uint32_t k = keys[slot];
+    if (k == key1) return (int)slot;
+    if (k == 0u) return -1;
+    slot = (slot + 1 == kPrivSlots) ? 0u : slot + 1;
+  }
+  return -1;
+}
+
+}  // namespace
 
 __global__ void __launch_bounds__(kBlock) k_count(BuildArgs a, const uint32_t* __restrict__ chunk_src,
                                                   const unsigned long long* __restrict__ n_chunks_p) {
   __shared__ uint32_t hist[kSmemBins];
   __shared__ SrcDesc s;
+  __shared__ uint32_t s_list;
+  extern __shared__ uint32_t ptab[];  // kPrivSlots keys, then kPrivSlots counts
+  uint32_t* pkeys = ptab;
+  uint32_t* pcnt = ptab + kPrivSlots;
   const uint64_t n_chunks = *n_chunks_p;
   const uint64_t per = (n_chunks + gridDim.x - 1) / gridDim.x;
   const uint64_t c0 = (uint64_t)blockIdx.x * per;
   const uint64_t c1 = min(c0 + per, n_chunks);
+  for (uint32_t i = threadIdx.x; i < kPrivSlots; i += blockDim.x) {
+    pkeys[i] = 0u;
+    pcnt[i] = 0u;
+  }
+  if (threadIdx.x == 0) {
+    s_list = 0;
+  }
   uint32_t cur = kNone;
   bool smem = false;
   uint32_t nbins = 0;
@@ -175,6 +231,7 @@ __global__ void __launch_bounds__(kBlock) k_count(BuildArgs a, const uint32_t* _
     __syncthreads();
   };
 
+  constexpr int kPer = (int)(kChunk / kBlock);
   for (uint64_t c = c0; c < c1; ++c) {
     const uint32_t sid = chunk_src[c];
     if (sid != cur) {
@@ -192,37 +249,72 @@ __global__ void __launch_bounds__(kBlock) k_count(BuildArgs a, const uint32_t* _
     const int4* pts = src_points(a, s, td);
     const uint64_t first = (c - s.chunk0) << kChunkLog2;
     const uint64_t end = min(first + kChunk, (uint64_t)s.n);
-    uint32_t* gcnt = s.cnt + pyr_off(s.d);
-    int4 p[kChunk / kBlock];
+    const int32_t mx = s.min[0], my = s.min[1], mz = s.min[2];
+    const uint32_t lg = s.log2size, d = s.d;
+    int4 p[kPer];
 #pragma unroll
-    for (int k = 0; k < (int)(kChunk / kBlock); ++k) {
+    for (int k = 0; k < kPer; ++k) {
       const uint64_t i = first + threadIdx.x + (uint64_t)k * kBlock;
       if (i < end) p[k] = ldg_stream(pts + i);
     }
+    if (smem) {
 #pragma unroll
-    for (int k = 0; k < (int)(kChunk / kBlock); ++k) {
+      for (int k = 0; k < kPer; ++k) {
+        const uint64_t i = first + threadIdx.x + (uint64_t)k * kBlock;
+        if (i < end) atomicAdd(&hist[src_bin(p[k], mx, my, mz, lg, d)], 1u);
+      }
+      continue;
+    }
+    const uint32_t kbase = (uint32_t)(s.cnt + pyr_off(d) - a.cnt_base);
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
       const uint64_t i = first + threadIdx.x + (uint64_t)k * kBlock;
-      const bool v = i < end;
-      const uint32_t bin = v ? src_bin(p[k], s.min, s.log2size, s.d) : 0u;
-      if (smem) {
-        if (v) atomicAdd(&hist[bin], 1u);
+      if (i >= end) continue;
+      const uint32_t key = kbase + src_bin(p[k], mx, my, mz, lg, d);
+      const int slot = priv_insert(pkeys, key + 1u);
+      if (slot >= 0) {
+        atomicAdd(&pcnt[slot], 1u);
       } else {
-        const unsigned m = __ballot_sync(0xFFFFFFFFu, v);
-        if (v) {
-          const unsigned peers = __match_any_sync(m, bin);
-          if ((int)lane_id() == __ffs(peers) - 1) atomicAdd(gcnt + bin, (uint32_t)__popc(peers));
-        }
+        atomicAdd(a.cnt_base + key, 1u);  // table full: count globally
+        if (a.diag) atomicAdd(&a.diag[0], 1ull);
       }
     }
   }
   if (cur != kNone) flush();
+  // publish the table: one global add per distinct cell, and the CTA's list
+  __syncthreads();
+  uint2* list = a.lists + (uint64_t)blockIdx.x * kPrivSlots;
+  const uint32_t lane = threadIdx.x & 31u;
+  for (uint32_t i0 = 0; i0 < kPrivSlots; i0 += blockDim.x) {
+    const uint32_t i = i0 + threadIdx.x;
+    const uint32_t key1 = pkeys[i];
+    const bool occ = key1 != 0u;
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, occ);
+    uint32_t wbase = 0;
+    if (lane == 0 && bal) wbase = atomicAdd(&s_list, (uint32_t)__popc(bal));
+    wbase = __shfl_sync(0xFFFFFFFFu, wbase, 0);
+    if (!occ) continue;
+    atomicAdd(a.cnt_base + key1 - 1u, pcnt[i]);
+    list[wbase + __popc(bal & ((1u << lane) - 1u))] = make_uint2(key1 - 1u, pcnt[i]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a.list_len[blockIdx.x] = s_list;
+    if (a.diag) atomicAdd(&a.diag[1], (unsigned long long)s_list);
+  }
 }
 
 cudaError_t launch_count(const BuildArgs& a, const uint32_t* chunk_src, const unsigned long long* n_chunks,
                          int grid, cudaStream_t st) {
-  k_count<<<grid, kBlock, 0, st>>>(a, chunk_src, n_chunks);
+  static bool once = [] {
+    cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * kPrivSlots));
+    return true;
+  }();
+  (void)once;
+  k_count<<<grid, kBlock, 8 * kPrivSlots, st>>>(a, chunk_src, n_chunks);
   return cudaGetLastError();
 }
+
 
 // ------------------------------------------------------------ pyramid: up-sweep
 // Per-level counts (the counting-grid pyramid of Section 3.1.2) from the
@@ -350,6 +442,8 @@ __global__ void __launch_bounds__(512) k_pyr_down(BuildArgs a, const PyrJob* __r
     ns.pt_off = sta[1 + lo[k] + q];
     ns.n = n;
     ns.chunk0 = 0;
+    ns.priv = 0;  // refinement grids are counted in dense shared histograms
+    ns.pad = 0;
     a.srcs[g] = ns;
     s.map[c] = g;
     atomicOr(&s.ovf[c >> 5], 1u << (c & 31));
@@ -366,22 +460,44 @@ cudaError_t launch_pyr_down(const BuildArgs& a, const PyrJob* jobs, uint32_t n_j
 // ------------------------------------------------------------------- scatter
 // Section 3.1.4 (insert): every point goes to its cell's cursor; points of
 // cells that will be refined go to the ping-pong buffer of the next round,
-// all others to their final place in the leaf-point array.  Cursors are
-// claimed with warp-aggregated atomics.
+// all others to their final place in the leaf-point array.  For large grids
+// the CTA re-creates its counting table from its list, claims one block of
+// positions per cell with one global atomic, and hands out positions inside
+// the block with shared-memory atomics (the CTA processes the same chunks as
+// in the counting pass).  Dense small grids claim cursors per point (one
+// atomic per warp when all its points share a cell).
 
 __global__ void __launch_bounds__(kBlock) k_scatter(BuildArgs a, const uint32_t* __restrict__ chunk_src,
                                                     const unsigned long long* __restrict__ n_chunks_p,
                                                     uint32_t round) {
   __shared__ SrcDesc s;
+  extern __shared__ uint32_t ptab[];  // kPrivSlots keys, then kPrivSlots cursors
+  uint32_t* pkeys = ptab;
+  uint32_t* pcur = ptab + kPrivSlots;
   const uint64_t n_chunks = *n_chunks_p;
   const uint64_t per = (n_chunks + gridDim.x - 1) / gridDim.x;
   const uint64_t c0 = (uint64_t)blockIdx.x * per;
   const uint64_t c1 = min(c0 + per, n_chunks);
-  uint32_t cur = kNone;
-  int4* ovf_dst = a.tmp[round & 1];
-  uint32_t* ovf_idx = a.tmp_idx[round & 1];
+  int4* ovf_dst = (round & 1) ? a.tmp[1] : a.tmp[0];
+  uint32_t* ovf_idx = (round & 1) ? a.tmp_idx[1] : a.tmp_idx[0];
   const uint32_t lane = lane_id();
+  // claim this CTA's block of every cell it counted
+  for (uint32_t i = threadIdx.x; i < kPrivSlots; i += blockDim.x) pkeys[i] = 0u;
+  __syncthreads();
+  {
+    const uint32_t len = a.list_len[blockIdx.x];
+    const uint2* list = a.lists + (uint64_t)blockIdx.x * kPrivSlots;
+    for (uint32_t j = threadIdx.x; j < len; j += blockDim.x) {
+      const uint2 e = list[j];
+      uint32_t slot = priv_home(e.x + 1u);
+      while (atomicCAS(&pkeys[slot], 0u, e.x + 1u) != 0u) slot = (slot + 1 == kPrivSlots) ? 0u : slot + 1;
+      pcur[slot] = atomicAdd(a.cnt_base + e.x + a.cursor_delta, e.y);
+    }
+  }
+  __syncthreads();
+  uint32_t cur = kNone;
 
+  constexpr int kPer = (int)(kChunk / kBlock);
   for (uint64_t c = c0; c < c1; ++c) {
     const uint32_t sid = chunk_src[c];
     if (sid != cur) {
@@ -392,30 +508,57 @@ __global__ void __launch_bounds__(kBlock) k_scatter(BuildArgs a, const uint32_t*
     }
     const TileDesc& td = a.tiles[s.tile];
     const int4* pts = src_points(a, s, td);
-    const uint32_t* src_idx = s.buf == 0 ? nullptr : a.tmp_idx[s.buf - 1] + td.pt_base + s.pt_off;
+    const uint32_t* src_idx =
+        s.buf == 0 ? nullptr : (s.buf == 1 ? a.tmp_idx[0] : a.tmp_idx[1]) + td.pt_base + s.pt_off;
     const uint64_t first = (c - s.chunk0) << kChunkLog2;
     const uint64_t end = min(first + kChunk, (uint64_t)s.n);
     uint32_t* cursor = s.start + pyr_off(s.d);
-    int4 p[kChunk / kBlock];
+    const int32_t mx = s.min[0], my = s.min[1], mz = s.min[2];
+    const uint32_t lg = s.log2size, d = s.d;
+    const uint32_t* ovfm = s.ovf;
+    const bool priv = s.priv != 0;
+    const uint32_t kbase = (uint32_t)(s.cnt + pyr_off(d) - a.cnt_base);
+    int4 p[kPer];
 #pragma unroll
-    for (int k = 0; k < (int)(kChunk / kBlock); ++k) {
+    for (int k = 0; k < kPer; ++k) {
       const uint64_t i = first + threadIdx.x + (uint64_t)k * kBlock;
       if (i < end) p[k] = ldg_stream(pts + i);
     }
+    // claim every position before the first store that needs one
+    uint32_t pb[kPer], ow[kPer], bit5 = 0, agg = 0;
 #pragma unroll
-    for (int k = 0; k < (int)(kChunk / kBlock); ++k) {
+    for (int k = 0; k < kPer; ++k) {
       const uint64_t i = first + threadIdx.x + (uint64_t)k * kBlock;
       const bool v = i < end;
       const unsigned m = __ballot_sync(0xFFFFFFFFu, v);
+      pb[k] = 0;
+      ow[k] = 0;
       if (!v) continue;
-      const uint32_t bin = src_bin(p[k], s.min, s.log2size, s.d);
-      const unsigned peers = __match_any_sync(m, bin);
-      const int leader = __ffs(peers) - 1;
-      uint32_t base = 0;
-      if ((int)lane == leader) base = atomicAdd(cursor + bin, (uint32_t)__popc(peers));
-      base = __shfl_sync(peers, base, leader);
-      const uint32_t pos = base + __popc(peers & ((1u << lane) - 1u));
-      const bool ovf = (s.ovf[bin >> 5] >> (bin & 31)) & 1u;
+      const uint32_t bin = src_bin(p[k], mx, my, mz, lg, d);
+      bit5 |= (bin & 31u) << (5 * k);
+      if (priv) {
+        const int slot = priv_find(pkeys, kbase + bin + 1u);
+        pb[k] = slot >= 0 ? atomicAdd(&pcur[slot], 1u) : atomicAdd(cursor + bin, 1u);
+      } else {
+        const int leader = __ffs(m) - 1;
+        const uint32_t b0 = __shfl_sync(m, bin, leader);
+        if (__all_sync(m, bin == b0)) {
+          agg |= 1u << k;
+          if ((int)lane == leader) pb[k] = atomicAdd(cursor + bin, (uint32_t)__popc(m));
+        } else {
+          pb[k] = atomicAdd(cursor + bin, 1u);
+        }
+      }
+      ow[k] = ovfm[bin >> 5];
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const uint64_t i = first + threadIdx.x + (uint64_t)k * kBlock;
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, i < end);
+      if (i >= end) continue;
+      uint32_t pos = pb[k];
+      if (agg >> k & 1u) pos = __shfl_sync(m, pos, __ffs(m) - 1) + __popc(m & ((1u << lane) - 1u));
+      const bool ovf = (ow[k] >> ((bit5 >> (5 * k)) & 31u)) & 1u;
       const uint64_t dst = td.pt_base + pos;
       if (ovf) {
         __stcs(ovf_dst + dst, p[k]);
@@ -432,9 +575,15 @@ __global__ void __launch_bounds__(kBlock) k_scatter(BuildArgs a, const uint32_t*
 
 cudaError_t launch_scatter(const BuildArgs& a, const uint32_t* chunk_src, const unsigned long long* n_chunks,
                            uint32_t round, int grid, cudaStream_t st) {
-  k_scatter<<<grid, kBlock, 0, st>>>(a, chunk_src, n_chunks, round);
+  static bool once = [] {
+    cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * kPrivSlots));
+    return true;
+  }();
+  (void)once;
+  k_scatter<<<grid, kBlock, 8 * kPrivSlots, st>>>(a, chunk_src, n_chunks, round);
   return cudaGetLastError();
 }
+
 
 // ---------------------------------------------------------------- node table
 // Breadth-first node list (Section 3.1.3 creates the node list from the

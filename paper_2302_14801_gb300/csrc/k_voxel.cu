@@ -30,31 +30,39 @@ constexpr uint32_t kHp = kSmemBytes / 16;  // pick: key + u64 hash + count
 constexpr uint64_t kNarrowMaxSamples = 0xFFFFFFFFull / 255;  // 32-bit channel sums cannot overflow
 constexpr uint64_t kMask40 = (1ull << 40) - 1;
 
-__device__ __forceinline__ uint32_t table_limit(uint32_t H) { return min(H / 4 * 3, H - kBlock - 1); }
+constexpr uint32_t kProbe = 48;  // longest probe sequence before the table counts as full
+
+// Cells one table pass can be expected to hold (linear probing stays short
+// up to about three quarters full); sizes the partitioning after an overflow.
+__device__ __forceinline__ uint32_t table_capacity(uint32_t H) { return H / 4 * 3; }
 
 __device__ __forceinline__ uint32_t part_of(uint32_t key1, uint32_t mlog) {
   return mlog ? (key1 * 0x85EBCA6Bu) >> (32 - mlog) : 0u;
 }
 
-// Find the slot of key1 (= local cell + 1), inserting it if absent.
-// Returns -1 when the table has reached its fill limit.
-__device__ __forceinline__ int find_or_insert(uint32_t* keys, uint32_t H, uint32_t key1, uint32_t* used,
-                                              uint32_t limit) {
-  uint32_t slot = __umulhi(key1 * 0x9E3779B1u, H);
-  while (true) {
-    const uint32_t k = ((volatile uint32_t*)keys)[slot];
+__device__ __forceinline__ uint32_t home_slot(uint32_t key1, uint32_t H) { return __umulhi(key1 * 0x9E3779B1u, H); }
+
+// Linear probing from `slot`, whose content was observed as k: the slot of
+// key1 (= local cell + 1), inserting it if absent.  Returns -1 when kProbe
+// consecutive slots hold other cells: the table is too full and the item
+// is redone in more partitions.  No shared fill counter is updated, so
+// inserts of different warps never serialise on one address.
+__device__ __forceinline__ int resolve_slot(uint32_t* keys, uint32_t H, uint32_t key1, uint32_t slot, uint32_t k) {
+  for (uint32_t probe = 0; probe < kProbe; ++probe) {
     if (k == key1) return (int)slot;
     if (k == 0u) {
-      if (*((volatile uint32_t*)used) >= limit) return -1;
       const uint32_t old = atomicCAS(&keys[slot], 0u, key1);
-      if (old == 0u) {
-        atomicAdd(used, 1u);
-        return (int)slot;
-      }
-      if (old == key1) return (int)slot;
+      if (old == 0u || old == key1) return (int)slot;
     }
     slot = (slot + 1 == H) ? 0u : slot + 1;
+    k = ((volatile uint32_t*)keys)[slot];
   }
+  return -1;
+}
+
+__device__ __forceinline__ int find_or_insert(uint32_t* keys, uint32_t H, uint32_t key1) {
+  const uint32_t slot = home_slot(key1, H);
+  return resolve_slot(keys, H, key1, slot, ((volatile uint32_t*)keys)[slot]);
 }
 
 struct ItemInfo {
@@ -95,10 +103,22 @@ __device__ __forceinline__ uint32_t key_to_cell(uint32_t key1, const ItemInfo& I
          (((I.kz << 6) | (l >> 12)) << 14);
 }
 
+// floor((s + n/2) / n) for a channel sum s of n 8-bit samples, i.e. the
+// mean rounded half up, which lies in [0, 255].  A single-precision
+// quotient is within 1 of it (relative error ~1e-7 on a value <= 255.5),
+// and one exact integer comparison each way settles it, avoiding a 64-bit
+// integer division.
+__device__ __forceinline__ uint32_t round_mean(uint64_t s, uint64_t n) {
+  const uint64_t num = s + (n >> 1);
+  uint32_t q = (uint32_t)__fdividef((float)num, (float)n);
+  q = q > 255u ? 255u : q;
+  if ((uint64_t)q * n > num) --q;
+  else if ((uint64_t)(q + 1) * n <= num) ++q;
+  return q;
+}
+
 __device__ __forceinline__ uint32_t mean_rgba(uint64_t r, uint64_t g, uint64_t b, uint64_t n) {
-  const uint64_t h = n >> 1;
-  return (uint32_t)((r + h) / n) | ((uint32_t)((g + h) / n) << 8) | ((uint32_t)((b + h) / n) << 16) |
-         0xFF000000u;
+  return round_mean(r, n) | (round_mean(g, n) << 8) | (round_mean(b, n) << 16) | 0xFF000000u;
 }
 
 }  // namespace
@@ -139,7 +159,6 @@ __global__ void __launch_bounds__(kBlock, 1) k_vox(BuildArgs a, VoxLevel v, DevC
   const lod_node_t& c = v.nodes[I.g];
   const bool narrow = MODE == LOD_FILTER && I.leaf && I.n <= kNarrowMaxSamples;
   const uint32_t H = MODE == LOD_PICK ? kHp : (narrow ? kHn : kHw);
-  const uint32_t limit = table_limit(H);
   // shared-memory carve-up (u64 arrays first)
   unsigned long long* A0 = reinterpret_cast<unsigned long long*>(smem);
   unsigned long long* A1 = A0 + H;
@@ -196,44 +215,100 @@ __global__ void __launch_bounds__(kBlock, 1) k_vox(BuildArgs a, VoxLevel v, DevC
 
       if (I.leaf) {
         const uint64_t n = I.n;
-        for (uint64_t base = 0; base < n; base += 4ull * blockDim.x) {
-          if (*((volatile uint32_t*)&s_fail)) break;
-          int4 q[4];
-          uint32_t ix[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const uint64_t i = base + threadIdx.x + (uint64_t)u * blockDim.x;
-            if (i < n) {
-              q[u] = __ldcs(pts + i);
-              if (MODE == LOD_PICK) ix[u] = __ldcs(pidx + i);
+        const uint64_t step = 2ull * blockDim.x;
+        // Lanes of a warp whose points share a cell are merged first (point
+        // order follows the scan in real data, so whole warps often hit one
+        // cell); one leader per distinct cell then probes and updates the
+        // table.  All sums stay exact: at most 32 samples are merged.
+        const uint32_t lane = threadIdx.x & 31u;
+        auto accumulate = [&](uint32_t key1, const int4& q, uint32_t ix) {
+          const unsigned act = __ballot_sync(0xFFFFFFFFu, key1 != 0u);
+          if (key1 == 0u) return;
+          const unsigned peers = __match_any_sync(act, key1);
+          const int leader = __ffs(peers) - 1;
+          const uint32_t n_same = __popc(peers);
+          const uint32_t rgba = (uint32_t)q.w;
+          uint64_t h = 0;
+          uint32_t r = rgba & 255u, g = (rgba >> 8) & 255u, b = (rgba >> 16) & 255u;
+          if (MODE == LOD_PICK) {
+            h = splitmix64(ix);
+            if (n_same > 1) {  // exact 64-bit minimum: high words first, then low
+              const uint32_t hi = __reduce_min_sync(peers, (uint32_t)(h >> 32));
+              const uint32_t lo = __reduce_min_sync(peers, (uint32_t)(h >> 32) == hi ? (uint32_t)h : 0xFFFFFFFFu);
+              h = ((uint64_t)hi << 32) | lo;
             }
+          } else if (n_same > 1) {
+            r = __reduce_add_sync(peers, r);
+            g = __reduce_add_sync(peers, g);
+            b = __reduce_add_sync(peers, b);
           }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const uint64_t i = base + threadIdx.x + (uint64_t)u * blockDim.x;
-            if (i >= n) continue;
-            const uint32_t key1 = point_key1(q[u], I);
-            if (part_of(key1, mlog) != part) continue;
-            const int slot = find_or_insert(keys, H, key1, &s_used, limit);
-            if (slot < 0) {
-              s_fail = 1;
-              continue;
-            }
-            const uint32_t rgba = (uint32_t)q[u].w;
-            const uint64_t r = rgba & 255u, g = (rgba >> 8) & 255u, b = (rgba >> 16) & 255u;
-            if (MODE == LOD_PICK) {
-              atomicMin(&A0[slot], splitmix64(ix[u]));
-              atomicAdd(&cnt32[slot], 1u);
-            } else if (narrow) {
-              atomicAdd(&A0[slot], r | (g << 32));
-              atomicAdd(&A1[slot], b | (1ull << 32));
-            } else {
-              atomicAdd(&A0[slot], r);
-              atomicAdd(&A1[slot], g);
-              atomicAdd(&A2[slot], b);
-              atomicAdd(&cnt32[slot], 1u);
-            }
+          if ((int)lane != leader) return;
+          const int slot = find_or_insert(keys, H, key1);
+          if (slot < 0) {
+            s_fail = 1;
+            return;
           }
+          if (MODE == LOD_PICK) {
+            atomicMin(&A0[slot], h);
+            atomicAdd(&cnt32[slot], n_same);
+          } else if (narrow) {
+            atomicAdd(&A0[slot], (uint64_t)r | ((uint64_t)g << 32));
+            atomicAdd(&A1[slot], (uint64_t)b | ((uint64_t)n_same << 32));
+          } else {
+            atomicAdd(&A0[slot], (uint64_t)r);
+            atomicAdd(&A1[slot], (uint64_t)g);
+            atomicAdd(&A2[slot], (uint64_t)b);
+            atomicAdd(&cnt32[slot], n_same);
+          }
+        };
+        // Software pipeline over pairs of points: the loads of the next pair
+        // are in flight while the current pair is hashed and accumulated,
+        // and both of a pair's first probes are issued before either is
+        // resolved.
+        int4 q0 = make_int4(0, 0, 0, 0), q1 = q0;
+        uint32_t x0 = 0, x1 = 0;
+        {
+          const uint64_t a0 = threadIdx.x, a1 = a0 + blockDim.x;
+          if (a0 < n) {
+            q0 = __ldcs(pts + a0);
+            if (MODE == LOD_PICK) x0 = __ldcs(pidx + a0);
+          }
+          if (a1 < n) {
+            q1 = __ldcs(pts + a1);
+            if (MODE == LOD_PICK) x1 = __ldcs(pidx + a1);
+          }
+        }
+        for (uint64_t base = 0; base < n; base += step) {
+          const uint64_t a0 = base + threadIdx.x, a1 = a0 + blockDim.x;
+          const uint64_t b0 = a0 + step, b1 = a1 + step;
+          int4 r0 = q0, r1 = q1;
+          uint32_t y0 = 0, y1 = 0;
+          if (b0 < n) {
+            r0 = __ldcs(pts + b0);
+            if (MODE == LOD_PICK) y0 = __ldcs(pidx + b0);
+          }
+          if (b1 < n) {
+            r1 = __ldcs(pts + b1);
+            if (MODE == LOD_PICK) y1 = __ldcs(pidx + b1);
+          }
+          // the whole warp leaves together: accumulate() uses full-warp
+          // collectives, so no lane may stop while its neighbours go on
+          if (__any_sync(0xFFFFFFFFu, *((volatile uint32_t*)&s_fail) != 0u)) break;
+          uint32_t k0 = 0u, k1 = 0u;
+          if (a0 < n) {
+            k0 = point_key1(q0, I);
+            if (part_of(k0, mlog) != part) k0 = 0u;
+          }
+          if (a1 < n) {
+            k1 = point_key1(q1, I);
+            if (part_of(k1, mlog) != part) k1 = 0u;
+          }
+          accumulate(k0, q0, x0);
+          accumulate(k1, q1, x1);
+          q0 = r0;
+          q1 = r1;
+          x0 = y0;
+          x1 = y1;
         }
       } else {
         // inner child: its voxels are the staged records of its own children
@@ -249,7 +324,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_vox(BuildArgs a, VoxLevel v, DevC
             if (part == 0) dst[i] = vr;  // publish the child's voxel (idempotent)
             const uint32_t key1 = voxel_key1((uint32_t)vr.x);
             if (part_of(key1, mlog) != part) continue;
-            const int slot = find_or_insert(keys, H, key1, &s_used, limit);
+            const int slot = find_or_insert(keys, H, key1);
             if (slot < 0) {
               s_fail = 1;
               continue;
@@ -272,7 +347,14 @@ __global__ void __launch_bounds__(kBlock, 1) k_vox(BuildArgs a, VoxLevel v, DevC
         failed = true;
         break;
       }
-      // extract this partition's occupied cells into staging
+      // count this partition's occupied cells, then extract them into staging
+      {
+        uint32_t mine = 0;
+        for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) mine += keys[i] != 0u ? 1u : 0u;
+        mine = __reduce_add_sync(0xFFFFFFFFu, mine);
+        if ((threadIdx.x & 31u) == 0 && mine) atomicAdd(&s_used, mine);
+      }
+      __syncthreads();
       const uint32_t used = s_used;
       if (mlog == 0 && threadIdx.x == 0) {
         s_stage = atomicAdd(v.stage_used, (unsigned long long)used);
@@ -296,7 +378,12 @@ __global__ void __launch_bounds__(kBlock, 1) k_vox(BuildArgs a, VoxLevel v, DevC
         int4 rec;
         rec.x = (int)cell;
         if (MODE == LOD_PICK) {
-          const uint32_t best = (uint32_t)splitmix64_inverse(A0[i]);
+          const uint64_t inv = splitmix64_inverse(A0[i]);
+          const uint32_t best = (uint32_t)inv;
+          if (inv >= td.n) {  // cannot happen for a cell that received a sample
+            atomicOr(&ctr->error, kErrInternal);
+            continue;
+          }
           rec.y = (int)__ldg(reinterpret_cast<const uint32_t*>(td.in) + 4ull * best + 3);
           rec.z = (int)cnt32[i];
           rec.w = (int)best;
@@ -326,9 +413,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_vox(BuildArgs a, VoxLevel v, DevC
       out_total += used;
       __syncthreads();
     }
+    if (threadIdx.x == 0) atomicAdd(&ctr->vox_passes, (unsigned long long)P);
     if (!failed) break;
+    if (threadIdx.x == 0 && mlog == 0) atomicAdd(&ctr->vox_retries, 1ull);
     // more partitions: first try two, then enough for the worst case
-    const uint32_t need = (uint32_t)((cap + limit - 1) / limit);
+    const uint32_t need = (uint32_t)((cap + table_capacity(H) - 1) / table_capacity(H));
     uint32_t bound = 0;
     while ((1u << bound) < need) ++bound;
     mlog = mlog == 0 ? 1u : max(mlog + 1, bound);

@@ -34,7 +34,7 @@ EXPORTED = [
     "lod_result_copy_to_host", "lod_result_device_bytes", "lod_free", "lod_error_string",
     "lod_server_create", "lod_submit", "lod_poll", "lod_wait", "lod_server_bytes_in_use",
     "lod_server_destroy", "lod_profile_enable", "lod_profile_reset", "lod_profile_read", "lod_launch_count",
-    "lod_root_cubes_noalloc",
+    "lod_root_cubes_noalloc", "lod_set_tuning", "lod_get_tuning",
 ]
 
 
@@ -61,6 +61,11 @@ class View(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("root_depth", ctypes.c_uint32), ("stream_ctas_per_sm", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 6)]
 
 
 class KernelStat(ctypes.Structure):
@@ -108,6 +113,8 @@ def _load():
         "lod_profile_read": (i, [P(KernelStat), u32, P(u32)]),
         "lod_launch_count": (u64, []),
         "lod_root_cubes_noalloc": (i, [P(vp), P(u64), u32, vp, vp]),
+        "lod_set_tuning": (i, [P(Tuning)]),
+        "lod_get_tuning": (i, [P(Tuning)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -166,6 +173,17 @@ def profile_read() -> dict:
     _check(lib().lod_profile_read(arr, n.value, ctypes.byref(n)), "lod_profile_read")
     return {arr[i].name.decode(): {"launches": int(arr[i].launches), "total_ms": float(arr[i].total_ms),
                                    "alg_bytes": float(arr[i].alg_bytes)} for i in range(n.value)}
+
+
+def set_tuning(root_depth: int = 0, stream_ctas_per_sm: int = 0) -> None:
+    """Process-wide speed knobs (never change results); 0 = default."""
+    _check(lib().lod_set_tuning(ctypes.byref(Tuning(int(root_depth), int(stream_ctas_per_sm)))), "lod_set_tuning")
+
+
+def get_tuning() -> dict:
+    t = Tuning()
+    _check(lib().lod_get_tuning(ctypes.byref(t)), "lod_get_tuning")
+    return {"root_depth": t.root_depth, "stream_ctas_per_sm": t.stream_ctas_per_sm}
 
 
 def launch_count() -> int:

@@ -149,6 +149,20 @@ def test_indoor_dense_clusters_refinement(lod, mode, T):
     parity(lod, synth.indoor(3_000_000, seed=3, n_prims=256), T, mode)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_volumetric_octants_overflow_tables(lod, mode):
+    # 400k points uniform in a cube with T = 150k: every child octant of the
+    # root holds ~50k distinct cells, more than one shared-memory table pass
+    # can take, so items are redone in hash partitions (and the parent of
+    # inner children merges wide sums).
+    rng = np.random.default_rng(31)
+    pts = np.empty((400_000, 4), np.int32)
+    pts[:, :3] = rng.integers(0, 1 << 16, size=(400_000, 3))
+    pts[:, 3] = rng.integers(-(2**31), 2**31, size=400_000)
+    parity(lod, pts, 150_000, mode)
+    parity(lod, pts, 20_000, mode)
+
+
 def test_keep_index_filtered(lod):
     pts = synth.sphere(200_000, seed=12)
     got = gpu_build(lod, pts, 5000, 0, keep_index=True)
