@@ -76,6 +76,10 @@ struct BuildArgs {
   uint32_t* out_idx;   // original input index per leaf point (or null)
   int4* tmp[2];        // refinement ping-pong buffers (absolute positions)
   uint32_t* tmp_idx[2];
+  int4* wide;          // when input indices are kept: the scatter writes each
+                       // leaf point as one full 32-byte sector {point},{index}
+                       // here (two int4 per position), and the bottom voxel
+                       // pass writes out / out_idx contiguously from it
   // privatised counting of large grids: counters are keyed by their index
   // relative to cnt_base; each CTA leaves its (key, count) list in lists
   uint32_t* cnt_base;      // count region of the round's pool

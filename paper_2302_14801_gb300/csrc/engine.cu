@@ -377,8 +377,11 @@ uint64_t estimate_build_bytes(uint64_t n, const lod_params_t& p) {
   const uint32_t d = choose_root_depth(n, (uint32_t)T, 32, 32);
   const uint64_t pool = (2 * pyr_size(d) + ipow8(d) + ipow8(d) / 32 + 1) * 4;
   const uint64_t nodes = 64 + 16 * ((n + T - 1) / T);
-  // result + one refinement buffer + two staging levels + node aux + pool
-  return estimate_result_bytes(n, p) + n * 20 + n * 40 + nodes * sizeof(NodeAux) + pool + (16u << 20);
+  // result + one refinement buffer + two staging levels + node aux + pool,
+  // plus the 32-byte leaf staging of modes that keep input indices
+  const bool keep_idx = p.mode == LOD_PICK || (p.flags & LOD_FLAG_LEAF_INDEX);
+  return estimate_result_bytes(n, p) + n * 20 + n * 40 + (keep_idx ? n * 32 : 0) + nodes * sizeof(NodeAux) + pool +
+         (16u << 20);
 }
 
 // Keep freed blocks of the device's stream-ordered pool instead of returning
@@ -528,6 +531,12 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
   A.out_idx = want_idx ? d_index.as<uint32_t>() : nullptr;
   A.lists = d_lists.as<uint2>();
   A.list_len = d_llen.as<uint32_t>();
+  // modes that keep input indices stage each leaf point as one 32-byte record
+  DevBuf d_wide(st);
+  if (want_idx) {
+    LOD_CK(d_wide.alloc(M * 32));
+    A.wide = d_wide.as<int4>();
+  }
   DevBuf d_diag(st);
   if (debug_stats()) {
     LOD_CK(d_diag.alloc(4 * sizeof(unsigned long long)));
@@ -834,6 +843,24 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
   if (have_top) {
     vl.dense = d_dense.as<int4>();
     LOD_LAUNCH("publish_top", 32.0 * V_top, launch_copy_items(A, vl, st));
+  }
+  if (A.wide) {
+    // a root that is a leaf is no voxel item: publish its points here
+    std::vector<uint32_t> leaf_roots;
+    uint32_t max_n = 0;
+    uint64_t moved = 0;
+    for (uint32_t t = 0; t < nt; ++t)
+      if (n_levels[t] == 1 && td[t].n > 0) {
+        leaf_roots.push_back(t);
+        max_n = std::max(max_n, td[t].n);
+        moved += td[t].n;
+      }
+    if (!leaf_roots.empty()) {
+      LOD_CK(d_itemp.alloc(leaf_roots.size() * 4));
+      LOD_CK(up_.put(d_itemp.p, leaf_roots.data(), leaf_roots.size() * 4));
+      LOD_LAUNCH("publish_leaf_roots", 52.0 * moved,
+                 launch_unwide(A, d_itemp.as<uint32_t>(), (uint32_t)leaf_roots.size(), max_n, st));
+    }
   }
   std::vector<unsigned long long> tvox(nt);
   LOD_CK(cudaMemcpyAsync(tvox.data(), d_tvox.p, nt * 8, cudaMemcpyDeviceToHost, st));

@@ -6,11 +6,15 @@
 // 128-bit loads in 4096-point chunks; each CTA owns a contiguous run of
 // chunks so that per-source state (a shared-memory histogram, a reduction)
 // is flushed only when the source changes.  Counting grids of up to 8^4
-// cells are privatised in shared memory; larger first grids (up to 256^3,
-// which stays resident in the 129 MB L2) use warp-aggregated global
-// atomics.  Grid pyramids (per-level sums and exclusive-scan starts) are
-// built in 4-level blocks in shared memory.  No kernel ever waits on
-// another CTA.
+// cells use a dense shared-memory histogram; larger first grids (up to
+// 256^3 cells) count through a per-CTA shared-memory hash table of the
+// cells the CTA's chunks touch, whose (cell, count) list is flushed with
+// one global atomic per distinct cell and reused by the scatter to claim
+// one block of positions per cell.  Points of cells that miss the table
+// fall back to warp-aggregated global atomics.  Grid pyramids (per-level
+// sums and exclusive-scan starts) are built in 4-level blocks in shared
+// memory.  With kept input indices the scatter writes one full 32-byte
+// sector per point.  No kernel ever waits on another CTA.
 #include <climits>
 
 #include "common.cuh"
@@ -269,10 +273,17 @@ __global__ void __launch_bounds__(kBlock) k_count(BuildArgs a, const uint32_t* _
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       const uint64_t i = first + threadIdx.x + (uint64_t)k * kBlock;
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, i < end);
       if (i >= end) continue;
       const uint32_t key = kbase + src_bin(p[k], mx, my, mz, lg, d);
       const int slot = priv_insert(pkeys, key + 1u);
-      if (slot >= 0) {
+      // a warp whose points all share one cell (scan-ordered input) adds once
+      const int leader = __ffs(m) - 1;
+      const int s0 = __shfl_sync(m, slot, leader);
+      const bool same = __all_sync(m, slot == s0);
+      if (same && s0 >= 0) {
+        if ((int)lane_id() == leader) atomicAdd(&pcnt[s0], (uint32_t)__popc(m));
+      } else if (slot >= 0) {
         atomicAdd(&pcnt[slot], 1u);
       } else {
         atomicAdd(a.cnt_base + key, 1u);  // table full: count globally
@@ -538,7 +549,14 @@ __global__ void __launch_bounds__(kBlock) k_scatter(BuildArgs a, const uint32_t*
       bit5 |= (bin & 31u) << (5 * k);
       if (priv) {
         const int slot = priv_find(pkeys, kbase + bin + 1u);
-        pb[k] = slot >= 0 ? atomicAdd(&pcur[slot], 1u) : atomicAdd(cursor + bin, 1u);
+        const int leader = __ffs(m) - 1;
+        const int s0 = __shfl_sync(m, slot, leader);
+        if (__all_sync(m, slot == s0) && s0 >= 0) {
+          agg |= 1u << k;  // one claim for the whole warp
+          if ((int)lane == leader) pb[k] = atomicAdd(&pcur[s0], (uint32_t)__popc(m));
+        } else {
+          pb[k] = slot >= 0 ? atomicAdd(&pcur[slot], 1u) : atomicAdd(cursor + bin, 1u);
+        }
       } else {
         const int leader = __ffs(m) - 1;
         const uint32_t b0 = __shfl_sync(m, bin, leader);
@@ -560,14 +578,18 @@ __global__ void __launch_bounds__(kBlock) k_scatter(BuildArgs a, const uint32_t*
       if (agg >> k & 1u) pos = __shfl_sync(m, pos, __ffs(m) - 1) + __popc(m & ((1u << lane) - 1u));
       const bool ovf = (ow[k] >> ((bit5 >> (5 * k)) & 31u)) & 1u;
       const uint64_t dst = td.pt_base + pos;
+      const uint32_t idx = a.out_idx ? (src_idx ? src_idx[i] : (uint32_t)i) : 0u;
       if (ovf) {
         __stcs(ovf_dst + dst, p[k]);
+        if (a.out_idx) ovf_idx[dst] = idx;
+      } else if (a.wide) {
+        // one full 32-byte sector per point and no separate 4-byte index
+        // write (isolated sub-sector writes are the costliest kind)
+        __stcs(a.wide + 2 * dst, p[k]);
+        __stcs(a.wide + 2 * dst + 1, make_int4((int)idx, 0, 0, 0));
       } else {
         __stcs(a.out + dst, p[k]);
-      }
-      if (a.out_idx) {
-        const uint32_t idx = src_idx ? src_idx[i] : (uint32_t)i;
-        (ovf ? ovf_idx : a.out_idx)[dst] = idx;
+        if (a.out_idx) a.out_idx[dst] = idx;
       }
     }
   }

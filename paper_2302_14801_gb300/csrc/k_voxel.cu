@@ -179,8 +179,12 @@ __global__ void __launch_bounds__(kBlock, 1) k_vox(BuildArgs a, VoxLevel v, DevC
   const uint64_t cap = umin64(I.n, kOctCells);
   uint32_t mlog = 0;
   uint64_t out_total = 0;
-  const int4* pts = a.out + td.pt_base + c.point_offset;
-  const uint32_t* pidx = (MODE == LOD_PICK) ? a.out_idx + td.pt_base + c.point_offset : nullptr;
+  const uint64_t pbase = td.pt_base + c.point_offset;
+  const int4* pts = a.out + pbase;
+  const uint32_t* pidx = (MODE == LOD_PICK) ? a.out_idx + pbase : nullptr;
+  // with kept indices the leaf is read from the 32-byte staging records and
+  // published to the point / index arrays here, contiguously
+  const int4* wsrc = a.wide ? a.wide + 2 * pbase : nullptr;
   const uint32_t nch = __popc(c.child_mask);
   const uint64_t fc = td.node_base + (c.first_child == kNone ? 0 : c.first_child);
 
@@ -224,25 +228,24 @@ __global__ void __launch_bounds__(kBlock, 1) k_vox(BuildArgs a, VoxLevel v, DevC
         auto accumulate = [&](uint32_t key1, const int4& q, uint32_t ix) {
           const unsigned act = __ballot_sync(0xFFFFFFFFu, key1 != 0u);
           if (key1 == 0u) return;
-          const unsigned peers = __match_any_sync(act, key1);
-          const int leader = __ffs(peers) - 1;
-          const uint32_t n_same = __popc(peers);
           const uint32_t rgba = (uint32_t)q.w;
           uint64_t h = 0;
           uint32_t r = rgba & 255u, g = (rgba >> 8) & 255u, b = (rgba >> 16) & 255u;
+          uint32_t n_same = 1;
           if (MODE == LOD_PICK) {
+            // a 64-bit minimum is cheap to contend for (most updates lose the
+            // comparison), so pick mode skips the merge
             h = splitmix64(ix);
-            if (n_same > 1) {  // exact 64-bit minimum: high words first, then low
-              const uint32_t hi = __reduce_min_sync(peers, (uint32_t)(h >> 32));
-              const uint32_t lo = __reduce_min_sync(peers, (uint32_t)(h >> 32) == hi ? (uint32_t)h : 0xFFFFFFFFu);
-              h = ((uint64_t)hi << 32) | lo;
+          } else {
+            const unsigned peers = __match_any_sync(act, key1);
+            n_same = __popc(peers);
+            if (n_same > 1) {
+              r = __reduce_add_sync(peers, r);
+              g = __reduce_add_sync(peers, g);
+              b = __reduce_add_sync(peers, b);
             }
-          } else if (n_same > 1) {
-            r = __reduce_add_sync(peers, r);
-            g = __reduce_add_sync(peers, g);
-            b = __reduce_add_sync(peers, b);
+            if ((int)lane != __ffs(peers) - 1) return;
           }
-          if ((int)lane != leader) return;
           const int slot = find_or_insert(keys, H, key1);
           if (slot < 0) {
             s_fail = 1;
@@ -265,35 +268,43 @@ __global__ void __launch_bounds__(kBlock, 1) k_vox(BuildArgs a, VoxLevel v, DevC
         // are in flight while the current pair is hashed and accumulated,
         // and both of a pair's first probes are issued before either is
         // resolved.
+        auto load = [&](uint64_t i, int4& q, uint32_t& x) {
+          if (wsrc) {
+            q = __ldcs(wsrc + 2 * i);
+            x = (uint32_t)__ldcs(wsrc + 2 * i + 1).x;
+          } else {
+            q = __ldcs(pts + i);
+            if (MODE == LOD_PICK) x = __ldcs(pidx + i);
+          }
+        };
+        const bool publish = wsrc != nullptr && part == 0;
         int4 q0 = make_int4(0, 0, 0, 0), q1 = q0;
         uint32_t x0 = 0, x1 = 0;
         {
           const uint64_t a0 = threadIdx.x, a1 = a0 + blockDim.x;
-          if (a0 < n) {
-            q0 = __ldcs(pts + a0);
-            if (MODE == LOD_PICK) x0 = __ldcs(pidx + a0);
-          }
-          if (a1 < n) {
-            q1 = __ldcs(pts + a1);
-            if (MODE == LOD_PICK) x1 = __ldcs(pidx + a1);
-          }
+          if (a0 < n) load(a0, q0, x0);
+          if (a1 < n) load(a1, q1, x1);
         }
         for (uint64_t base = 0; base < n; base += step) {
           const uint64_t a0 = base + threadIdx.x, a1 = a0 + blockDim.x;
           const uint64_t b0 = a0 + step, b1 = a1 + step;
           int4 r0 = q0, r1 = q1;
           uint32_t y0 = 0, y1 = 0;
-          if (b0 < n) {
-            r0 = __ldcs(pts + b0);
-            if (MODE == LOD_PICK) y0 = __ldcs(pidx + b0);
-          }
-          if (b1 < n) {
-            r1 = __ldcs(pts + b1);
-            if (MODE == LOD_PICK) y1 = __ldcs(pidx + b1);
-          }
+          if (b0 < n) load(b0, r0, y0);
+          if (b1 < n) load(b1, r1, y1);
           // the whole warp leaves together: accumulate() uses full-warp
           // collectives, so no lane may stop while its neighbours go on
           if (__any_sync(0xFFFFFFFFu, *((volatile uint32_t*)&s_fail) != 0u)) break;
+          if (publish) {  // idempotent: a retried item writes the same values
+            if (a0 < n) {
+              a.out[pbase + a0] = q0;
+              a.out_idx[pbase + a0] = x0;
+            }
+            if (a1 < n) {
+              a.out[pbase + a1] = q1;
+              a.out_idx[pbase + a1] = x1;
+            }
+          }
           uint32_t k0 = 0u, k1 = 0u;
           if (a0 < n) {
             k0 = point_key1(q0, I);
@@ -536,6 +547,28 @@ __global__ void __launch_bounds__(256) k_copy_items(BuildArgs a, VoxLevel v) {
 cudaError_t launch_copy_items(const BuildArgs& a, const VoxLevel& v, cudaStream_t st) {
   if (!v.n_items) return cudaSuccess;
   k_copy_items<<<v.n_items, 256, 0, st>>>(a, v);
+  return cudaGetLastError();
+}
+
+// Publish the leaf points and indices of tiles whose root is a leaf (no
+// voxel pass reads those points): blockIdx.y selects the tile.
+__global__ void __launch_bounds__(256) k_unwide(BuildArgs a, const uint32_t* __restrict__ tiles) {
+  const TileDesc& td = a.tiles[tiles[blockIdx.y]];
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < td.n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t p = td.pt_base + i;
+    a.out[p] = __ldcs(a.wide + 2 * p);
+    a.out_idx[p] = (uint32_t)__ldcs(a.wide + 2 * p + 1).x;
+  }
+}
+
+cudaError_t launch_unwide(const BuildArgs& a, const uint32_t* tiles, uint32_t n_tiles, uint32_t max_points,
+                          cudaStream_t st) {
+  if (!n_tiles) return cudaSuccess;
+  const uint32_t gx = (uint32_t)umin64(((uint64_t)max_points + 255) / 256, 1024);
+  for (uint32_t t0 = 0; t0 < n_tiles; t0 += 65535) {
+    const uint32_t m = n_tiles - t0 < 65535 ? n_tiles - t0 : 65535;
+    k_unwide<<<dim3(gx ? gx : 1, m), 256, 0, st>>>(a, tiles + t0);
+  }
   return cudaGetLastError();
 }
 
