@@ -42,6 +42,8 @@ WORKLOADS = {
     "aerial50m": ("aerial", 50_000_000, 2, 50000),
     "sphere1m": ("sphere", 1_000_000, 1, 50000),
     "indoor100m": ("indoor", 100_000_000, 3, 50000),
+    # small case of the aerial workload (inputs still larger than L2) for profiler captures
+    "aerial12m": ("aerial", 12_000_000, 2, 50000),
 }
 METRIC = "LOD build M points/s (filtered & sample-pick), % HBM roofline; tile p50/p99 ms"
 

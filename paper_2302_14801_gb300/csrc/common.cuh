@@ -149,33 +149,6 @@ __host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   return z ^ (z >> 31);
 }
 
-// Multiplicative inverse of an odd a modulo 2^64 by Newton's iteration
-// x <- x (2 - a x), which doubles the number of correct low bits each step.
-__host__ __device__ constexpr uint64_t inv_mod64(uint64_t a) {
-  uint64_t x = a;  // correct to 3 bits for odd a
-  for (int i = 0; i < 6; ++i) x *= 2 - a * x;
-  return x;
-}
-
-// Inverse of y = x ^ (x >> s) on 64 bits.
-__host__ __device__ __forceinline__ uint64_t unxorshift(uint64_t y, int s) {
-  uint64_t x = y;
-  for (int i = s; i < 64; i += s) x = y ^ (x >> s);
-  return x;
-}
-
-// splitmix64 is a bijection; this undoes it, step by step in reverse.
-__host__ __device__ __forceinline__ uint64_t splitmix64_inverse(uint64_t h) {
-  constexpr uint64_t i2 = inv_mod64(0x94D049BB133111EBull);
-  constexpr uint64_t i1 = inv_mod64(0xBF58476D1CE4E5B9ull);
-  uint64_t z = unxorshift(h, 31);
-  z *= i2;
-  z = unxorshift(z, 27);
-  z *= i1;
-  z = unxorshift(z, 30);
-  return z - 0x9E3779B97F4A7C15ull;
-}
-
 // 128^3 grid coordinate of an offset d (0 <= d < 2^L) inside a cube of edge
 // 2^L (Section 3.2: every node samples onto a 128^3 grid).
 __device__ __forceinline__ uint32_t grid_coord(uint32_t d, uint32_t L) {
@@ -183,5 +156,19 @@ __device__ __forceinline__ uint32_t grid_coord(uint32_t d, uint32_t L) {
 }
 
 __device__ __forceinline__ int4 ldg_stream(const int4* p) { return __ldcs(p); }
+
+// One 32-byte staging record {point, index, 0, 0, 0} moved with a single
+// 256-bit access (sm_100 and later), evict-first.  p is 32-byte aligned.
+__device__ __forceinline__ void st_wide(int4* p, const int4& q, uint32_t idx) {
+  asm volatile("st.global.cs.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %6, %6};" ::"l"(p), "r"(q.x), "r"(q.y),
+               "r"(q.z), "r"(q.w), "r"(idx), "r"(0u)
+               : "memory");
+}
+__device__ __forceinline__ void ld_wide(const int4* p, int4& q, uint32_t& idx) {
+  uint32_t u0, u1, u2;
+  asm("ld.global.cs.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(q.x), "=r"(q.y), "=r"(q.z), "=r"(q.w), "=r"(idx), "=r"(u0), "=r"(u1), "=r"(u2)
+               : "l"(p));
+}
 
 }  // namespace lodk

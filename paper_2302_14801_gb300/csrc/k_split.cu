@@ -28,14 +28,22 @@ __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
 // Morton cell of point p inside a source grid (8^d cells under a cube of
 // edge 2^log2size with min corner mn).
+// Grids have d <= 8, so each coordinate has at most 8 bits and the shift
+// log2size - d is at most 31.
+__device__ __forceinline__ uint32_t spread3_8(uint32_t v) {
+  v = (v | (v << 8)) & 0x0000F00Fu;
+  v = (v | (v << 4)) & 0x000C30C3u;
+  v = (v | (v << 2)) & 0x00249249u;
+  return v;
+}
 __device__ __forceinline__ uint32_t src_bin(const int4& p, int32_t mx, int32_t my, int32_t mz, uint32_t log2size,
                                             uint32_t d) {
   if (d == 0) return 0;
   const uint32_t sh = log2size - d;
-  const uint32_t ux = (uint32_t)((uint64_t)((uint32_t)p.x - (uint32_t)mx) >> sh);
-  const uint32_t uy = (uint32_t)((uint64_t)((uint32_t)p.y - (uint32_t)my) >> sh);
-  const uint32_t uz = (uint32_t)((uint64_t)((uint32_t)p.z - (uint32_t)mz) >> sh);
-  return morton3(ux, uy, uz);
+  const uint32_t ux = ((uint32_t)p.x - (uint32_t)mx) >> sh;
+  const uint32_t uy = ((uint32_t)p.y - (uint32_t)my) >> sh;
+  const uint32_t uz = ((uint32_t)p.z - (uint32_t)mz) >> sh;
+  return (spread3_8(ux) << 2) | (spread3_8(uy) << 1) | spread3_8(uz);
 }
 
 // Compact every third bit (inverse of spread3) for 8 output bits.
@@ -52,6 +60,68 @@ __device__ __forceinline__ uint32_t compact3(uint32_t v) {
 __device__ __forceinline__ const int4* src_points(const BuildArgs& a, const SrcDesc& s, const TileDesc& t) {
   if (s.buf == 0) return t.in;  // round 0 reads the caller's input, index = input index
   return (s.buf == 1 ? a.tmp[0] : a.tmp[1]) + t.pt_base + s.pt_off;
+}
+
+// ------------------------------------------------------- chunk staging
+// Each thread copies its own records of the NEXT chunk from global to
+// shared memory with asynchronous copies (cp.async, L2 only) while it
+// works on the current one, so the DRAM latency of one chunk hides behind
+// the atomics and stores of the previous one.  A thread only ever reads
+// the staging slots it wrote itself, so no CTA barrier is needed: the
+// wait_group of the issuing thread makes its copies visible to it.
+
+// L2 policies: the streamed input is evicted first, so that the partly
+// written sectors of the scatter's output runs stay in L2 until they are
+// complete (a sector evicted half written costs a DRAM read-modify-write).
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t l2_evict_last() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void st_keep(int4* p, const int4& q, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.s32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(q.x), "r"(q.y), "r"(q.z),
+               "r"(q.w), "l"(pol)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t dep, uint64_t pol) {
+  // `dep` is an opaque zero computed from the values this thread last read
+  // from the same slots; as an operand it makes the copy wait for those
+  // reads (no write-after-read on the slot)
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2, %3;\n" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(16u + dep), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// An opaque zero that depends on v (the compiler cannot fold it away).
+__device__ __forceinline__ uint32_t opaque_zero(uint32_t v) {
+  uint32_t z;
+  asm volatile("and.b32 %0, %1, 0;" : "=r"(z) : "r"(v));
+  return z;
+}
+
+// Issue the staging copies of this thread's records of chunk c.
+__device__ __forceinline__ void stage_chunk(const BuildArgs& a, const uint32_t* __restrict__ chunk_src, uint64_t c,
+                                            int4* stage, uint32_t dep, uint64_t pol) {
+  const SrcDesc& s = a.srcs[chunk_src[c]];
+  const TileDesc& td = a.tiles[s.tile];
+  const int4* pts = src_points(a, s, td);
+  const uint64_t first = (c - s.chunk0) << kChunkLog2;
+  const uint64_t end = min(first + kChunk, (uint64_t)s.n);
+#pragma unroll
+  for (uint32_t k = 0; k < kChunk / kBlock; ++k) {
+    const uint64_t i = first + threadIdx.x + (uint64_t)k * kBlock;
+    if (i < end) cp_async16(stage + k * kBlock + threadIdx.x, pts + i, dep, pol);
+  }
+  cp_async_commit();
 }
 
 // Depth of a refinement grid for a cell of n points (surfaces shrink by
@@ -202,14 +272,15 @@ __device__ __forceinline__ int priv_find(const uint32_t* keys, uint32_t key1) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(kBlock) k_count(BuildArgs a, const uint32_t* __restrict__ chunk_src,
+__global__ void __launch_bounds__(kBlock, 1) k_count(BuildArgs a, const uint32_t* __restrict__ chunk_src,
                                                   const unsigned long long* __restrict__ n_chunks_p) {
   __shared__ uint32_t hist[kSmemBins];
   __shared__ SrcDesc s;
   __shared__ uint32_t s_list;
-  extern __shared__ uint32_t ptab[];  // kPrivSlots keys, then kPrivSlots counts
+  extern __shared__ __align__(16) uint32_t ptab[];  // kPrivSlots keys, kPrivSlots counts, chunk stage
   uint32_t* pkeys = ptab;
   uint32_t* pcnt = ptab + kPrivSlots;
+  int4* stage = reinterpret_cast<int4*>(ptab + 2 * kPrivSlots);
   const uint64_t n_chunks = *n_chunks_p;
   const uint64_t per = (n_chunks + gridDim.x - 1) / gridDim.x;
   const uint64_t c0 = (uint64_t)blockIdx.x * per;
@@ -236,6 +307,8 @@ __global__ void __launch_bounds__(kBlock) k_count(BuildArgs a, const uint32_t* _
   };
 
   constexpr int kPer = (int)(kChunk / kBlock);
+  const uint64_t pol_in = l2_evict_first();
+  if (c0 < c1) stage_chunk(a, chunk_src, c0, stage, 0u, pol_in);
   for (uint64_t c = c0; c < c1; ++c) {
     const uint32_t sid = chunk_src[c];
     if (sid != cur) {
@@ -249,23 +322,23 @@ __global__ void __launch_bounds__(kBlock) k_count(BuildArgs a, const uint32_t* _
         for (uint32_t b = threadIdx.x; b < nbins; b += blockDim.x) hist[b] = 0;
       __syncthreads();
     }
-    const TileDesc& td = a.tiles[s.tile];
-    const int4* pts = src_points(a, s, td);
     const uint64_t first = (c - s.chunk0) << kChunkLog2;
     const uint64_t end = min(first + kChunk, (uint64_t)s.n);
     const int32_t mx = s.min[0], my = s.min[1], mz = s.min[2];
     const uint32_t lg = s.log2size, d = s.d;
-    int4 p[kPer];
+    uint32_t bin[kPer];
+    cp_async_wait_all();
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       const uint64_t i = first + threadIdx.x + (uint64_t)k * kBlock;
-      if (i < end) p[k] = ldg_stream(pts + i);
+      bin[k] = i < end ? src_bin(stage[k * kBlock + threadIdx.x], mx, my, mz, lg, d) : 0u;
     }
+    if (c + 1 < c1) stage_chunk(a, chunk_src, c + 1, stage, opaque_zero(bin[0] ^ bin[1] ^ bin[2] ^ bin[3]), pol_in);
     if (smem) {
 #pragma unroll
       for (int k = 0; k < kPer; ++k) {
         const uint64_t i = first + threadIdx.x + (uint64_t)k * kBlock;
-        if (i < end) atomicAdd(&hist[src_bin(p[k], mx, my, mz, lg, d)], 1u);
+        if (i < end) atomicAdd(&hist[bin[k]], 1u);
       }
       continue;
     }
@@ -275,7 +348,7 @@ __global__ void __launch_bounds__(kBlock) k_count(BuildArgs a, const uint32_t* _
       const uint64_t i = first + threadIdx.x + (uint64_t)k * kBlock;
       const unsigned m = __ballot_sync(0xFFFFFFFFu, i < end);
       if (i >= end) continue;
-      const uint32_t key = kbase + src_bin(p[k], mx, my, mz, lg, d);
+      const uint32_t key = kbase + bin[k];
       const int slot = priv_insert(pkeys, key + 1u);
       // a warp whose points all share one cell (scan-ordered input) adds once
       const int leader = __ffs(m) - 1;
@@ -318,11 +391,11 @@ __global__ void __launch_bounds__(kBlock) k_count(BuildArgs a, const uint32_t* _
 cudaError_t launch_count(const BuildArgs& a, const uint32_t* chunk_src, const unsigned long long* n_chunks,
                          int grid, cudaStream_t st) {
   static bool once = [] {
-    cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * kPrivSlots));
+    cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * kPrivSlots + 16 * kChunk));
     return true;
   }();
   (void)once;
-  k_count<<<grid, kBlock, 8 * kPrivSlots, st>>>(a, chunk_src, n_chunks);
+  k_count<<<grid, kBlock, 8 * kPrivSlots + 16 * kChunk, st>>>(a, chunk_src, n_chunks);
   return cudaGetLastError();
 }
 
@@ -482,9 +555,13 @@ __global__ void __launch_bounds__(kBlock) k_scatter(BuildArgs a, const uint32_t*
                                                     const unsigned long long* __restrict__ n_chunks_p,
                                                     uint32_t round) {
   __shared__ SrcDesc s;
-  extern __shared__ uint32_t ptab[];  // kPrivSlots keys, then kPrivSlots cursors
+  __shared__ uint32_t s_ovf[kSmemBins / 32];  // overflow mask of a dense grid
+  // kPrivSlots keys, kPrivSlots cursors, the chunk stage, kPrivSlots overflow flags
+  extern __shared__ __align__(16) uint32_t ptab[];
   uint32_t* pkeys = ptab;
   uint32_t* pcur = ptab + kPrivSlots;
+  int4* stage = reinterpret_cast<int4*>(ptab + 2 * kPrivSlots);
+  uint8_t* pflag = reinterpret_cast<uint8_t*>(stage + kChunk);
   const uint64_t n_chunks = *n_chunks_p;
   const uint64_t per = (n_chunks + gridDim.x - 1) / gridDim.x;
   const uint64_t c0 = (uint64_t)blockIdx.x * per;
@@ -498,27 +575,44 @@ __global__ void __launch_bounds__(kBlock) k_scatter(BuildArgs a, const uint32_t*
   {
     const uint32_t len = a.list_len[blockIdx.x];
     const uint2* list = a.lists + (uint64_t)blockIdx.x * kPrivSlots;
+    // the listed cells belong to the CTA's sources, whose count regions are
+    // laid out in source order: a binary search finds each cell's source,
+    // whose overflow bit is kept beside the cursor
+    const uint32_t sid_lo = c0 < c1 ? chunk_src[c0] : 0u, sid_hi = c0 < c1 ? chunk_src[c1 - 1] : 0u;
     for (uint32_t j = threadIdx.x; j < len; j += blockDim.x) {
       const uint2 e = list[j];
       uint32_t slot = priv_home(e.x + 1u);
       while (atomicCAS(&pkeys[slot], 0u, e.x + 1u) != 0u) slot = (slot + 1 == kPrivSlots) ? 0u : slot + 1;
       pcur[slot] = atomicAdd(a.cnt_base + e.x + a.cursor_delta, e.y);
+      uint32_t lo = sid_lo, hi = sid_hi;  // last source whose count region starts at or before e.x
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if ((uint64_t)(a.srcs[mid].cnt - a.cnt_base) <= e.x) lo = mid;
+        else hi = mid - 1;
+      }
+      const SrcDesc& es = a.srcs[lo];
+      const uint32_t cell = e.x - (uint32_t)(es.cnt + pyr_off(es.d) - a.cnt_base);
+      pflag[slot] = (uint8_t)((es.ovf[cell >> 5] >> (cell & 31u)) & 1u);
     }
   }
   __syncthreads();
   uint32_t cur = kNone;
 
   constexpr int kPer = (int)(kChunk / kBlock);
+  const uint64_t pol_in = l2_evict_first(), pol_out = l2_evict_last();
+  if (c0 < c1) stage_chunk(a, chunk_src, c0, stage, 0u, pol_in);
   for (uint64_t c = c0; c < c1; ++c) {
     const uint32_t sid = chunk_src[c];
     if (sid != cur) {
       __syncthreads();
       if (threadIdx.x == 0) s = a.srcs[sid];
       __syncthreads();
+      if (!s.priv)
+        for (uint32_t w = threadIdx.x; w < ((1u << (3 * s.d)) + 31u) / 32u; w += blockDim.x) s_ovf[w] = s.ovf[w];
+      __syncthreads();
       cur = sid;
     }
     const TileDesc& td = a.tiles[s.tile];
-    const int4* pts = src_points(a, s, td);
     const uint32_t* src_idx =
         s.buf == 0 ? nullptr : (s.buf == 1 ? a.tmp_idx[0] : a.tmp_idx[1]) + td.pt_base + s.pt_off;
     const uint64_t first = (c - s.chunk0) << kChunkLog2;
@@ -526,27 +620,32 @@ __global__ void __launch_bounds__(kBlock) k_scatter(BuildArgs a, const uint32_t*
     uint32_t* cursor = s.start + pyr_off(s.d);
     const int32_t mx = s.min[0], my = s.min[1], mz = s.min[2];
     const uint32_t lg = s.log2size, d = s.d;
-    const uint32_t* ovfm = s.ovf;
     const bool priv = s.priv != 0;
     const uint32_t kbase = (uint32_t)(s.cnt + pyr_off(d) - a.cnt_base);
     int4 p[kPer];
+    uint32_t bins[kPer];
+    cp_async_wait_all();
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       const uint64_t i = first + threadIdx.x + (uint64_t)k * kBlock;
-      if (i < end) p[k] = ldg_stream(pts + i);
+      p[k] = make_int4(0, 0, 0, 0);
+      if (i < end) p[k] = stage[k * kBlock + threadIdx.x];
+      bins[k] = src_bin(p[k], mx, my, mz, lg, d);
     }
+    if (c + 1 < c1)
+      stage_chunk(a, chunk_src, c + 1, stage,
+                  opaque_zero(bins[0] ^ bins[1] ^ bins[2] ^ bins[3] ^ (uint32_t)(p[0].w ^ p[1].w ^ p[2].w ^ p[3].w)),
+                  pol_in);
     // claim every position before the first store that needs one
-    uint32_t pb[kPer], ow[kPer], bit5 = 0, agg = 0;
+    uint32_t pb[kPer], ovf_bits = 0, agg = 0;
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       const uint64_t i = first + threadIdx.x + (uint64_t)k * kBlock;
       const bool v = i < end;
       const unsigned m = __ballot_sync(0xFFFFFFFFu, v);
       pb[k] = 0;
-      ow[k] = 0;
       if (!v) continue;
-      const uint32_t bin = src_bin(p[k], mx, my, mz, lg, d);
-      bit5 |= (bin & 31u) << (5 * k);
+      const uint32_t bin = bins[k];
       if (priv) {
         const int slot = priv_find(pkeys, kbase + bin + 1u);
         const int leader = __ffs(m) - 1;
@@ -557,6 +656,8 @@ __global__ void __launch_bounds__(kBlock) k_scatter(BuildArgs a, const uint32_t*
         } else {
           pb[k] = slot >= 0 ? atomicAdd(&pcur[slot], 1u) : atomicAdd(cursor + bin, 1u);
         }
+        const uint32_t f = slot >= 0 ? (uint32_t)pflag[slot] : (s.ovf[bin >> 5] >> (bin & 31u)) & 1u;
+        ovf_bits |= f << k;
       } else {
         const int leader = __ffs(m) - 1;
         const uint32_t b0 = __shfl_sync(m, bin, leader);
@@ -567,7 +668,7 @@ __global__ void __launch_bounds__(kBlock) k_scatter(BuildArgs a, const uint32_t*
           pb[k] = atomicAdd(cursor + bin, 1u);
         }
       }
-      ow[k] = ovfm[bin >> 5];
+      if (!priv) ovf_bits |= ((s_ovf[bin >> 5] >> (bin & 31u)) & 1u) << k;
     }
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
@@ -576,19 +677,18 @@ __global__ void __launch_bounds__(kBlock) k_scatter(BuildArgs a, const uint32_t*
       if (i >= end) continue;
       uint32_t pos = pb[k];
       if (agg >> k & 1u) pos = __shfl_sync(m, pos, __ffs(m) - 1) + __popc(m & ((1u << lane) - 1u));
-      const bool ovf = (ow[k] >> ((bit5 >> (5 * k)) & 31u)) & 1u;
+      const bool ovf = (ovf_bits >> k) & 1u;
       const uint64_t dst = td.pt_base + pos;
       const uint32_t idx = a.out_idx ? (src_idx ? src_idx[i] : (uint32_t)i) : 0u;
       if (ovf) {
-        __stcs(ovf_dst + dst, p[k]);
+        st_keep(ovf_dst + dst, p[k], pol_out);
         if (a.out_idx) ovf_idx[dst] = idx;
       } else if (a.wide) {
         // one full 32-byte sector per point and no separate 4-byte index
         // write (isolated sub-sector writes are the costliest kind)
-        __stcs(a.wide + 2 * dst, p[k]);
-        __stcs(a.wide + 2 * dst + 1, make_int4((int)idx, 0, 0, 0));
+        st_wide(a.wide + 2 * dst, p[k], idx);
       } else {
-        __stcs(a.out + dst, p[k]);
+        st_keep(a.out + dst, p[k], pol_out);
         if (a.out_idx) a.out_idx[dst] = idx;
       }
     }
@@ -598,11 +698,11 @@ __global__ void __launch_bounds__(kBlock) k_scatter(BuildArgs a, const uint32_t*
 cudaError_t launch_scatter(const BuildArgs& a, const uint32_t* chunk_src, const unsigned long long* n_chunks,
                            uint32_t round, int grid, cudaStream_t st) {
   static bool once = [] {
-    cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * kPrivSlots));
+    cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(9 * kPrivSlots + 16 * kChunk));
     return true;
   }();
   (void)once;
-  k_scatter<<<grid, kBlock, 8 * kPrivSlots, st>>>(a, chunk_src, n_chunks, round);
+  k_scatter<<<grid, kBlock, 9 * kPrivSlots + 16 * kChunk, st>>>(a, chunk_src, n_chunks, round);
   return cudaGetLastError();
 }
 

@@ -9,8 +9,10 @@
 // shared-memory open-addressing hash table instead of a dense grid.  An
 // octant whose occupied cells exceed the table is processed in several
 // hash-partitioned passes.  Colour sums are exact integers (32-bit lanes
-// while they provably cannot overflow, 64-bit otherwise); the pick keeps the
-// minimal splitmix64(input index) with a 64-bit atomicMin.
+// while they provably cannot overflow, 64-bit otherwise); the pick keeps,
+// per cell, the entry {splitmix64(index), rgba | index << 32} of minimal
+// hash, updated by a 128-bit compare-and-swap, so the picked colour travels
+// with the winning hash and is never gathered from the input.
 //
 // Every octant's voxels go to a staging area; a level scan then assigns
 // each parent one contiguous voxel range (children are consecutive in node
@@ -23,10 +25,10 @@ namespace lodk {
 
 namespace {
 
-constexpr int kSmemBytes = 200 * 1024;
+constexpr int kSmemBytes = 224 * 1024;
 constexpr uint32_t kHn = kSmemBytes / 20;  // filtered, 32-bit sums: key + 2 x u64
 constexpr uint32_t kHw = kSmemBytes / 32;  // filtered, 64-bit sums: key + 3 x u64 + count
-constexpr uint32_t kHp = kSmemBytes / 16;  // pick: key + u64 hash + count
+constexpr uint32_t kHp = kSmemBytes / 24;  // pick: key + {u64 hash, u64 payload} + count
 constexpr uint64_t kNarrowMaxSamples = 0xFFFFFFFFull / 255;  // 32-bit channel sums cannot overflow
 constexpr uint64_t kMask40 = (1ull << 40) - 1;
 
@@ -41,6 +43,32 @@ __device__ __forceinline__ uint32_t part_of(uint32_t key1, uint32_t mlog) {
 }
 
 __device__ __forceinline__ uint32_t home_slot(uint32_t key1, uint32_t H) { return __umulhi(key1 * 0x9E3779B1u, H); }
+
+// Keep the sample of smaller hash in a pick entry {hash, rgba | index << 32}
+// (hashes of distinct indices differ: splitmix64 is a bijection).  Most
+// samples lose against the value read first and never write; an improvement
+// is installed with a 128-bit compare-and-swap, retried while others lower
+// the entry meanwhile (each retry sees a strictly smaller hash, so the loop
+// ends; the bound only guards against a broken invariant).
+__device__ __forceinline__ bool pick_update(ulonglong2* e, uint64_t h, uint64_t pay) {
+  const uint32_t addr = (uint32_t)__cvta_generic_to_shared(e);
+  uint64_t c0, c1;
+  asm volatile("ld.volatile.shared.v2.u64 {%0, %1}, [%2];" : "=l"(c0), "=l"(c1) : "r"(addr) : "memory");
+  for (uint32_t tries = 0; h < c0; ++tries) {
+    if (tries == (1u << 20)) return false;
+    uint64_t p0, p1;
+    asm volatile(
+        "{\n .reg .b128 d, c, s;\n mov.b128 c, {%2, %3};\n mov.b128 s, {%4, %5};\n"
+        " atom.shared.cas.b128 d, [%6], c, s;\n mov.b128 {%0, %1}, d;\n}"
+        : "=l"(p0), "=l"(p1)
+        : "l"(c0), "l"(c1), "l"(h), "l"(pay), "r"(addr)
+        : "memory");
+    if (p0 == c0 && p1 == c1) return true;
+    c0 = p0;
+    c1 = p1;
+  }
+  return true;
+}
 
 // Linear probing from `slot`, whose content was observed as k: the slot of
 // key1 (= local cell + 1), inserting it if absent.  Returns -1 when kProbe
@@ -163,10 +191,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_vox(BuildArgs a, VoxLevel v, DevC
   unsigned long long* A0 = reinterpret_cast<unsigned long long*>(smem);
   unsigned long long* A1 = A0 + H;
   unsigned long long* A2 = A1 + H;  // wide only
+  ulonglong2* E = reinterpret_cast<ulonglong2*>(smem);  // pick entries
   uint32_t* keys;
   uint32_t* cnt32;
   if (MODE == LOD_PICK) {
-    keys = reinterpret_cast<uint32_t*>(A0 + H);
+    keys = reinterpret_cast<uint32_t*>(E + H);
     cnt32 = keys + H;
   } else if (narrow) {
     keys = reinterpret_cast<uint32_t*>(A0 + 2 * H);
@@ -200,7 +229,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_vox(BuildArgs a, VoxLevel v, DevC
       for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) {
         keys[i] = 0u;
         if (MODE == LOD_PICK) {
-          A0[i] = ~0ull;
+          E[i] = make_ulonglong2(~0ull, 0ull);
           cnt32[i] = 0u;
         } else {
           A0[i] = 0ull;
@@ -252,7 +281,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_vox(BuildArgs a, VoxLevel v, DevC
             return;
           }
           if (MODE == LOD_PICK) {
-            atomicMin(&A0[slot], h);
+            if (!pick_update(&E[slot], h, (uint64_t)rgba | ((uint64_t)ix << 32))) atomicOr(&ctr->error, kErrInternal);
             atomicAdd(&cnt32[slot], n_same);
           } else if (narrow) {
             atomicAdd(&A0[slot], (uint64_t)r | ((uint64_t)g << 32));
@@ -270,8 +299,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_vox(BuildArgs a, VoxLevel v, DevC
         // resolved.
         auto load = [&](uint64_t i, int4& q, uint32_t& x) {
           if (wsrc) {
-            q = __ldcs(wsrc + 2 * i);
-            x = (uint32_t)__ldcs(wsrc + 2 * i + 1).x;
+            ld_wide(wsrc + 2 * i, q, x);
           } else {
             q = __ldcs(pts + i);
             if (MODE == LOD_PICK) x = __ldcs(pidx + i);
@@ -341,7 +369,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_vox(BuildArgs a, VoxLevel v, DevC
               continue;
             }
             if (MODE == LOD_PICK) {
-              atomicMin(&A0[slot], splitmix64((uint32_t)vr.w));
+              const uint32_t idx = (uint32_t)vr.w;
+              if (!pick_update(&E[slot], splitmix64(idx), (uint64_t)(uint32_t)vr.y | ((uint64_t)idx << 32)))
+                atomicOr(&ctr->error, kErrInternal);
               atomicAdd(&cnt32[slot], (uint32_t)vr.z);
             } else {
               const ulonglong2 sm = sums[i];
@@ -389,13 +419,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_vox(BuildArgs a, VoxLevel v, DevC
         int4 rec;
         rec.x = (int)cell;
         if (MODE == LOD_PICK) {
-          const uint64_t inv = splitmix64_inverse(A0[i]);
-          const uint32_t best = (uint32_t)inv;
-          if (inv >= td.n) {  // cannot happen for a cell that received a sample
+          const ulonglong2 e = E[i];
+          const uint32_t best = (uint32_t)(e.y >> 32);
+          if (best >= td.n || splitmix64(best) != e.x) {  // cannot happen for a cell that received a sample
             atomicOr(&ctr->error, kErrInternal);
             continue;
           }
-          rec.y = (int)__ldg(reinterpret_cast<const uint32_t*>(td.in) + 4ull * best + 3);
+          rec.y = (int)(uint32_t)e.y;
           rec.z = (int)cnt32[i];
           rec.w = (int)best;
         } else {
@@ -556,8 +586,11 @@ __global__ void __launch_bounds__(256) k_unwide(BuildArgs a, const uint32_t* __r
   const TileDesc& td = a.tiles[tiles[blockIdx.y]];
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < td.n; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t p = td.pt_base + i;
-    a.out[p] = __ldcs(a.wide + 2 * p);
-    a.out_idx[p] = (uint32_t)__ldcs(a.wide + 2 * p + 1).x;
+    int4 q;
+    uint32_t x;
+    ld_wide(a.wide + 2 * p, q, x);
+    a.out[p] = q;
+    a.out_idx[p] = x;
   }
 }
 
