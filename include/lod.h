@@ -3,16 +3,16 @@
  *
  * The library builds the hybrid voxel-point octree of "GPU-Accelerated LOD
  * Generation for Point Clouds" (Schuetz, Kerbl, Klaus, Wimmer 2023):
- *   - Section 3.1: the input points are split top-down into an octree whose
+ *   - Section 4.1: the input points are split top-down into an octree whose
  *     leaves hold at most T original points (hierarchical counting sort);
- *   - Section 3.2: every inner node is then filled bottom-up with the
+ *   - Section 4.2: every inner node is then filled bottom-up with the
  *     occupied cells ("voxels") of a 128^3 grid laid over its cube.
  * Two sampling modes are provided:
- *   - LOD_FILTER: the cell-wise average of Section 3.2.3, made exact — each
+ *   - LOD_FILTER: the cell-wise average of Section 4.2.3, made exact — each
  *     voxel carries the integer mean (rounded half up) of the RGB of all
  *     original points inside its cell, accumulated as unsigned 64-bit sums;
  *     alpha is 255.
- *   - LOD_PICK: replaces the random pick of Section 3.2.2 (Listing 1) by an
+ *   - LOD_PICK: replaces the random pick of Section 4.2.2 (Listing 1) by an
  *     order-independent rule — each voxel keeps the original point of
  *     minimal splitmix64(input index); pick_index is that index.
  *
@@ -114,7 +114,7 @@ typedef struct lod_node {
   uint32_t voxel_count, reserved;
 } lod_node_t;
 
-/* One voxel of an inner node, 16 bytes (Section 3.2).
+/* One voxel of an inner node, 16 bytes (Section 4.2).
  *   cell        x | y << 7 | z << 14, the 128^3 grid cell relative to the
  *               node's cube (cell edge 2^log2_size / 128).
  *   rgba        LOD_FILTER: rounded-half-up mean RGB, A = 255;
@@ -156,7 +156,7 @@ typedef struct lod_result lod_result_t;
 /* Fill *p with the defaults: T = 50000, LOD_FILTER, max_depth 21, flags 0. */
 int lod_params_init(lod_params_t* p);
 
-/* Build the LOD octree of n device points (Sections 3.1 and 3.2).
+/* Build the LOD octree of n device points (Sections 4.1 and 4.2).
  *   d_points  device, 16-byte aligned, n records; read only.  n < 2^32.
  *   params    host; NULL selects the defaults.
  *   stream    cudaStream_t as void*; all device work is ordered on it.

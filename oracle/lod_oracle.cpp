@@ -8,29 +8,29 @@
 // written top-down per node from the definitions, with no blocking, fusion
 // or bottom-up merging:
 //
-//  * Root cube (Section 3 with the reading that the paper's float coordinates
+//  * Root cube (Section 4 with the reading that the paper's float coordinates
 //    become int32): the bounding box minimum is the cube's min corner and
 //    its edge S is the smallest power of two strictly greater than the
 //    largest per-axis extent.  N = 0 gives an empty root leaf at the origin.
-//  * Split into leaves (Section 3.1): a node holding more than T points is
+//  * Split into leaves (Section 4.1): a node holding more than T points is
 //    subdivided into its non-empty octants; a node with at most T points is
 //    a leaf.  The fixed 8-level grid plus one 4-level extension of Section
 //    3.1.5 becomes "recurse until it fits", capped by max_depth and by unit
 //    cubes (such capped leaves may exceed T and are flagged overfull).
-//    Merging 2x2x2 groups whose sum stays below T (Section 3.1.2) yields the
+//    Merging 2x2x2 groups whose sum stays below T (Section 4.1.2) yields the
 //    same tree apart from the T boundary, which follows "at most T points".
 //  * Octant index k = (bx << 2) | (by << 1) | bz, b = the half a point falls
 //    into along each axis; children are listed in ascending k.
 //  * Node order: breadth first by level, within a level by the parent's
 //    order and then ascending octant (ascending path key).
-//  * Leaf point layout (Section 3.1.3 allocates each leaf's points; the
+//  * Leaf point layout (Section 4.1.3 allocates each leaf's points; the
 //    layout is free there): leaves are laid out depth first in octant
 //    order, so every subtree owns one contiguous point range.
-//  * Voxel sampling (Section 3.2): every inner node gets the occupied cells
-//    of a 128^3 grid over its cube.  Cell-wise average (Section 3.2.3) with
+//  * Voxel sampling (Section 4.2): every inner node gets the occupied cells
+//    of a 128^3 grid over its cube.  Cell-wise average (Section 4.2.3) with
 //    exact u64 sums over all original points of the cube and a rounded-half-
 //    up integer mean, alpha 255; sample pick (replacing the random pick of
-//    Section 3.2.2, Listing 1) keeps the point of minimal splitmix64(index).
+//    Section 4.2.2, Listing 1) keeps the point of minimal splitmix64(index).
 //
 // Function-level citations are beside each function.
 
@@ -87,7 +87,7 @@ uint64_t splitmix64(uint64_t x) {
 inline int64_t rel(int32_t p, int32_t c) { return (int64_t)p - (int64_t)c; }
 
 // 128^3 grid coordinate of an offset d inside a cube of edge 2^L
-// (Section 3.2: samples are projected onto a 128^3 grid per node).
+// (Section 4.2: samples are projected onto a 128^3 grid per node).
 inline uint32_t grid_coord(int64_t d, uint32_t L) {
   if (L >= 7) return (uint32_t)(d >> (L - 7));
   return (uint32_t)(d << (7 - L));
@@ -103,7 +103,7 @@ struct Builder {
   std::vector<OPoint> leaf_points;
   std::vector<uint32_t> leaf_index;
 
-  // Section 3.2 + 3.2.3 / replacement of 3.2.2: the voxels of one inner node
+  // Section 4.2 + 4.2.3 / replacement of 4.2.2: the voxels of one inner node
   // computed directly from every original point inside its cube.
   void voxelize(ONode& nd, const std::vector<uint32_t>& idx) {
     std::vector<std::pair<uint32_t, uint32_t>> keyed;  // (cell, point index)
@@ -125,7 +125,7 @@ struct Builder {
       v.cell = keyed[a].first;
       v.count = (uint32_t)(b - a);
       if (mode == 0) {
-        // Cell-wise average (Section 3.2.3): sum each channel over all
+        // Cell-wise average (Section 4.2.3): sum each channel over all
         // samples of the cell, then the arithmetic mean, rounded half up.
         uint64_t sr = 0, sg = 0, sb = 0;
         for (size_t j = a; j < b; ++j) {
@@ -203,7 +203,7 @@ struct Builder {
     nodes.push_back(root);
     leaf_lists.emplace_back();
 
-    // Breadth-first split, one level at a time (Section 3.1).
+    // Breadth-first split, one level at a time (Section 4.1).
     std::vector<std::pair<uint32_t, std::vector<uint32_t>>> cur, next;
     {
       std::vector<uint32_t> all(n);

@@ -15,9 +15,9 @@ constexpr uint32_t kChunk = 4096;      // points per work chunk of the streaming
 constexpr uint32_t kChunkLog2 = 12;
 constexpr uint32_t kMaxLevels = 34;    // levels 0..32 plus one sentinel slot
 constexpr uint32_t kRootMaxD = 8;      // depth of the largest first counting grid (256^3 cells)
-constexpr uint32_t kSegMaxD = 4;       // depth of a refinement grid (16^3 cells, as in Section 3.1.5)
+constexpr uint32_t kSegMaxD = 4;       // depth of a refinement grid (16^3 cells, as in Section 4.1.5)
 constexpr uint32_t kSmemBins = 4096;   // grids up to 8^4 bins are counted in shared memory
-constexpr uint32_t kOctCells = 1u << 18;  // 64^3 cells of one child octant (Section 3.2.1)
+constexpr uint32_t kOctCells = 1u << 18;  // 64^3 cells of one child octant (Section 4.2)
 constexpr uint32_t kBlock = 1024;
 
 // Offset of level j inside a count/start pyramid stored level by level
@@ -43,7 +43,7 @@ struct TileDesc {
 
 // A counting grid ("source"): 8^d cells under one cube, the whole root for
 // the first grid of a tile, or an overflowing cell for a refinement grid
-// (Section 3.1.5).  Its points occupy [pt_off, pt_off + n) of the tile.
+// (Section 4.1.5).  Its points occupy [pt_off, pt_off + n) of the tile.
 struct SrcDesc {
   uint32_t* cnt;       // count pyramid, levels 0..d (level j: 8^j cells)
   uint32_t* start;     // start pyramid (tile-relative positions); its
@@ -150,7 +150,7 @@ __host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 }
 
 // 128^3 grid coordinate of an offset d (0 <= d < 2^L) inside a cube of edge
-// 2^L (Section 3.2: every node samples onto a 128^3 grid).
+// 2^L (Section 4.2: every node samples onto a 128^3 grid).
 __device__ __forceinline__ uint32_t grid_coord(uint32_t d, uint32_t L) {
   return L >= 7 ? (uint32_t)((uint64_t)d >> (L - 7)) : (d << (7 - L));
 }

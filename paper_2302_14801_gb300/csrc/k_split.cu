@@ -1,4 +1,4 @@
-// Split of the input into octree leaves (Section 3.1 of the paper):
+// Split of the input into octree leaves (Section 4.1 of the paper):
 // bounding box, hierarchical counting sort with recursive refinement of
 // overflowing cells, and the breadth-first node table.
 //
@@ -224,7 +224,7 @@ cudaError_t launch_bbox(const TileDesc* tiles, const uint32_t* chunk_tile, uint6
 }
 
 // ------------------------------------------------------------------- counting
-// Section 3.1.1 (count per cell of the grid) and 3.1.5 (count again inside
+// Section 4.1.1 (count per cell of the grid) and 4.1.5 (count again inside
 // the extended grids of overflowing cells): one histogram per source.
 //
 // Grids of up to 8^4 cells are counted in a dense shared-memory histogram.
@@ -401,7 +401,7 @@ cudaError_t launch_count(const BuildArgs& a, const uint32_t* chunk_src, const un
 
 
 // ------------------------------------------------------------ pyramid: up-sweep
-// Per-level counts (the counting-grid pyramid of Section 3.1.2) from the
+// Per-level counts (the counting-grid pyramid of Section 4.1.2) from the
 // bottom histogram, 4 levels per CTA in shared memory.
 
 __global__ void __launch_bounds__(512) k_pyr_up(BuildArgs a, const PyrJob* __restrict__ jobs) {
@@ -443,7 +443,7 @@ cudaError_t launch_pyr_up(const BuildArgs& a, const PyrJob* jobs, uint32_t n_job
 // 3.1.3: where each node's points go), top-down 4 levels per CTA.  At the
 // bottom level the starts become the scatter cursors, and every cell with
 // more than T points that can still be split becomes a refinement grid
-// for the next round (Section 3.1.5, extended to any depth).
+// for the next round (Section 4.1.5, extended to any depth).
 
 __global__ void __launch_bounds__(512) k_pyr_down(BuildArgs a, const PyrJob* __restrict__ jobs,
                                                   uint32_t next_base, uint32_t next_cap, uint32_t next_buf,
@@ -542,7 +542,7 @@ cudaError_t launch_pyr_down(const BuildArgs& a, const PyrJob* jobs, uint32_t n_j
 }
 
 // ------------------------------------------------------------------- scatter
-// Section 3.1.4 (insert): every point goes to its cell's cursor; points of
+// Section 4.1.4 (insert): every point goes to its cell's cursor; points of
 // cells that will be refined go to the ping-pong buffer of the next round,
 // all others to their final place in the leaf-point array.  For large grids
 // the CTA re-creates its counting table from its list, claims one block of
@@ -708,7 +708,7 @@ cudaError_t launch_scatter(const BuildArgs& a, const uint32_t* chunk_src, const 
 
 
 // ---------------------------------------------------------------- node table
-// Breadth-first node list (Section 3.1.3 creates the node list from the
+// Breadth-first node list (Section 4.1.3 creates the node list from the
 // count pyramid): one CTA per tile walks the levels; a node is split iff it
 // holds more than T points, is above max_depth and larger than a unit cube.
 // Children are the non-empty octants in octant order, their counts read

@@ -1,11 +1,11 @@
-// Bottom-up voxel sampling (Section 3.2 of the paper).
+// Bottom-up voxel sampling (Section 4.2 of the paper).
 //
 // The paper processes one node per workgroup with one 128^3 grid per SM in
-// global memory (8 MB / 33 MB per workgroup, Sections 3.2.2-3.2.3).  Here a
+// global memory (8 MB / 33 MB per workgroup, Sections 4.2.2-4.2.3).  Here a
 // CTA handles one (parent, child octant) pair: the child's samples (its
 // leaf points, or the voxels the child itself received one level below)
 // all fall into one 64^3 octant of the parent's 128^3 grid (the observation
-// of Section 3.2.1), and their cells are accumulated in a ~200 KB
+// of Section 4.2), and their cells are accumulated in a ~200 KB
 // shared-memory open-addressing hash table instead of a dense grid.  An
 // octant whose occupied cells exceed the table is processed in several
 // hash-partitioned passes.  Colour sums are exact integers (32-bit lanes

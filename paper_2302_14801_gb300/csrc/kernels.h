@@ -11,7 +11,7 @@ struct PyrJob {
   uint32_t block;  // block index (cell index at the block's top level)
 };
 
-// ----- split (Section 3.1) -----
+// ----- split (Section 4.1) -----
 cudaError_t launch_bbox(const TileDesc* tiles, const uint32_t* chunk_tile, uint64_t n_chunks,
                         const uint64_t* tile_chunk0, int* bbox, int grid, cudaStream_t st);
 cudaError_t launch_count(const BuildArgs& a, const uint32_t* chunk_src, const unsigned long long* n_chunks,
@@ -24,7 +24,7 @@ cudaError_t launch_scatter(const BuildArgs& a, const uint32_t* chunk_src, const 
 cudaError_t launch_nodes(const BuildArgs& a, lod_node_t* nodes, NodeAux* aux, uint32_t* lvl_start,
                          uint32_t* n_nodes, unsigned long long* leaf_cap, DevCounters* ctr, cudaStream_t st);
 
-// ----- voxel sampling (Section 3.2) -----
+// ----- voxel sampling (Section 4.2) -----
 struct VoxLevel {
   uint32_t level;              // parent level l; items are the nodes at level l + 1
   uint32_t n_items;

@@ -1,6 +1,6 @@
 """Seeded synthetic point clouds shaped like the paper's evaluation workloads.
 
-The paper evaluates on four scanned data sets (Section 5, Figure 4 and
+The paper evaluates on four scanned data sets (Section 6, Figure 4 and
 Table 1: Retz, Palmyra, Saint Roman, CA21 Bunds) that are not available
 here.  These generators stand in for them.  They hold none of the LOD
 construction's arithmetic: they only draw points.  Both the CUDA path and

@@ -4,8 +4,8 @@ definitions and by mathematics, not by the oracle itself.
 * splitmix64: the published first output for seed 0 (Steele, Lea & Flood,
   OOPSLA 2014; the value every reference implementation prints).
 * Hand-derived closed forms: root cube sizing, octant bit order, node order,
-  rounding of the cell mean (Section 3.2.3), the unique minimal-hash pick,
-  duplicate-point chains capped by unit cubes and max_depth (Section 3.1.5
+  rounding of the cell mean (Section 4.2.3), the unique minimal-hash pick,
+  duplicate-point chains capped by unit cubes and max_depth (Section 4.1.5
   reading), complete lattices and a line with closed-form counts.
 * An independent brute-force checker (tests/bruteforce.py) on random tiny
   clouds with small T (deep trees), in both modes.
