@@ -15,7 +15,7 @@
 //  * Split into leaves (Section 4.1): a node holding more than T points is
 //    subdivided into its non-empty octants; a node with at most T points is
 //    a leaf.  The fixed 8-level grid plus one 4-level extension of Section
-//    3.1.5 becomes "recurse until it fits", capped by max_depth and by unit
+//    4.1.5 becomes "recurse until it fits", capped by max_depth and by unit
 //    cubes (such capped leaves may exceed T and are flagged overfull).
 //    Merging 2x2x2 groups whose sum stays below T (Section 4.1.2) yields the
 //    same tree apart from the T boundary, which follows "at most T points".

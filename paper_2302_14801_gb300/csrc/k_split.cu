@@ -440,7 +440,7 @@ cudaError_t launch_pyr_up(const BuildArgs& a, const PyrJob* jobs, uint32_t n_job
 
 // ---------------------------------------------------------- pyramid: down-sweep
 // Exclusive-scan starts of every cell (the "target pointers" of Section
-// 3.1.3: where each node's points go), top-down 4 levels per CTA.  At the
+// 4.1.3: where each node's points go), top-down 4 levels per CTA.  At the
 // bottom level the starts become the scatter cursors, and every cell with
 // more than T points that can still be split becomes a refinement grid
 // for the next round (Section 4.1.5, extended to any depth).
