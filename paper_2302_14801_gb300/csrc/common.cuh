@@ -110,6 +110,8 @@ struct DevCounters {
   unsigned long long vox_retries;     // voxel items that needed more table passes
   unsigned long long vox_passes;      // table passes over all voxel items
   unsigned int error;                 // nonzero: a kernel detected a problem
+  unsigned int units;                 // voxel partition units queued this level
+  unsigned int unit_head;             // units taken by the partition kernel
   unsigned int pad;
 };
 
@@ -169,6 +171,9 @@ __device__ __forceinline__ void ld_wide(const int4* p, int4& q, uint32_t& idx) {
   asm("ld.global.cs.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                : "=r"(q.x), "=r"(q.y), "=r"(q.z), "=r"(q.w), "=r"(idx), "=r"(u0), "=r"(u1), "=r"(u2)
                : "l"(p));
+  (void)u0;
+  (void)u1;
+  (void)u2;
 }
 
 }  // namespace lodk

@@ -750,6 +750,8 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
 
   // ---- voxel levels, bottom-up
   DevBuf d_dense(st), d_stage0(st), d_stage1(st), d_sum0(st), d_sum1(st), d_itemp(st), d_parp(st), d_tvox(st);
+  DevBuf d_units(st);  // queue of partition units of overflowing voxel items
+  uint32_t units_cap = 0;
   const bool filt = prm.mode == LOD_FILTER;
   uint64_t dense_cap = std::max<uint64_t>(M / 2, 1024);
   LOD_CK(d_dense.alloc(dense_cap * 16));
@@ -797,6 +799,13 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
     vl.stage_in_sum = filt ? (par ? d_sum0 : d_sum1).as<ulonglong2>() : nullptr;
     vl.dense = d_dense.as<int4>();
     vl.stage_used = &d_ctr.as<DevCounters>()->stage_used[par];
+    const uint32_t want_units = (uint32_t)std::min<uint64_t>((uint64_t)n_items * 64, 1u << 20);
+    if (want_units > units_cap) {
+      LOD_CK(d_units.alloc((size_t)want_units * sizeof(uint4)));
+      units_cap = want_units;
+    }
+    vl.units = d_units.as<uint4>();
+    vl.unit_cap = units_cap;
     A.tiles = d_tiles.as<TileDesc>();
     static const char* kVoxLevelNames[kMaxLevels] = {
         "voxelize_L00", "voxelize_L01", "voxelize_L02", "voxelize_L03", "voxelize_L04", "voxelize_L05",

@@ -101,6 +101,7 @@ struct ItemInfo {
   int32_t pmin[3];
   bool leaf;
   uint64_t n;        // samples
+  uint64_t npts;     // original points in the child's cube
 };
 
 __device__ __forceinline__ uint32_t find_tile(const uint32_t* prefix, uint32_t n_tiles, uint32_t it) {
@@ -153,39 +154,73 @@ __device__ __forceinline__ uint32_t mean_rgba(uint64_t r, uint64_t g, uint64_t b
 
 int vox_smem_bytes() { return kSmemBytes; }
 
-// One CTA per item (a child node c of an inner node p at level v.level).
-template <int MODE>
-__global__ void __launch_bounds__(kBlock, 1) k_vox(BuildArgs a, VoxLevel v, DevCounters* __restrict__ ctr) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ uint32_t s_used, s_out, s_fail;
-  __shared__ unsigned long long s_stage;
-  __shared__ ItemInfo I;
+// Shared state of one voxel CTA.
+struct VoxShared {
+  uint32_t used, out, fail, sp, seen, queued;
+  unsigned long long base;  // first staging record of the current pass's output
+  ItemInfo I;
+  uint2 stack[48];          // pending {partition, log2 partitions} of the item
+};
 
+constexpr uint32_t kMaxQueuedLog = 6;  // an overflowing item is queued as at most 64 units
+constexpr uint32_t kMaxPartLog = 16;   // deeper partitions cannot overflow (a few cells each)
+
+// Reserve `n` consecutive slots of the unit queue; false when it is full
+// (the reservation is all or nothing, so no slot is left unwritten).
+__device__ __forceinline__ bool reserve_units(unsigned int* count, uint32_t cap, uint32_t n, uint32_t* first) {
+  uint32_t old = *((volatile unsigned int*)count);
+  for (int tries = 0; tries < 4096; ++tries) {
+    if (old + n > cap) return false;
+    const uint32_t prev = atomicCAS(count, old, old + n);
+    if (prev == old) {
+      *first = old;
+      return true;
+    }
+    old = prev;
+  }
+  return false;
+}
+
+// Voxelize one item (a child node c of an inner node p at level v.level):
+// its samples are hashed into the shared table, one pass per partition of
+// its cells.  `first`: the item's first attempt, all cells in one pass; if
+// the table overflows, the item is split into 2^m hash partitions that the
+// partition kernel processes in parallel (or, when the queue is full, this
+// CTA processes them itself).  A partition that still overflows is split in
+// two, depth first, by the CTA that holds it.
+template <int MODE>
+__device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, DevCounters* __restrict__ ctr,
+                                         unsigned char* smem, VoxShared& S, uint32_t it, uint32_t p_first,
+                                         uint32_t m_first, bool first) {
   if (threadIdx.x == 0) {
-    const uint32_t it = blockIdx.x;
     const uint32_t t = find_tile(v.item_prefix, a.n_tiles, it);
     const uint32_t* ls = v.lvl_start + (uint64_t)t * (kMaxLevels + 1);
     const TileDesc& td = a.tiles[t];
     const uint64_t g = td.node_base + ls[v.level + 1] + (it - v.item_prefix[t]);
     const lod_node_t c = v.nodes[g];
     const lod_node_t p = v.nodes[td.node_base + c.parent];
-    I.tile = t;
-    I.g = g;
-    I.Lp = p.log2_size;
-    I.pmin[0] = p.min[0];
-    I.pmin[1] = p.min[1];
-    I.pmin[2] = p.min[2];
-    I.kx = c.min[0] != p.min[0];
-    I.ky = c.min[1] != p.min[1];
-    I.kz = c.min[2] != p.min[2];
-    I.leaf = (c.flags & LOD_NODE_LEAF) != 0;
-    I.n = I.leaf ? c.point_count : c.voxel_count;
-    s_stage = ~0ull;
+    S.I.tile = t;
+    S.I.g = g;
+    S.I.Lp = p.log2_size;
+    S.I.pmin[0] = p.min[0];
+    S.I.pmin[1] = p.min[1];
+    S.I.pmin[2] = p.min[2];
+    S.I.kx = c.min[0] != p.min[0];
+    S.I.ky = c.min[1] != p.min[1];
+    S.I.kz = c.min[2] != p.min[2];
+    S.I.leaf = (c.flags & LOD_NODE_LEAF) != 0;
+    S.I.n = S.I.leaf ? c.point_count : c.voxel_count;
+    S.I.npts = c.point_count;
+    S.stack[0] = make_uint2(p_first, m_first);
+    S.sp = 1;
+    S.queued = 0;
   }
   __syncthreads();
+  const ItemInfo& I = S.I;
   const TileDesc& td = a.tiles[I.tile];
   const lod_node_t& c = v.nodes[I.g];
-  const bool narrow = MODE == LOD_FILTER && I.leaf && I.n <= kNarrowMaxSamples;
+  // 32-bit channel sums cannot overflow when the cube holds few enough points
+  const bool narrow = MODE == LOD_FILTER && I.npts <= kNarrowMaxSamples;
   const uint32_t H = MODE == LOD_PICK ? kHp : (narrow ? kHn : kHw);
   // shared-memory carve-up (u64 arrays first)
   unsigned long long* A0 = reinterpret_cast<unsigned long long*>(smem);
@@ -205,9 +240,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_vox(BuildArgs a, VoxLevel v, DevC
     cnt32 = keys + H;
   }
 
-  const uint64_t cap = umin64(I.n, kOctCells);
-  uint32_t mlog = 0;
-  uint64_t out_total = 0;
+  const uint64_t bound = umin64(I.n, kOctCells);  // cells the item can occupy
   const uint64_t pbase = td.pt_base + c.point_offset;
   const int4* pts = a.out + pbase;
   const uint32_t* pidx = (MODE == LOD_PICK) ? a.out_idx + pbase : nullptr;
@@ -216,278 +249,353 @@ __global__ void __launch_bounds__(kBlock, 1) k_vox(BuildArgs a, VoxLevel v, DevC
   const int4* wsrc = a.wide ? a.wide + 2 * pbase : nullptr;
   const uint32_t nch = __popc(c.child_mask);
   const uint64_t fc = td.node_base + (c.first_child == kNone ? 0 : c.first_child);
+  const uint32_t lane = threadIdx.x & 31u;
+  uint32_t passes = 0;
+  bool split = false;
 
-  for (;;) {  // attempts with more partitions after an overflow
-    const uint32_t P = 1u << mlog;
-    out_total = 0;
-    bool failed = false;
-    if (mlog > 0 && threadIdx.x == 0 && s_stage == ~0ull) {
-      s_stage = atomicAdd(v.stage_used, (unsigned long long)cap);
-      if (s_stage + cap > v.stage_cap) atomicOr(&ctr->error, kErrStageCap);
-    }
-    for (uint32_t part = 0; part < P; ++part) {
-      for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) {
-        keys[i] = 0u;
-        if (MODE == LOD_PICK) {
-          E[i] = make_ulonglong2(~0ull, 0ull);
+  for (;;) {
+    __syncthreads();
+    if (S.sp == 0) break;
+    const uint2 pm = S.stack[S.sp - 1];
+    const uint32_t part = pm.x, mlog = pm.y;
+    for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) {
+      keys[i] = 0u;
+      if (MODE == LOD_PICK) {
+        E[i] = make_ulonglong2(~0ull, 0ull);
+        cnt32[i] = 0u;
+      } else {
+        A0[i] = 0ull;
+        A1[i] = 0ull;
+        if (!narrow) {
+          A2[i] = 0ull;
           cnt32[i] = 0u;
-        } else {
-          A0[i] = 0ull;
-          A1[i] = 0ull;
-          if (!narrow) {
-            A2[i] = 0ull;
-            cnt32[i] = 0u;
-          }
         }
       }
-      if (threadIdx.x == 0) {
-        s_used = 0;
-        s_fail = 0;
-      }
-      __syncthreads();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      S.sp -= 1;
+      S.used = 0;
+      S.fail = 0;
+      S.seen = 0;
+    }
+    __syncthreads();
+    ++passes;
+    uint32_t seen = 0;  // samples this thread went through (for the overflow estimate)
 
-      if (I.leaf) {
-        const uint64_t n = I.n;
-        const uint64_t step = 2ull * blockDim.x;
-        // Lanes of a warp whose points share a cell are merged first (point
-        // order follows the scan in real data, so whole warps often hit one
-        // cell); one leader per distinct cell then probes and updates the
-        // table.  All sums stay exact: at most 32 samples are merged.
-        const uint32_t lane = threadIdx.x & 31u;
-        auto accumulate = [&](uint32_t key1, const int4& q, uint32_t ix) {
-          const unsigned act = __ballot_sync(0xFFFFFFFFu, key1 != 0u);
-          if (key1 == 0u) return;
-          const uint32_t rgba = (uint32_t)q.w;
-          uint64_t h = 0;
-          uint32_t r = rgba & 255u, g = (rgba >> 8) & 255u, b = (rgba >> 16) & 255u;
-          uint32_t n_same = 1;
-          if (MODE == LOD_PICK) {
-            // a 64-bit minimum is cheap to contend for (most updates lose the
-            // comparison), so pick mode skips the merge
-            h = splitmix64(ix);
-          } else {
-            const unsigned peers = __match_any_sync(act, key1);
-            n_same = __popc(peers);
-            if (n_same > 1) {
-              r = __reduce_add_sync(peers, r);
-              g = __reduce_add_sync(peers, g);
-              b = __reduce_add_sync(peers, b);
-            }
-            if ((int)lane != __ffs(peers) - 1) return;
+    if (I.leaf) {
+      const uint64_t n = I.n;
+      const uint64_t step = 2ull * blockDim.x;
+      // Lanes of a warp whose points share a cell are merged first (point
+      // order follows the scan in real data, so whole warps often hit one
+      // cell); one leader per distinct cell then probes and updates the
+      // table.  All sums stay exact: at most 32 samples are merged.
+      auto accumulate = [&](uint32_t key1, const int4& q, uint32_t ix) {
+        const unsigned act = __ballot_sync(0xFFFFFFFFu, key1 != 0u);
+        if (key1 == 0u) return;
+        const uint32_t rgba = (uint32_t)q.w;
+        uint64_t h = 0;
+        uint32_t r = rgba & 255u, g = (rgba >> 8) & 255u, b = (rgba >> 16) & 255u;
+        uint32_t n_same = 1;
+        if (MODE == LOD_PICK) {
+          // most updates lose the comparison against the entry they read,
+          // so pick mode skips the merge
+          h = splitmix64(ix);
+        } else {
+          const unsigned peers = __match_any_sync(act, key1);
+          n_same = __popc(peers);
+          if (n_same > 1) {
+            r = __reduce_add_sync(peers, r);
+            g = __reduce_add_sync(peers, g);
+            b = __reduce_add_sync(peers, b);
           }
-          const int slot = find_or_insert(keys, H, key1);
-          if (slot < 0) {
-            s_fail = 1;
-            return;
-          }
-          if (MODE == LOD_PICK) {
-            if (!pick_update(&E[slot], h, (uint64_t)rgba | ((uint64_t)ix << 32))) atomicOr(&ctr->error, kErrInternal);
-            atomicAdd(&cnt32[slot], n_same);
-          } else if (narrow) {
-            atomicAdd(&A0[slot], (uint64_t)r | ((uint64_t)g << 32));
-            atomicAdd(&A1[slot], (uint64_t)b | ((uint64_t)n_same << 32));
-          } else {
-            atomicAdd(&A0[slot], (uint64_t)r);
-            atomicAdd(&A1[slot], (uint64_t)g);
-            atomicAdd(&A2[slot], (uint64_t)b);
-            atomicAdd(&cnt32[slot], n_same);
-          }
-        };
-        // Software pipeline over pairs of points: the loads of the next pair
-        // are in flight while the current pair is hashed and accumulated,
-        // and both of a pair's first probes are issued before either is
-        // resolved.
-        auto load = [&](uint64_t i, int4& q, uint32_t& x) {
-          if (wsrc) {
-            ld_wide(wsrc + 2 * i, q, x);
-          } else {
-            q = __ldcs(pts + i);
-            if (MODE == LOD_PICK) x = __ldcs(pidx + i);
-          }
-        };
-        const bool publish = wsrc != nullptr && part == 0;
-        int4 q0 = make_int4(0, 0, 0, 0), q1 = q0;
-        uint32_t x0 = 0, x1 = 0;
-        {
-          const uint64_t a0 = threadIdx.x, a1 = a0 + blockDim.x;
-          if (a0 < n) load(a0, q0, x0);
-          if (a1 < n) load(a1, q1, x1);
+          if ((int)lane != __ffs(peers) - 1) return;
         }
-        for (uint64_t base = 0; base < n; base += step) {
-          const uint64_t a0 = base + threadIdx.x, a1 = a0 + blockDim.x;
-          const uint64_t b0 = a0 + step, b1 = a1 + step;
-          int4 r0 = q0, r1 = q1;
-          uint32_t y0 = 0, y1 = 0;
-          if (b0 < n) load(b0, r0, y0);
-          if (b1 < n) load(b1, r1, y1);
-          // the whole warp leaves together: accumulate() uses full-warp
-          // collectives, so no lane may stop while its neighbours go on
-          if (__any_sync(0xFFFFFFFFu, *((volatile uint32_t*)&s_fail) != 0u)) break;
-          if (publish) {  // idempotent: a retried item writes the same values
-            if (a0 < n) {
-              a.out[pbase + a0] = q0;
-              a.out_idx[pbase + a0] = x0;
-            }
-            if (a1 < n) {
-              a.out[pbase + a1] = q1;
-              a.out_idx[pbase + a1] = x1;
-            }
-          }
-          uint32_t k0 = 0u, k1 = 0u;
+        const int slot = find_or_insert(keys, H, key1);
+        if (slot < 0) {
+          S.fail = 1;
+          return;
+        }
+        if (MODE == LOD_PICK) {
+          if (!pick_update(&E[slot], h, (uint64_t)rgba | ((uint64_t)ix << 32))) atomicOr(&ctr->error, kErrInternal);
+          atomicAdd(&cnt32[slot], n_same);
+        } else if (narrow) {
+          atomicAdd(&A0[slot], (uint64_t)r | ((uint64_t)g << 32));
+          atomicAdd(&A1[slot], (uint64_t)b | ((uint64_t)n_same << 32));
+        } else {
+          atomicAdd(&A0[slot], (uint64_t)r);
+          atomicAdd(&A1[slot], (uint64_t)g);
+          atomicAdd(&A2[slot], (uint64_t)b);
+          atomicAdd(&cnt32[slot], n_same);
+        }
+      };
+      // Software pipeline over pairs of points: the loads of the next pair
+      // are in flight while the current pair is hashed and accumulated.
+      auto load = [&](uint64_t i, int4& q, uint32_t& x) {
+        if (wsrc) {
+          ld_wide(wsrc + 2 * i, q, x);
+        } else {
+          q = __ldcs(pts + i);
+          if (MODE == LOD_PICK) x = __ldcs(pidx + i);
+        }
+      };
+      const bool publish = wsrc != nullptr && part == 0;
+      int4 q0 = make_int4(0, 0, 0, 0), q1 = q0;
+      uint32_t x0 = 0, x1 = 0;
+      {
+        const uint64_t a0 = threadIdx.x, a1 = a0 + blockDim.x;
+        if (a0 < n) load(a0, q0, x0);
+        if (a1 < n) load(a1, q1, x1);
+      }
+      for (uint64_t base = 0; base < n; base += step) {
+        const uint64_t a0 = base + threadIdx.x, a1 = a0 + blockDim.x;
+        const uint64_t b0 = a0 + step, b1 = a1 + step;
+        int4 r0 = q0, r1 = q1;
+        uint32_t y0 = 0, y1 = 0;
+        if (b0 < n) load(b0, r0, y0);
+        if (b1 < n) load(b1, r1, y1);
+        // the whole warp leaves together: accumulate() uses full-warp
+        // collectives, so no lane may stop while its neighbours go on
+        if (__any_sync(0xFFFFFFFFu, *((volatile uint32_t*)&S.fail) != 0u)) break;
+        if (publish) {  // idempotent: a retried item writes the same values
           if (a0 < n) {
-            k0 = point_key1(q0, I);
-            if (part_of(k0, mlog) != part) k0 = 0u;
+            a.out[pbase + a0] = q0;
+            a.out_idx[pbase + a0] = x0;
           }
           if (a1 < n) {
-            k1 = point_key1(q1, I);
-            if (part_of(k1, mlog) != part) k1 = 0u;
-          }
-          accumulate(k0, q0, x0);
-          accumulate(k1, q1, x1);
-          q0 = r0;
-          q1 = r1;
-          x0 = y0;
-          x1 = y1;
-        }
-      } else {
-        // inner child: its voxels are the staged records of its own children
-        for (uint32_t r = 0; r < nch; ++r) {
-          const NodeAux& ca = v.aux[fc + r];
-          const int4* rec = v.stage_in + ca.stage;
-          const ulonglong2* sums = (MODE == LOD_FILTER) ? v.stage_in_sum + ca.stage : nullptr;
-          int4* dst = v.dense + ca.dense;
-          const uint32_t m = ca.occ;
-          for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
-            if (*((volatile uint32_t*)&s_fail)) break;
-            const int4 vr = rec[i];
-            if (part == 0) dst[i] = vr;  // publish the child's voxel (idempotent)
-            const uint32_t key1 = voxel_key1((uint32_t)vr.x);
-            if (part_of(key1, mlog) != part) continue;
-            const int slot = find_or_insert(keys, H, key1);
-            if (slot < 0) {
-              s_fail = 1;
-              continue;
-            }
-            if (MODE == LOD_PICK) {
-              const uint32_t idx = (uint32_t)vr.w;
-              if (!pick_update(&E[slot], splitmix64(idx), (uint64_t)(uint32_t)vr.y | ((uint64_t)idx << 32)))
-                atomicOr(&ctr->error, kErrInternal);
-              atomicAdd(&cnt32[slot], (uint32_t)vr.z);
-            } else {
-              const ulonglong2 sm = sums[i];
-              atomicAdd(&A0[slot], sm.x & kMask40);
-              atomicAdd(&A1[slot], (sm.x >> 40) | ((sm.y & 0xFFFFull) << 24));
-              atomicAdd(&A2[slot], sm.y >> 16);
-              atomicAdd(&cnt32[slot], (uint32_t)vr.z);
-            }
+            a.out[pbase + a1] = q1;
+            a.out_idx[pbase + a1] = x1;
           }
         }
+        uint32_t k0 = 0u, k1 = 0u;
+        if (a0 < n) {
+          ++seen;
+          k0 = point_key1(q0, I);
+          if (part_of(k0, mlog) != part) k0 = 0u;
+        }
+        if (a1 < n) {
+          ++seen;
+          k1 = point_key1(q1, I);
+          if (part_of(k1, mlog) != part) k1 = 0u;
+        }
+        accumulate(k0, q0, x0);
+        accumulate(k1, q1, x1);
+        q0 = r0;
+        q1 = r1;
+        x0 = y0;
+        x1 = y1;
       }
-      __syncthreads();
-      if (s_fail) {
-        failed = true;
-        break;
-      }
-      // count this partition's occupied cells, then extract them into staging
-      {
-        uint32_t mine = 0;
-        for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) mine += keys[i] != 0u ? 1u : 0u;
-        mine = __reduce_add_sync(0xFFFFFFFFu, mine);
-        if ((threadIdx.x & 31u) == 0 && mine) atomicAdd(&s_used, mine);
-      }
-      __syncthreads();
-      const uint32_t used = s_used;
-      if (mlog == 0 && threadIdx.x == 0) {
-        s_stage = atomicAdd(v.stage_used, (unsigned long long)used);
-        if (s_stage + used > v.stage_cap) atomicOr(&ctr->error, kErrStageCap);
-      }
-      if (threadIdx.x == 0) s_out = 0;
-      __syncthreads();
-      const bool room = s_stage + out_total + used <= v.stage_cap;
-      const uint32_t lane = threadIdx.x & 31u;
-      for (uint32_t i0 = 0; i0 < H; i0 += blockDim.x) {
-        const uint32_t i = i0 + threadIdx.x;
-        const uint32_t key1 = i < H ? keys[i] : 0u;
-        const bool occ = key1 != 0u;
-        const unsigned bal = __ballot_sync(0xFFFFFFFFu, occ);
-        uint32_t wbase = 0;
-        if (lane == 0 && bal) wbase = atomicAdd(&s_out, (uint32_t)__popc(bal));
-        wbase = __shfl_sync(0xFFFFFFFFu, wbase, 0);
-        if (!occ || !room) continue;
-        const uint64_t o = s_stage + out_total + wbase + __popc(bal & ((1u << lane) - 1u));
-        const uint32_t cell = key_to_cell(key1, I);
-        int4 rec;
-        rec.x = (int)cell;
-        if (MODE == LOD_PICK) {
-          const ulonglong2 e = E[i];
-          const uint32_t best = (uint32_t)(e.y >> 32);
-          if (best >= td.n || splitmix64(best) != e.x) {  // cannot happen for a cell that received a sample
-            atomicOr(&ctr->error, kErrInternal);
+    } else {
+      // inner child: its voxels are the staged records of its own children
+      for (uint32_t r = 0; r < nch; ++r) {
+        const NodeAux& ca = v.aux[fc + r];
+        const int4* rec = v.stage_in + ca.stage;
+        const ulonglong2* sums = (MODE == LOD_FILTER) ? v.stage_in_sum + ca.stage : nullptr;
+        int4* dst = v.dense + ca.dense;
+        const uint32_t m = ca.occ;
+        for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
+          if (*((volatile uint32_t*)&S.fail)) break;
+          const int4 vr = rec[i];
+          ++seen;
+          if (part == 0) dst[i] = vr;  // publish the child's voxel (idempotent)
+          const uint32_t key1 = voxel_key1((uint32_t)vr.x);
+          if (part_of(key1, mlog) != part) continue;
+          const int slot = find_or_insert(keys, H, key1);
+          if (slot < 0) {
+            S.fail = 1;
             continue;
           }
-          rec.y = (int)(uint32_t)e.y;
-          rec.z = (int)cnt32[i];
-          rec.w = (int)best;
-        } else {
-          uint64_t sr, sg, sb, n;
-          if (narrow) {
-            sr = A0[i] & 0xFFFFFFFFull;
-            sg = A0[i] >> 32;
-            sb = A1[i] & 0xFFFFFFFFull;
-            n = A1[i] >> 32;
+          if (MODE == LOD_PICK) {
+            const uint32_t idx = (uint32_t)vr.w;
+            if (!pick_update(&E[slot], splitmix64(idx), (uint64_t)(uint32_t)vr.y | ((uint64_t)idx << 32)))
+              atomicOr(&ctr->error, kErrInternal);
+            atomicAdd(&cnt32[slot], (uint32_t)vr.z);
           } else {
-            sr = A0[i];
-            sg = A1[i];
-            sb = A2[i];
-            n = cnt32[i];
+            const ulonglong2 sm = sums[i];
+            const uint64_t sr = sm.x & kMask40, sg = (sm.x >> 40) | ((sm.y & 0xFFFFull) << 24), sb = sm.y >> 16;
+            if (narrow) {
+              atomicAdd(&A0[slot], sr | (sg << 32));
+              atomicAdd(&A1[slot], sb | ((uint64_t)(uint32_t)vr.z << 32));
+            } else {
+              atomicAdd(&A0[slot], sr);
+              atomicAdd(&A1[slot], sg);
+              atomicAdd(&A2[slot], sb);
+              atomicAdd(&cnt32[slot], (uint32_t)vr.z);
+            }
           }
-          rec.y = (int)mean_rgba(sr, sg, sb, n);
-          rec.z = (int)n;
-          rec.w = (int)kNone;
-          ulonglong2 sm;
-          sm.x = sr | (sg << 40);
-          sm.y = (sg >> 24) | (sb << 16);
-          v.stage_out_sum[o] = sm;
         }
-        v.stage_out[o] = rec;
       }
-      out_total += used;
-      __syncthreads();
     }
-    if (threadIdx.x == 0) atomicAdd(&ctr->vox_passes, (unsigned long long)P);
-    if (!failed) break;
-    if (threadIdx.x == 0 && mlog == 0) atomicAdd(&ctr->vox_retries, 1ull);
-    // more partitions: first try two, then enough for the worst case
-    const uint32_t need = (uint32_t)((cap + table_capacity(H) - 1) / table_capacity(H));
-    uint32_t bound = 0;
-    while ((1u << bound) < need) ++bound;
-    mlog = mlog == 0 ? 1u : max(mlog + 1, bound);
+    __syncthreads();  // every insert of the pass is done
+    // occupied cells of this pass, and how far the pass got
+    {
+      uint32_t mine = 0;
+      for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) mine += keys[i] != 0u ? 1u : 0u;
+      mine = __reduce_add_sync(0xFFFFFFFFu, mine);
+      seen = __reduce_add_sync(0xFFFFFFFFu, seen);
+      if (lane == 0) {
+        if (mine) atomicAdd(&S.used, mine);
+        if (seen) atomicAdd(&S.seen, seen);
+      }
+    }
     __syncthreads();
+    const uint32_t used = S.used;
+
+    if (S.fail) {
+      split = true;
+      if (threadIdx.x == 0) {
+        bool handed = false;
+        if (first && mlog == 0) {
+          // the cells of the whole item get one staging block, filled by
+          // the passes over its partitions in any order
+          S.base = atomicAdd(v.stage_used, (unsigned long long)bound);
+          if (S.base + bound > v.stage_cap) atomicOr(&ctr->error, kErrStageCap);
+          v.aux[I.g].stage = S.base;
+          v.aux[I.g].occ = 0u;
+          if (v.units) {
+            // occupied cells projected from the part seen so far
+            const uint64_t sn = S.seen ? S.seen : 1u;
+            const uint64_t est = umin64(bound, (uint64_t)used * I.n / sn + (uint64_t)used / 4 + 1);
+            const uint64_t per = table_capacity(H) / 4 * 3;
+            uint32_t m = 1;
+            while (m < kMaxQueuedLog && (est >> m) > per) ++m;
+            uint32_t q0 = 0;
+            if (reserve_units(&ctr->units, v.unit_cap, 1u << m, &q0)) {
+              for (uint32_t j = 0; j < (1u << m); ++j) v.units[q0 + j] = make_uint4(it, j, m, 0u);
+              handed = true;
+              S.queued = 1;
+            }
+          }
+        }
+        if (!handed) {
+          if (mlog >= kMaxPartLog) {
+            atomicOr(&ctr->error, kErrInternal);
+          } else {  // split this partition in two, depth first
+            S.stack[S.sp] = make_uint2(2 * part + 1, mlog + 1);
+            S.stack[S.sp + 1] = make_uint2(2 * part, mlog + 1);
+            S.sp += 2;
+          }
+        }
+      }
+      continue;
+    }
+
+    // extract this pass's occupied cells into staging
+    if (threadIdx.x == 0) {
+      if (first && mlog == 0) {  // the whole item in one pass
+        S.base = atomicAdd(v.stage_used, (unsigned long long)used);
+        if (S.base + used > v.stage_cap) atomicOr(&ctr->error, kErrStageCap);
+        v.aux[I.g].stage = S.base;
+        v.aux[I.g].occ = used;
+      } else {  // one partition: append to the item's block
+        const uint64_t blk = v.aux[I.g].stage;
+        const uint32_t o = atomicAdd(&v.aux[I.g].occ, used);
+        S.base = blk + o;
+        if (o + used > bound || blk + o + used > v.stage_cap) atomicOr(&ctr->error, kErrStageCap);
+      }
+      S.out = 0;
+    }
+    __syncthreads();
+    const bool room = S.base + used <= v.stage_cap;
+    for (uint32_t i0 = 0; i0 < H; i0 += blockDim.x) {
+      const uint32_t i = i0 + threadIdx.x;
+      const uint32_t key1 = i < H ? keys[i] : 0u;
+      const bool occ = key1 != 0u;
+      const unsigned bal = __ballot_sync(0xFFFFFFFFu, occ);
+      uint32_t wbase = 0;
+      if (lane == 0 && bal) wbase = atomicAdd(&S.out, (uint32_t)__popc(bal));
+      wbase = __shfl_sync(0xFFFFFFFFu, wbase, 0);
+      if (!occ || !room) continue;
+      const uint64_t o = S.base + wbase + __popc(bal & ((1u << lane) - 1u));
+      const uint32_t cell = key_to_cell(key1, I);
+      int4 rec;
+      rec.x = (int)cell;
+      if (MODE == LOD_PICK) {
+        const ulonglong2 e = E[i];
+        const uint32_t best = (uint32_t)(e.y >> 32);
+        if (best >= td.n || splitmix64(best) != e.x) {  // cannot happen for a cell that received a sample
+          atomicOr(&ctr->error, kErrInternal);
+          continue;
+        }
+        rec.y = (int)(uint32_t)e.y;
+        rec.z = (int)cnt32[i];
+        rec.w = (int)best;
+      } else {
+        uint64_t sr, sg, sb, n;
+        if (narrow) {
+          sr = A0[i] & 0xFFFFFFFFull;
+          sg = A0[i] >> 32;
+          sb = A1[i] & 0xFFFFFFFFull;
+          n = A1[i] >> 32;
+        } else {
+          sr = A0[i];
+          sg = A1[i];
+          sb = A2[i];
+          n = cnt32[i];
+        }
+        rec.y = (int)mean_rgba(sr, sg, sb, n);
+        rec.z = (int)n;
+        rec.w = (int)kNone;
+        ulonglong2 sm;
+        sm.x = sr | (sg << 40);
+        sm.y = (sg >> 24) | (sb << 16);
+        v.stage_out_sum[o] = sm;
+      }
+      v.stage_out[o] = rec;
+    }
   }
   if (threadIdx.x == 0) {
-    v.aux[I.g].stage = s_stage == ~0ull ? 0ull : s_stage;
-    v.aux[I.g].occ = (uint32_t)out_total;
+    atomicAdd(&ctr->vox_passes, (unsigned long long)passes);
+    if (split && first) atomicAdd(&ctr->vox_retries, 1ull);
   }
+  __syncthreads();
+}
+
+// First attempt: one CTA per item.
+template <int MODE>
+__global__ void __launch_bounds__(kBlock, 1) k_vox(BuildArgs a, VoxLevel v, DevCounters* __restrict__ ctr) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ VoxShared S;
+  vox_item<MODE>(a, v, ctr, smem, S, blockIdx.x, 0u, 0u, true);
+}
+
+// Partitions of the items that overflowed their first attempt, taken from
+// the queue by persistent CTAs (the queue is complete when this starts).
+template <int MODE>
+__global__ void __launch_bounds__(kBlock, 1) k_vox_units(BuildArgs a, VoxLevel v, DevCounters* __restrict__ ctr) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ VoxShared S;
+  __shared__ uint32_t s_unit;
+  const uint32_t n_units = min(ctr->units, v.unit_cap);
+  for (;;) {
+    if (threadIdx.x == 0) s_unit = atomicAdd(&ctr->unit_head, 1u);
+    __syncthreads();
+    const uint32_t u = s_unit;
+    __syncthreads();
+    if (u >= n_units) break;
+    const uint4 w = v.units[u];
+    vox_item<MODE>(a, v, ctr, smem, S, w.x, w.y, w.z, false);
+  }
+}
+
+template <int MODE>
+static cudaError_t launch_vox_mode(const BuildArgs& a, const VoxLevel& v, DevCounters* ctr, cudaStream_t st) {
+  static int sms = [] {
+    cudaFuncSetAttribute(k_vox<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaFuncSetAttribute(k_vox_units<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+  }();
+  k_vox<MODE><<<v.n_items, kBlock, kSmemBytes, st>>>(a, v, ctr);
+  if (v.units) k_vox_units<MODE><<<sms, kBlock, kSmemBytes, st>>>(a, v, ctr);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_vox(const BuildArgs& a, const VoxLevel& v, DevCounters* ctr, cudaStream_t st) {
   if (!v.n_items) return cudaSuccess;
-  if (a.mode == LOD_PICK) {
-    static bool once = [] {
-      cudaFuncSetAttribute(k_vox<LOD_PICK>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-      return true;
-    }();
-    (void)once;
-    k_vox<LOD_PICK><<<v.n_items, kBlock, kSmemBytes, st>>>(a, v, ctr);
-  } else {
-    static bool once = [] {
-      cudaFuncSetAttribute(k_vox<LOD_FILTER>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-      return true;
-    }();
-    (void)once;
-    k_vox<LOD_FILTER><<<v.n_items, kBlock, kSmemBytes, st>>>(a, v, ctr);
-  }
-  return cudaGetLastError();
+  return a.mode == LOD_PICK ? launch_vox_mode<LOD_PICK>(a, v, ctr, st) : launch_vox_mode<LOD_FILTER>(a, v, ctr, st);
 }
 
 // Assign every item its place in the level's contiguous voxel block

@@ -39,6 +39,8 @@ struct VoxLevel {
   const ulonglong2* stage_in_sum;
   int4* dense;                 // public voxel array
   unsigned long long* stage_used;
+  uint4* units;                // queue of {item, partition, log2 partitions} for overflowing items
+  uint32_t unit_cap;
 };
 cudaError_t launch_vox(const BuildArgs& a, const VoxLevel& v, DevCounters* ctr, cudaStream_t st);
 cudaError_t launch_level_scan(const BuildArgs& a, const VoxLevel& v, const uint32_t* parent_prefix,

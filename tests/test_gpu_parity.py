@@ -128,6 +128,16 @@ def test_random_tiny_deep_trees(lod, seed):
             check(pts, got, T, mode, max_depth)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("extra", [0, 1])
+def test_threshold_boundary(lod, mode, extra):
+    # exactly T points stay one leaf; T + 1 points split (leaf iff n <= T)
+    T = 5000
+    pts = synth.sphere(T + extra, seed=11)
+    got = parity(lod, pts, T, mode)
+    assert (len(got["level"]) == 1) == (extra == 0)
+
+
 # --------------------------------------------------- workload-shaped inputs
 
 @pytest.mark.parametrize("mode", [0, 1])
