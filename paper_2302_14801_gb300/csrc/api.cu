@@ -305,7 +305,7 @@ struct lod_server {
       lodk::TileInput ti{rq->d_points, rq->n};
       std::shared_ptr<lodk::SharedBuffers> sh;
       std::vector<lodk::TileResult> tr;
-      int rc = lodk::run_build(&ti, 1, rq->params, st, &sh, &tr, nullptr);
+      int rc = lodk::run_build(&ti, 1, rq->params, st, &sh, &tr, nullptr, /*use_workspace=*/false);
       lod_result_t* res = nullptr;
       if (rc == LOD_OK) {
         res = make_result(sh, tr[0], rq->params.mode, sh->bytes);

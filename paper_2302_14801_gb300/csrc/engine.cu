@@ -9,6 +9,7 @@
 // once per voxel level.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <climits>
 #include <cstdio>
 #include <cstdlib>
@@ -39,41 +40,135 @@ int sm_count() {
   return n > 0 ? n : 1;
 }
 
-// Stream-ordered device buffer released on destruction.
+// Device scratch kept between the builds of one stream.  Blocks are handed
+// out best fit and given back when a buffer is released; the same stream
+// enqueues every later use, so reuse is stream ordered.  Steady-state
+// builds thus make no allocator calls for scratch (large stream-ordered
+// allocations from a fragmented pool can take a fraction of a
+// millisecond each).  A workspace serves one build at a time.
+struct Workspace {
+  struct Block {
+    void* p;
+    size_t bytes;
+    bool used;
+  };
+  std::vector<Block> blocks;
+  bool busy = false;
+  int take(size_t b) {
+    int best = -1;
+    for (size_t i = 0; i < blocks.size(); ++i)
+      if (!blocks[i].used && blocks[i].bytes >= b && (best < 0 || blocks[i].bytes < blocks[best].bytes))
+        best = (int)i;
+    if (best < 0) {
+      const size_t r = (b + (2u << 20) - 1) & ~size_t((2u << 20) - 1);
+      void* p = nullptr;
+      if (cudaMalloc(&p, r) != cudaSuccess) {
+        (void)cudaGetLastError();
+        // give the idle blocks back and retry once
+        for (auto& k : blocks)
+          if (!k.used && k.p) {
+            cudaFree(k.p);
+            k.p = nullptr;
+            k.bytes = 0;
+          }
+        if (cudaMalloc(&p, r) != cudaSuccess) {
+          (void)cudaGetLastError();
+          return -1;
+        }
+      }
+      for (size_t i = 0; i < blocks.size(); ++i)
+        if (!blocks[i].p) {
+          blocks[i] = {p, r, false};
+          best = (int)i;
+          break;
+        }
+      if (best < 0) {
+        blocks.push_back({p, r, false});
+        best = (int)blocks.size() - 1;
+      }
+    }
+    blocks[best].used = true;
+    return best;
+  }
+};
+
+std::mutex g_ws_mu;
+std::map<std::pair<int, cudaStream_t>, Workspace*> g_ws;
+
+// Exclusive use of the calling stream's workspace for one build (none when
+// another build on the same stream holds it, or when disabled).
+struct WsLease {
+  Workspace* ws = nullptr;
+  WsLease(cudaStream_t st, bool enable) {
+    if (!enable) return;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    Workspace*& w = g_ws[{dev, st}];
+    if (!w) w = new Workspace();
+    if (w->busy) return;
+    w->busy = true;
+    ws = w;
+  }
+  ~WsLease() {
+    if (!ws) return;
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    ws->busy = false;
+  }
+};
+
+// Stream-ordered device buffer released on destruction; from the build's
+// workspace when it has one (scratch), else from the stream-ordered pool
+// (results, which outlive the build).
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
   cudaStream_t st;
-  explicit DevBuf(cudaStream_t s) : st(s) {}
+  Workspace* ws = nullptr;
+  int blk = -1;
+  explicit DevBuf(cudaStream_t s, Workspace* w = nullptr) : st(s), ws(w) {}
   DevBuf(const DevBuf&) = delete;
   ~DevBuf() { release(); }
   cudaError_t alloc(size_t b) {
     release();
     if (b == 0) b = 16;
+    if (ws) {
+      const int k = ws->take(b);
+      if (k >= 0) {
+        blk = k;
+        p = ws->blocks[k].p;
+        bytes = b;
+        return cudaSuccess;
+      }
+    }
     bytes = b;
     return cudaMallocAsync(&p, b, st);
   }
   // grow keeping the first `keep` bytes
   cudaError_t grow(size_t b, size_t keep) {
     if (b <= bytes) return cudaSuccess;
-    void* q = nullptr;
-    cudaError_t e = cudaMallocAsync(&q, b, st);
+    DevBuf q(st, ws);
+    cudaError_t e = q.alloc(b);
     if (e != cudaSuccess) return e;
     if (p && keep) {
-      e = cudaMemcpyAsync(q, p, std::min(keep, bytes), cudaMemcpyDeviceToDevice, st);
+      e = cudaMemcpyAsync(q.p, p, std::min(keep, bytes), cudaMemcpyDeviceToDevice, st);
       if (e != cudaSuccess) return e;
     }
-    release();
-    p = q;
-    bytes = b;
+    std::swap(p, q.p);
+    std::swap(bytes, q.bytes);
+    std::swap(blk, q.blk);
     return cudaSuccess;
   }
   void release() {
-    if (p) cudaFreeAsync(p, st);
+    if (p) {
+      if (blk >= 0) ws->blocks[blk].used = false;
+      else cudaFreeAsync(p, st);
+    }
     p = nullptr;
     bytes = 0;
+    blk = -1;
   }
-  void* take() {
+  void* take() {  // only for pool buffers
     void* q = p;
     p = nullptr;
     bytes = 0;
@@ -233,8 +328,11 @@ cudaEvent_t pool_event() {
   return e;
 }
 
+bool debug_stats();
+
 // Brackets every launch of one build with events on the build stream when
 // profiling is on; resolves them after the build's host synchronisations.
+// With LOD_DEBUG_STATS the launches' device timeline is printed as well.
 struct Prof {
   struct Rec {
     const char* name;
@@ -244,6 +342,8 @@ struct Prof {
   cudaStream_t st;
   bool on;
   cudaEvent_t a = nullptr;
+  cudaEvent_t origin = nullptr;  // first event of the build (timeline printing)
+  std::string timeline;
   std::vector<Rec> recs;
   explicit Prof(cudaStream_t s) : st(s), on(g_prof_on.load()) {}
   ~Prof() {
@@ -253,9 +353,15 @@ struct Prof {
       g_event_pool.push_back(r.a);
       g_event_pool.push_back(r.b);
     }
+    if (origin) g_event_pool.push_back(origin);
+    if (!timeline.empty()) std::fprintf(stderr, "[lod] device ms:%s\n", timeline.c_str());
   }
   void begin() {
     if (!on) return;
+    if (!origin && debug_stats()) {
+      origin = pool_event();
+      if (origin) cudaEventRecord(origin, st);
+    }
     a = pool_event();
     if (a) cudaEventRecord(a, st);
   }
@@ -274,6 +380,15 @@ struct Prof {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     for (auto& r : recs) {
       float ms = 0.f;
+      if (origin) {
+        float t0 = 0.f, t1 = 0.f;
+        if (cudaEventElapsedTime(&t0, origin, r.a) == cudaSuccess &&
+            cudaEventElapsedTime(&t1, origin, r.b) == cudaSuccess) {
+          char buf[96];
+          std::snprintf(buf, sizeof(buf), " %s@%.3f-%.3f", r.name, t0, t1);
+          timeline += buf;
+        }
+      }
       if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
         KStat& k = g_prof[r.name];
         k.launches += 1;
@@ -377,11 +492,14 @@ uint64_t estimate_build_bytes(uint64_t n, const lod_params_t& p) {
   const uint32_t d = choose_root_depth(n, (uint32_t)T, 32, 32);
   const uint64_t pool = (2 * pyr_size(d) + ipow8(d) + ipow8(d) / 32 + 1) * 4;
   const uint64_t nodes = 64 + 16 * ((n + T - 1) / T);
-  // result + one refinement buffer + two staging levels + node aux + pool,
-  // plus the 32-byte leaf staging of modes that keep input indices
+  // result + one refinement buffer + two staging levels of one record per
+  // point (plus exact sums when filtering) + the voxel array's first
+  // estimate + node aux + pool, plus the 32-byte leaf staging of modes that
+  // keep input indices
   const bool keep_idx = p.mode == LOD_PICK || (p.flags & LOD_FLAG_LEAF_INDEX);
-  return estimate_result_bytes(n, p) + n * 20 + n * 40 + (keep_idx ? n * 32 : 0) + nodes * sizeof(NodeAux) + pool +
-         (16u << 20);
+  const uint64_t staging = n * (p.mode == LOD_FILTER ? 64 : 32);
+  return estimate_result_bytes(n, p) + n * 20 + staging + n * 8 + (keep_idx ? n * 32 : 0) +
+         nodes * sizeof(NodeAux) + pool + (16u << 20);
 }
 
 // Keep freed blocks of the device's stream-ordered pool instead of returning
@@ -402,9 +520,33 @@ static void retain_pool_memory() {
   done[dev] = true;
 }
 
+// Host-side phase clock of one build (printed with LOD_DEBUG_STATS).
+struct PhaseClock {
+  bool on = debug_stats();
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now(), last = t0;
+  std::string line;
+  void tick(const char* what) {
+    if (!on) return;
+    const auto now = std::chrono::steady_clock::now();
+    char buf[96];
+    std::snprintf(buf, sizeof(buf), " %s +%.3f", what, std::chrono::duration<double, std::milli>(now - last).count());
+    line += buf;
+    last = now;
+  }
+  ~PhaseClock() {
+    if (on)
+      std::fprintf(stderr, "[lod] host ms:%s | total %.3f\n", line.c_str(),
+                   std::chrono::duration<double, std::milli>(last - t0).count());
+  }
+};
+
 int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaStream_t st,
-              std::shared_ptr<SharedBuffers>* shared_out, std::vector<TileResult>* tiles_out, BuildStats* stats) {
+              std::shared_ptr<SharedBuffers>* shared_out, std::vector<TileResult>* tiles_out, BuildStats* stats,
+              bool use_workspace) {
   BuildStats S;
+  PhaseClock clk;
+  WsLease lease(st, use_workspace);  // declared first: outlives every scratch buffer
+  Workspace* const ws = lease.ws;
   if (nt == 0 || !tin) return LOD_ERR_INVALID_ARG;
   retain_pool_memory();
   if (prm.leaf_threshold == 0 || prm.mode > 1 || prm.max_depth > 32) return LOD_ERR_INVALID_ARG;
@@ -446,8 +588,8 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
     ++S.launches;                     \
   } while (0)
 
-  DevBuf d_points(st), d_index(st), d_tiles(st), d_chunk0(st), d_chunk_src(st), d_bbox(st), d_ctr(st),
-      d_nchunks(st);
+  DevBuf d_points(st), d_index(st);  // results
+  DevBuf d_tiles(st, ws), d_chunk0(st, ws), d_chunk_src(st, ws), d_bbox(st, ws), d_ctr(st, ws), d_nchunks(st, ws);
   LOD_CK(d_points.alloc(M * 16));
   if (want_idx) LOD_CK(d_index.alloc(M * 4));
   LOD_CK(d_tiles.alloc(nt * sizeof(TileDesc)));
@@ -478,6 +620,7 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
   std::vector<int> bbox(6 * nt);
   LOD_CK(cudaMemcpyAsync(bbox.data(), d_bbox.p, bbox.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
   LOD_CK(cudaStreamSynchronize(st));
+  clk.tick("bbox");
   up_.recycle();
   prof.resolve();
   ++S.host_syncs;
@@ -514,7 +657,8 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
   }
 
   // ---- counting rounds
-  DevBuf d_srcs(st), d_jobs(st), d_tmp0(st), d_tmp1(st), d_tmpi0(st), d_tmpi1(st), d_lists(st), d_llen(st);
+  DevBuf d_srcs(st, ws), d_jobs(st, ws), d_tmp0(st, ws), d_tmp1(st, ws), d_tmpi0(st, ws), d_tmpi1(st, ws),
+      d_lists(st, ws), d_llen(st, ws);
   LOD_CK(d_lists.alloc((size_t)grid * kPrivSlots * sizeof(uint2)));
   LOD_CK(d_llen.alloc((size_t)grid * sizeof(uint32_t)));
   std::vector<std::unique_ptr<DevBuf>> pools;
@@ -532,12 +676,12 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
   A.lists = d_lists.as<uint2>();
   A.list_len = d_llen.as<uint32_t>();
   // modes that keep input indices stage each leaf point as one 32-byte record
-  DevBuf d_wide(st);
+  DevBuf d_wide(st, ws);
   if (want_idx) {
     LOD_CK(d_wide.alloc(M * 32));
     A.wide = d_wide.as<int4>();
   }
-  DevBuf d_diag(st);
+  DevBuf d_diag(st, ws);
   if (debug_stats()) {
     LOD_CK(d_diag.alloc(4 * sizeof(unsigned long long)));
     LOD_CK(cudaMemsetAsync(d_diag.p, 0, 4 * sizeof(unsigned long long), st));
@@ -551,7 +695,7 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
     // pool for this round's grids
     std::vector<uint64_t> offs;
     const PoolLayout L = layout_pool(srcs, round_first, round_n, &offs);
-    pools.emplace_back(new DevBuf(st));
+    pools.emplace_back(new DevBuf(st, ws));
     DevBuf& pool = *pools.back();
     LOD_CK(pool.alloc(L.total * 4));
     LOD_CK(cudaMemsetAsync(pool.p, 0, L.zero * 4, st));
@@ -630,24 +774,10 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
                                  (uint32_t)(src_cap - n_src), next_buf, d_ctr.as<DevCounters>(), st));
       jo += v.size();
     }
-    DevCounters* hc = static_cast<DevCounters*>(tl_stage.get(sizeof(DevCounters)));
-    if (!hc) return LOD_ERR_OOM;
-    LOD_CK(cudaMemcpyAsync(hc, d_ctr.p, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
-    LOD_CK(cudaStreamSynchronize(st));
-    up_.recycle();
-    prof.resolve();
-    ++S.host_syncs;
-    if (hc->error) return LOD_ERR_INTERNAL;
-    if (A.diag) {
-      unsigned long long dg[2] = {0, 0};
-      LOD_CK(cudaMemcpy(dg, A.diag, sizeof(dg), cudaMemcpyDeviceToHost));
-      std::fprintf(stderr, "[lod] round %u: %u grids, %llu points, root depth %u, %llu counted outside "
-                   "the CTA tables, %llu table inserts\n", round, round_n, (unsigned long long)round_points,
-                   srcs[round_first].d, dg[0], dg[1]);
-    }
-    const uint32_t new_srcs = (uint32_t)hc->new_srcs;
-    const uint64_t new_points = hc->new_points;
-    if (new_srcs) {
+    // the cells refined by this round (if any) go to a ping-pong buffer; it
+    // is set up before the counters are known so that the scatter follows
+    // the pyramid without a host round trip
+    {
       DevBuf& tb = (round & 1) ? d_tmp1 : d_tmp0;
       DevBuf& ti = (round & 1) ? d_tmpi1 : d_tmpi0;
       if (!tb.p) {
@@ -661,6 +791,24 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
     }
     LOD_LAUNCH("scatter", 32.0 * round_points,
                launch_scatter(A, d_chunk_src.as<uint32_t>(), d_nchunks.as<unsigned long long>(), round, cgrid, st));
+    DevCounters* hc = static_cast<DevCounters*>(tl_stage.get(sizeof(DevCounters)));
+    if (!hc) return LOD_ERR_OOM;
+    LOD_CK(cudaMemcpyAsync(hc, d_ctr.p, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+    LOD_CK(cudaStreamSynchronize(st));
+    clk.tick("round");
+    up_.recycle();
+    prof.resolve();
+    ++S.host_syncs;
+    if (hc->error) return LOD_ERR_INTERNAL;
+    if (A.diag) {
+      unsigned long long dg[2] = {0, 0};
+      LOD_CK(cudaMemcpy(dg, A.diag, sizeof(dg), cudaMemcpyDeviceToHost));
+      std::fprintf(stderr, "[lod] round %u: %u grids, %llu points, root depth %u, %llu counted outside "
+                   "the CTA tables, %llu table inserts\n", round, round_n, (unsigned long long)round_points,
+                   srcs[round_first].d, dg[0], dg[1]);
+    }
+    const uint32_t new_srcs = (uint32_t)hc->new_srcs;
+    const uint64_t new_points = hc->new_points;
     if (!new_srcs) break;
 
     // next round: the new grids, their chunk space
@@ -668,8 +816,7 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
     LOD_CK(cudaMemcpyAsync(srcs.data() + n_src, d_srcs.as<SrcDesc>() + n_src, new_srcs * sizeof(SrcDesc),
                            cudaMemcpyDeviceToHost, st));
     LOD_CK(cudaStreamSynchronize(st));
-    up_.recycle();
-    prof.resolve();
+    clk.tick("new_srcs");
     ++S.host_syncs;
     round_first = n_src;
     round_n = new_srcs;
@@ -694,7 +841,8 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
   // ---- node tables
   std::vector<uint32_t> node_cap(nt);
   for (uint32_t t = 0; t < nt; ++t) node_cap[t] = (uint32_t)std::min<uint64_t>(64 + 16 * ((td[t].n + T - 1) / T), 0x7FFFFFFFull);
-  DevBuf d_nodes(st), d_aux(st), d_lvl(st), d_nn(st), d_leafcap(st);
+  DevBuf d_nodes(st);  // result
+  DevBuf d_aux(st, ws), d_lvl(st, ws), d_nn(st, ws), d_leafcap(st, ws);
   std::vector<uint32_t> n_nodes(nt), lvl((size_t)nt * (kMaxLevels + 1));
   // [0, L): per level sum of min(leaf points, 64^3); [L, 2L): exact leaf points
   std::vector<unsigned long long> leaf_cap(2 * (kMaxLevels + 1));
@@ -721,6 +869,7 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
     LOD_CK(cudaMemcpyAsync(lvl.data(), d_lvl.p, lvl.size() * 4, cudaMemcpyDeviceToHost, st));
     LOD_CK(cudaMemcpyAsync(leaf_cap.data(), d_leafcap.p, leaf_cap.size() * 8, cudaMemcpyDeviceToHost, st));
     LOD_CK(cudaStreamSynchronize(st));
+    clk.tick("nodes");
     up_.recycle();
     prof.resolve();
     ++S.host_syncs;
@@ -748,110 +897,134 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
   d_tmpi0.release();
   d_tmpi1.release();
 
-  // ---- voxel levels, bottom-up
-  DevBuf d_dense(st), d_stage0(st), d_stage1(st), d_sum0(st), d_sum1(st), d_itemp(st), d_parp(st), d_tvox(st);
-  DevBuf d_units(st);  // queue of partition units of overflowing voxel items
-  uint32_t units_cap = 0;
+  // ---- voxel levels, bottom-up (Section 4.2).  Every level is enqueued
+  // without a host round trip: the staging of one level holds at most one
+  // record per point under its items (so M records always suffice), each
+  // level's place in the voxel array is kept on the device, and the voxel
+  // array starts at an estimate; if the levels need more, the phase is run
+  // once more with the exact size (every step of it is idempotent).
+  DevBuf d_dense(st);  // result
+  DevBuf d_stage0(st, ws), d_stage1(st, ws), d_sum0(st, ws), d_sum1(st, ws), d_pref(st, ws), d_tvox(st, ws);
+  DevBuf d_units(st, ws), d_lctr(st, ws), d_vstate(st, ws);
   const bool filt = prm.mode == LOD_FILTER;
-  uint64_t dense_cap = std::max<uint64_t>(M / 2, 1024);
-  LOD_CK(d_dense.alloc(dense_cap * 16));
-  LOD_CK(d_tvox.alloc(nt * 8));
-  LOD_CK(cudaMemsetAsync(d_tvox.p, 0, nt * 8, st));
-  LOD_CK(d_itemp.alloc((nt + 1) * 4));
-  LOD_CK(d_parp.alloc((nt + 1) * 4));
-  uint64_t V = 0, inner_cap = 0, V_child = 0, V_top = 0;
-  uint64_t stage_cap[2] = {0, 0};
-  VoxLevel vl;
-  std::memset(&vl, 0, sizeof(vl));
-  bool have_top = false;
-  std::vector<uint32_t> item_prefix(nt + 1), parent_prefix(nt + 1);
-  for (int l = (int)max_levels - 2; l >= 0; --l) {
-    // items: nodes at level l + 1; parents: nodes at level l
-    item_prefix[0] = parent_prefix[0] = 0;
+  const int n_vlev = max_levels >= 2 ? (int)max_levels - 1 : 0;  // parent levels max_levels-2 .. 0
+  const size_t pstride = 2 * (size_t)(nt + 1);
+  std::vector<uint32_t> pref((size_t)std::max(n_vlev, 1) * pstride, 0u);
+  uint32_t max_items = 1;
+  for (int l = 0; l < n_vlev; ++l) {
+    uint32_t* ip = &pref[(size_t)l * pstride];  // items (nodes at level l + 1) per tile, prefix
+    uint32_t* pp = ip + (nt + 1);               // parents (nodes at level l) per tile, prefix
     for (uint32_t t = 0; t < nt; ++t) {
       const uint32_t* ls = &lvl[(size_t)t * (kMaxLevels + 1)];
-      item_prefix[t + 1] = item_prefix[t] + (ls[l + 2] - ls[l + 1]);
-      parent_prefix[t + 1] = parent_prefix[t] + (ls[l + 1] - ls[l]);
+      ip[t + 1] = ip[t] + (ls[l + 2] - ls[l + 1]);
+      pp[t + 1] = pp[t] + (ls[l + 1] - ls[l]);
     }
-    const uint32_t n_items = item_prefix[nt], n_par = parent_prefix[nt];
-    const int par = (l + 1) & 1;
-    DevBuf& stg = par ? d_stage1 : d_stage0;
-    DevBuf& sum = par ? d_sum1 : d_sum0;
-    const uint64_t bound = leaf_cap[l + 1] + inner_cap + 1;
-    if (bound > stage_cap[par]) {
-      LOD_CK(stg.alloc(bound * 16));
-      if (filt) LOD_CK(sum.alloc(bound * 16));
-      stage_cap[par] = bound;
-    }
-    LOD_CK(up_.put(d_itemp.p, item_prefix.data(), (nt + 1) * 4));
-    LOD_CK(up_.put(d_parp.p, parent_prefix.data(), (nt + 1) * 4));
-    LOD_CK(cudaMemsetAsync(d_ctr.p, 0, sizeof(DevCounters), st));
-    vl.level = (uint32_t)l;
-    vl.n_items = n_items;
-    vl.item_prefix = d_itemp.as<uint32_t>();
-    vl.lvl_start = d_lvl.as<uint32_t>();
-    vl.nodes = d_nodes.as<lod_node_t>();
-    vl.aux = d_aux.as<NodeAux>();
-    vl.stage_out = stg.as<int4>();
-    vl.stage_out_sum = filt ? sum.as<ulonglong2>() : nullptr;
-    vl.stage_cap = stage_cap[par];
-    vl.stage_in = (par ? d_stage0 : d_stage1).as<int4>();
-    vl.stage_in_sum = filt ? (par ? d_sum0 : d_sum1).as<ulonglong2>() : nullptr;
-    vl.dense = d_dense.as<int4>();
-    vl.stage_used = &d_ctr.as<DevCounters>()->stage_used[par];
-    const uint32_t want_units = (uint32_t)std::min<uint64_t>((uint64_t)n_items * 64, 1u << 20);
-    if (want_units > units_cap) {
-      LOD_CK(d_units.alloc((size_t)want_units * sizeof(uint4)));
-      units_cap = want_units;
-    }
-    vl.units = d_units.as<uint4>();
-    vl.unit_cap = units_cap;
-    A.tiles = d_tiles.as<TileDesc>();
-    static const char* kVoxLevelNames[kMaxLevels] = {
-        "voxelize_L00", "voxelize_L01", "voxelize_L02", "voxelize_L03", "voxelize_L04", "voxelize_L05",
-        "voxelize_L06", "voxelize_L07", "voxelize_L08", "voxelize_L09", "voxelize_L10", "voxelize_L11",
-        "voxelize_L12", "voxelize_L13", "voxelize_L14", "voxelize_L15", "voxelize_L16", "voxelize_L17",
-        "voxelize_L18", "voxelize_L19", "voxelize_L20", "voxelize_L21", "voxelize_L22", "voxelize_L23",
-        "voxelize_L24", "voxelize_L25", "voxelize_L26", "voxelize_L27", "voxelize_L28", "voxelize_L29",
-        "voxelize_L30", "voxelize_L31", "voxelize_L32", "voxelize_L33"};
-    LOD_LAUNCH(debug_stats() ? kVoxLevelNames[l] : "voxelize", 0, launch_vox(A, vl, d_ctr.as<DevCounters>(), st));
-    const size_t vox_rec = prof.recs.size();
-    LOD_LAUNCH("level_scan", 0,
-               launch_level_scan(A, vl, d_parp.as<uint32_t>(), n_par, V, d_tvox.as<unsigned long long>(),
-                                 d_ctr.as<DevCounters>(), st));
-    DevCounters* hc = static_cast<DevCounters*>(tl_stage.get(sizeof(DevCounters)));
-    if (!hc) return LOD_ERR_OOM;
-    LOD_CK(cudaMemcpyAsync(hc, d_ctr.p, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
-    LOD_CK(cudaStreamSynchronize(st));
-    up_.recycle();
-    ++S.host_syncs;
-    if (hc->error) return LOD_ERR_INTERNAL;
-    V += hc->level_voxels;
-    inner_cap = hc->next_cap;
-    if (prof.on && vox_rec >= 1 && vox_rec <= prof.recs.size()) {
-      // reads: leaf points and the children's voxels; writes: this level's voxels
-      prof.recs[vox_rec - 1].bytes =
-          16.0 * (double)(leaf_cap[kMaxLevels + 1 + l + 1] + V_child + hc->level_voxels);
-    }
-    prof.resolve();
-    if (debug_stats())
-      std::fprintf(stderr, "[lod] level %d: items %u (leaf points %llu, child voxels %llu) -> voxels %llu, "
-                   "retried items %llu, table passes %llu\n", l, n_items,
-                   (unsigned long long)leaf_cap[kMaxLevels + 1 + l + 1], (unsigned long long)V_child,
-                   (unsigned long long)hc->level_voxels, (unsigned long long)hc->vox_retries,
-                   (unsigned long long)hc->vox_passes);
-    V_child = hc->level_voxels;
-    V_top = hc->level_voxels;
-    if (V > dense_cap) {
-      const uint64_t nc = std::max<uint64_t>(V, dense_cap * 2);
-      LOD_CK(d_dense.grow(nc * 16, (V - hc->level_voxels) * 16));
-      dense_cap = nc;
-    }
-    have_top = true;
+    max_items = std::max(max_items, ip[nt]);
   }
-  if (have_top) {
-    vl.dense = d_dense.as<int4>();
-    LOD_LAUNCH("publish_top", 32.0 * V_top, launch_copy_items(A, vl, st));
+  LOD_CK(d_pref.alloc(pref.size() * 4));
+  LOD_CK(up_.put(d_pref.p, pref.data(), pref.size() * 4));
+  const uint64_t stage_cap = M + 1;
+  if (n_vlev > 0) {
+    LOD_CK(d_stage0.alloc(stage_cap * 16));
+    LOD_CK(d_stage1.alloc(stage_cap * 16));
+    if (filt) {
+      LOD_CK(d_sum0.alloc(stage_cap * 16));
+      LOD_CK(d_sum1.alloc(stage_cap * 16));
+    }
+  }
+  const uint32_t units_cap = (uint32_t)std::min<uint64_t>((uint64_t)max_items * 64, 1u << 20);
+  LOD_CK(d_units.alloc((size_t)units_cap * sizeof(uint4)));
+  const size_t lctr_bytes = (size_t)std::max(n_vlev, 1) * sizeof(DevCounters);
+  LOD_CK(d_lctr.alloc(lctr_bytes));
+  LOD_CK(d_vstate.alloc(2 * sizeof(unsigned long long)));
+  LOD_CK(d_tvox.alloc(nt * 8));
+  uint64_t dense_cap = std::max<uint64_t>(M / 2, 4096);
+  std::vector<DevCounters> lctr(std::max(n_vlev, 1));
+  unsigned long long vstate[2] = {0, 0};
+  std::vector<unsigned long long> tvox(nt);
+  std::vector<size_t> vox_rec(std::max(n_vlev, 1), 0);
+  static const char* kVoxLevelNames[kMaxLevels] = {
+      "voxelize_L00", "voxelize_L01", "voxelize_L02", "voxelize_L03", "voxelize_L04", "voxelize_L05",
+      "voxelize_L06", "voxelize_L07", "voxelize_L08", "voxelize_L09", "voxelize_L10", "voxelize_L11",
+      "voxelize_L12", "voxelize_L13", "voxelize_L14", "voxelize_L15", "voxelize_L16", "voxelize_L17",
+      "voxelize_L18", "voxelize_L19", "voxelize_L20", "voxelize_L21", "voxelize_L22", "voxelize_L23",
+      "voxelize_L24", "voxelize_L25", "voxelize_L26", "voxelize_L27", "voxelize_L28", "voxelize_L29",
+      "voxelize_L30", "voxelize_L31", "voxelize_L32", "voxelize_L33"};
+  A.tiles = d_tiles.as<TileDesc>();
+  for (int attempt = 0;; ++attempt) {
+    LOD_CK(d_dense.alloc(dense_cap * 16));
+    LOD_CK(cudaMemsetAsync(d_tvox.p, 0, nt * 8, st));
+    LOD_CK(cudaMemsetAsync(d_lctr.p, 0, lctr_bytes, st));
+    LOD_CK(cudaMemsetAsync(d_vstate.p, 0, 2 * sizeof(unsigned long long), st));
+    VoxLevel vl;
+    std::memset(&vl, 0, sizeof(vl));
+    for (int l = n_vlev - 1; l >= 0; --l) {
+      const uint32_t* ip = &pref[(size_t)l * pstride];
+      const uint32_t n_items = ip[nt], n_par = ip[nt + 1 + nt];
+      DevCounters* lc = d_lctr.as<DevCounters>() + l;
+      const int par = (l + 1) & 1;
+      vl.level = (uint32_t)l;
+      vl.n_items = n_items;
+      vl.item_prefix = d_pref.as<uint32_t>() + (size_t)l * pstride;
+      vl.lvl_start = d_lvl.as<uint32_t>();
+      vl.nodes = d_nodes.as<lod_node_t>();
+      vl.aux = d_aux.as<NodeAux>();
+      vl.stage_out = (par ? d_stage1 : d_stage0).as<int4>();
+      vl.stage_out_sum = filt ? (par ? d_sum1 : d_sum0).as<ulonglong2>() : nullptr;
+      vl.stage_cap = stage_cap;
+      vl.stage_in = (par ? d_stage0 : d_stage1).as<int4>();
+      vl.stage_in_sum = filt ? (par ? d_sum0 : d_sum1).as<ulonglong2>() : nullptr;
+      vl.dense = d_dense.as<int4>();
+      vl.stage_used = &lc->stage_used[0];
+      vl.units = d_units.as<uint4>();
+      vl.unit_cap = units_cap;
+      vl.dense_cap = dense_cap;
+      vl.vstate = d_vstate.as<unsigned long long>();
+      LOD_LAUNCH(debug_stats() ? kVoxLevelNames[l] : "voxelize", 0, launch_vox(A, vl, lc, st));
+      vox_rec[l] = prof.recs.size();
+      LOD_LAUNCH("level_scan", 0,
+                 launch_level_scan(A, vl, d_pref.as<uint32_t>() + (size_t)l * pstride + (nt + 1), n_par,
+                                   d_tvox.as<unsigned long long>(), lc, st));
+    }
+    if (n_vlev > 0) {
+      // the roots' voxels: the items of the top level have no parent pass
+      // that would copy their staged records
+      LOD_LAUNCH("publish_top", 0, launch_copy_items(A, vl, st));
+    }
+    LOD_CK(cudaMemcpyAsync(lctr.data(), d_lctr.p, lctr_bytes, cudaMemcpyDeviceToHost, st));
+    LOD_CK(cudaMemcpyAsync(vstate, d_vstate.p, sizeof(vstate), cudaMemcpyDeviceToHost, st));
+    LOD_CK(cudaMemcpyAsync(tvox.data(), d_tvox.p, nt * 8, cudaMemcpyDeviceToHost, st));
+    LOD_CK(cudaStreamSynchronize(st));
+    clk.tick("voxels");
+    ++S.host_syncs;
+    for (int l = 0; l < n_vlev; ++l)
+      if (lctr[l].error) return LOD_ERR_INTERNAL;
+    if (vstate[1] && attempt == 0) {
+      dense_cap = std::max<uint64_t>(vstate[0], 1);  // exact: every level's count is known now
+      prof.resolve();
+      continue;
+    }
+    if (vstate[1]) return LOD_ERR_INTERNAL;
+    break;
+  }
+  const uint64_t V = vstate[0];
+  {
+    // reads: leaf points and the children's voxels; writes: this level's voxels
+    uint64_t V_child = 0;
+    for (int l = n_vlev - 1; l >= 0; --l) {
+      const uint64_t lv = lctr[l].level_voxels;
+      if (prof.on && vox_rec[l] >= 1 && vox_rec[l] <= prof.recs.size())
+        prof.recs[vox_rec[l] - 1].bytes = 16.0 * (double)(leaf_cap[kMaxLevels + 1 + l + 1] + V_child + lv);
+      if (debug_stats())
+        std::fprintf(stderr, "[lod] level %d: items %u (leaf points %llu, child voxels %llu) -> voxels %llu, "
+                     "retried items %llu, table passes %llu, partition units %u\n", l,
+                     pref[(size_t)l * pstride + nt], (unsigned long long)leaf_cap[kMaxLevels + 1 + l + 1],
+                     (unsigned long long)V_child, (unsigned long long)lv,
+                     (unsigned long long)lctr[l].vox_retries, (unsigned long long)lctr[l].vox_passes,
+                     lctr[l].units);
+      V_child = lv;
+    }
+    if (prof.on && n_vlev > 0 && !prof.recs.empty()) prof.recs.back().bytes = 32.0 * (double)V_child;
   }
   if (A.wide) {
     // a root that is a leaf is no voxel item: publish its points here
@@ -865,18 +1038,23 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
         moved += td[t].n;
       }
     if (!leaf_roots.empty()) {
-      LOD_CK(d_itemp.alloc(leaf_roots.size() * 4));
-      LOD_CK(up_.put(d_itemp.p, leaf_roots.data(), leaf_roots.size() * 4));
+      LOD_CK(d_units.alloc(leaf_roots.size() * 4));
+      LOD_CK(up_.put(d_units.p, leaf_roots.data(), leaf_roots.size() * 4));
       LOD_LAUNCH("publish_leaf_roots", 52.0 * moved,
-                 launch_unwide(A, d_itemp.as<uint32_t>(), (uint32_t)leaf_roots.size(), max_n, st));
+                 launch_unwide(A, d_units.as<uint32_t>(), (uint32_t)leaf_roots.size(), max_n, st));
     }
   }
-  std::vector<unsigned long long> tvox(nt);
-  LOD_CK(cudaMemcpyAsync(tvox.data(), d_tvox.p, nt * 8, cudaMemcpyDeviceToHost, st));
-  LOD_CK(cudaStreamSynchronize(st));
+  // keep the voxel array at its exact size when the estimate was generous
+  if (dense_cap > V + V / 2 + 4096) {
+    DevBuf exact(st);
+    LOD_CK(exact.alloc(std::max<uint64_t>(V, 1) * 16));
+    if (V) LOD_CK(cudaMemcpyAsync(exact.p, d_dense.p, V * 16, cudaMemcpyDeviceToDevice, st));
+    std::swap(exact.p, d_dense.p);
+    std::swap(exact.bytes, d_dense.bytes);
+    dense_cap = std::max<uint64_t>(V, 1);
+  }
   up_.recycle();
   prof.resolve();
-  ++S.host_syncs;
 
   // ---- results
   tiles_out->assign(nt, TileResult());
@@ -897,6 +1075,7 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
   *shared_out = sh;
   S.voxels = V;
   if (stats) *stats = S;
+  clk.tick("end");
   return LOD_OK;
 }
 

@@ -44,9 +44,13 @@ struct TileInput {
 };
 
 // Runs the complete build of n_tiles independent tiles on stream st.
-// On LOD_OK fills *shared and tiles_out (one entry per tile).
+// On LOD_OK fills *shared and tiles_out (one entry per tile).  With
+// use_workspace the build's scratch comes from device memory kept for the
+// stream between builds (the serving path, which budgets device memory per
+// request, passes false).
 int run_build(const TileInput* tiles, uint32_t n_tiles, const lod_params_t& params, cudaStream_t st,
-              std::shared_ptr<SharedBuffers>* shared, std::vector<TileResult>* tiles_out, BuildStats* stats);
+              std::shared_ptr<SharedBuffers>* shared, std::vector<TileResult>* tiles_out, BuildStats* stats,
+              bool use_workspace = true);
 
 // Rough device footprint (bytes) of building n points (result + temporaries).
 uint64_t estimate_build_bytes(uint64_t n, const lod_params_t& params);

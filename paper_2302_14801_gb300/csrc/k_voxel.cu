@@ -393,11 +393,12 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
         const ulonglong2* sums = (MODE == LOD_FILTER) ? v.stage_in_sum + ca.stage : nullptr;
         int4* dst = v.dense + ca.dense;
         const uint32_t m = ca.occ;
+        const bool fits = ca.dense + m <= v.dense_cap;  // else the build is redone with a larger array
         for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
           if (*((volatile uint32_t*)&S.fail)) break;
           const int4 vr = rec[i];
           ++seen;
-          if (part == 0) dst[i] = vr;  // publish the child's voxel (idempotent)
+          if (part == 0 && fits) dst[i] = vr;  // publish the child's voxel (idempotent)
           const uint32_t key1 = voxel_key1((uint32_t)vr.x);
           if (part_of(key1, mlog) != part) continue;
           const int slot = find_or_insert(keys, H, key1);
@@ -602,12 +603,14 @@ cudaError_t launch_vox(const BuildArgs& a, const VoxLevel& v, DevCounters* ctr, 
 // (exclusive scan of the occupied counts in node order), then give every
 // parent the range of its children's items.
 __global__ void __launch_bounds__(kBlock) k_level_scan(BuildArgs a, VoxLevel v, const uint32_t* __restrict__ parent_prefix,
-                                                       uint32_t n_parents, uint64_t level_base,
+                                                       uint32_t n_parents,
                                                        unsigned long long* __restrict__ tile_voxels,
                                                        DevCounters* __restrict__ ctr) {
   __shared__ unsigned long long warp_sum[32];
   __shared__ unsigned long long s_carry;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // this level's voxels follow those of the levels below in the voxel array
+  const uint64_t level_base = v.vstate[0];
   if (threadIdx.x == 0) s_carry = 0;
   __syncthreads();
   for (uint32_t chunk = 0; chunk < v.n_items; chunk += blockDim.x) {
@@ -645,7 +648,10 @@ __global__ void __launch_bounds__(kBlock) k_level_scan(BuildArgs a, VoxLevel v, 
     if (threadIdx.x == blockDim.x - 1) s_carry = excl + x;
     __syncthreads();
   }
-  if (threadIdx.x == 0) ctr->level_voxels = s_carry;
+  if (threadIdx.x == 0) {
+    ctr->level_voxels = s_carry;
+    if (level_base + s_carry > v.dense_cap) v.vstate[1] = 1ull;
+  }
   __syncthreads();
   for (uint32_t ip = threadIdx.x; ip < n_parents; ip += blockDim.x) {
     const uint32_t t = find_tile(parent_prefix, a.n_tiles, ip);
@@ -662,12 +668,14 @@ __global__ void __launch_bounds__(kBlock) k_level_scan(BuildArgs a, VoxLevel v, 
     atomicAdd(&ctr->next_cap, (unsigned long long)umin64(cnt, kOctCells));
     atomicAdd(&tile_voxels[t], (unsigned long long)cnt);
   }
+  __syncthreads();  // every thread has read vstate[0]
+  if (threadIdx.x == 0) v.vstate[0] = level_base + s_carry;
 }
 
 cudaError_t launch_level_scan(const BuildArgs& a, const VoxLevel& v, const uint32_t* parent_prefix,
-                              uint32_t n_parents, uint64_t level_base, unsigned long long* tile_voxels,
-                              DevCounters* ctr, cudaStream_t st) {
-  k_level_scan<<<1, kBlock, 0, st>>>(a, v, parent_prefix, n_parents, level_base, tile_voxels, ctr);
+                              uint32_t n_parents, unsigned long long* tile_voxels, DevCounters* ctr,
+                              cudaStream_t st) {
+  k_level_scan<<<1, kBlock, 0, st>>>(a, v, parent_prefix, n_parents, tile_voxels, ctr);
   return cudaGetLastError();
 }
 
@@ -679,6 +687,7 @@ __global__ void __launch_bounds__(256) k_copy_items(BuildArgs a, VoxLevel v) {
   const uint64_t g = a.tiles[t].node_base + v.lvl_start[(uint64_t)t * (kMaxLevels + 1) + v.level + 1] +
                      (it - v.item_prefix[t]);
   const NodeAux ca = v.aux[g];
+  if (ca.dense + ca.occ > v.dense_cap) return;  // the build is redone with a larger array
   for (uint32_t i = threadIdx.x; i < ca.occ; i += blockDim.x) v.dense[ca.dense + i] = v.stage_out[ca.stage + i];
 }
 

@@ -41,11 +41,13 @@ struct VoxLevel {
   unsigned long long* stage_used;
   uint4* units;                // queue of {item, partition, log2 partitions} for overflowing items
   uint32_t unit_cap;
+  uint64_t dense_cap;          // records the public voxel array holds
+  unsigned long long* vstate;  // [0] voxels of the levels done so far, [1] nonzero: dense_cap too small
 };
 cudaError_t launch_vox(const BuildArgs& a, const VoxLevel& v, DevCounters* ctr, cudaStream_t st);
 cudaError_t launch_level_scan(const BuildArgs& a, const VoxLevel& v, const uint32_t* parent_prefix,
-                              uint32_t n_parents, uint64_t level_base, unsigned long long* tile_voxels,
-                              DevCounters* ctr, cudaStream_t st);
+                              uint32_t n_parents, unsigned long long* tile_voxels, DevCounters* ctr,
+                              cudaStream_t st);
 cudaError_t launch_copy_items(const BuildArgs& a, const VoxLevel& v, cudaStream_t st);
 cudaError_t launch_unwide(const BuildArgs& a, const uint32_t* tiles, uint32_t n_tiles, uint32_t max_points,
                           cudaStream_t st);
