@@ -44,6 +44,8 @@ WORKLOADS = {
     "indoor100m": ("indoor", 100_000_000, 3, 50000),
     # small case of the aerial workload (inputs still larger than L2) for profiler captures
     "aerial12m": ("aerial", 12_000_000, 2, 50000),
+    # the billion-point indoor scan, drawn on the device (same recipe, torch RNG)
+    "indoor1b": ("indoor_gpu", 1_000_000_000, 3, 50000),
 }
 METRIC = "LOD build M points/s (filtered & sample-pick), % HBM roofline; tile p50/p99 ms"
 
@@ -61,6 +63,19 @@ def gen(name: str, seed_offset: int = 0) -> np.ndarray:
         np.save(path, pts)
         return pts
     return _gen(name, seed_offset)
+
+
+def on_device(name: str) -> bool:
+    return WORKLOADS[name][0].endswith("_gpu")
+
+
+def gen_device(name: str, seed_offset: int = 0):
+    """Device-drawn workloads (timing only: their random stream is torch's)."""
+    from paper_2302_14801_gb300 import synth_gpu
+    g, n, seed, _ = WORKLOADS[name]
+    if g == "indoor_gpu":
+        return synth_gpu.indoor(n, seed=seed + seed_offset)
+    return synth_gpu.sphere(n, seed=seed + seed_offset)
 
 
 def _gen(name: str, seed_offset: int) -> np.ndarray:
@@ -206,6 +221,191 @@ def run_reference(args):
     return 0
 
 
+def _tile_offsets(n_tiles: int, seed0: int) -> list:
+    """bbox offset of every tile (each tile is a sphere with its own seed and offset)."""
+    out = []
+    for t in range(n_tiles):
+        rng = np.random.default_rng((seed0 + t) ^ 0x5EED)
+        out.append(tuple(int(o) for o in rng.integers(0, (1 << 30) - (1 << 21), size=3)))
+    return out
+
+
+def run_batched(args):
+    """Many independent tiles (point counts log-uniform in [1e4, tile_max],
+    each a sphere with its own seed and bbox), filtered mode, built with one
+    lod_build_batched call per wave of about wave_points points; compared
+    with building the same tiles one lod_build call after another."""
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2302_14801_gb300 import lod, synth, synth_gpu
+    T = 50000
+    sizes = synth.tile_sizes(args.tiles, 1e4, args.tile_max, seed=4 + rank)
+    offs = _tile_offsets(args.tiles, 1000 + 100000 * rank)
+    waves, cur, acc = [], [], 0
+    for t, m in enumerate(sizes):
+        if cur and acc + int(m) > args.wave_points:
+            waves.append(cur)
+            cur, acc = [], 0
+        cur.append(t)
+        acc += int(m)
+    if cur:
+        waves.append(cur)
+    cap = max(sum(int(sizes[t]) for t in w) for w in waves)
+    buf = torch.empty((cap, 4), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def load(w):
+        views, o = [], 0
+        for t in w:
+            m = int(sizes[t])
+            synth_gpu.sphere(m, seed=1000 + t + 100000 * rank, offset=offs[t], out=buf[o:o + m])
+            views.append(buf[o:o + m])
+            o += m
+        torch.cuda.synchronize()
+        return views
+
+    def timed(fn):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        rs = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        for r in rs:
+            r.free()
+        return a.elapsed_time(b)
+
+    # warm-up on the first wave (fills the stream's scratch workspace)
+    views = load(waves[0])
+    for _ in range(max(1, args.warmup - 2)):
+        timed(lambda: lod.build_batched(views, T, lod.FILTER, stream=stream))
+        timed(lambda: [lod.build(v, T, lod.FILTER, stream=stream) for v in views])
+    t_batch, t_single, wave_ms = 0.0, 0.0, []
+    launches0 = lod.launch_count()
+    for w in waves:
+        views = load(w)
+        ms = timed(lambda: lod.build_batched(views, T, lod.FILTER, stream=stream))
+        wave_ms.append(ms)
+        t_batch += ms
+    launches = lod.launch_count() - launches0
+    for w in waves:
+        views = load(w)
+        t_single += timed(lambda: [lod.build(v, T, lod.FILTER, stream=stream) for v in views])
+    total = int(sizes.sum())
+    if rank == 0:
+        line = {
+            "metric": METRIC, "suite": "batched", "value": world * total / (t_batch * 1e-3) / 1e6,
+            "unit": "M points/s", "n_gpus": world, "steps": 1, "warmup": args.warmup,
+            "ms_per_step": t_batch, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32/u64", "data": "synthetic (drawn on the device)",
+            "config": {"workload": f"{args.tiles} tiles, sizes log-uniform in [1e4, {args.tile_max:.0e}] "
+                                   f"({total} points), spheres with their own seed and bbox, T={T}, filtered; "
+                                   f"{len(waves)} waves of <= {args.wave_points:.0e} points, one "
+                                   "lod_build_batched call per wave", "replicas": world},
+            "single_calls": {"value": total / (t_single * 1e-3) / 1e6, "unit": "M points/s",
+                             "ms": t_single, "what": "the same tiles, one lod_build call each"},
+            "batched_vs_single_calls": t_single / t_batch,
+            "wave_ms": wave_ms, "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Poisson stream of build requests through the serving loop
+    (lod_submit / lod_poll): sizes log-uniform in [1e5, 5e7] points,
+    alternately a sphere cloud and an aerial cloud (prefixes of shuffled
+    50M-point clouds held on the device), both modes alternating by request,
+    admitted by an HBM budget; reports submit->ready latency p50/p99 and
+    points/s per arrival rate, against the same requests built one
+    lod_build call after another."""
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2302_14801_gb300 import lod, synth, synth_gpu
+    T = 50000
+    n_max = 50_000_000
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    base = [synth_gpu.sphere(n_max, seed=1), torch.from_numpy(gen("aerial50m")).cuda()]
+    base = [b[torch.randperm(n_max, generator=g, device="cuda")].contiguous() for b in base]
+    torch.cuda.synchronize()
+    rates = [float(r) for r in args.rates.split(",") if r]
+    stream = torch.cuda.current_stream()
+    results = []
+    for ri, rate in enumerate(rates):
+        n_req = args.requests
+        warm = min(20, n_req)
+        sizes = synth.tile_sizes(warm + n_req, 1e5, 5e7, seed=5000 + ri)
+        arrive = synth.poisson_arrivals(warm + n_req, rate, seed=5 + ri)
+        srv = lod.Server(int(args.budget_gb * 1e9), args.inflight)
+        pend = {}  # ticket -> (k, arrival)
+        lat, done_pts, first, last = [], 0, None, None
+        k = 0
+        t0 = time.perf_counter()
+        while k < len(sizes) or pend:
+            now = time.perf_counter() - t0
+            while k < len(sizes) and arrive[k] <= now:
+                m = int(sizes[k])
+                tk = srv.submit(base[k % 2][:m], T, lod.FILTER if (k // 2) % 2 == 0 else lod.PICK)
+                pend[tk] = (k, arrive[k], m)
+                k += 1
+            for tk in list(pend):
+                r = srv.poll(tk)
+                if r is None:
+                    continue
+                kk, arr, m = pend.pop(tk)
+                t_ready = time.perf_counter() - t0
+                r.free()
+                if kk >= warm:
+                    lat.append((t_ready - arr) * 1e3)
+                    done_pts += m
+                    first = arr if first is None else min(first, arr)
+                    last = t_ready if last is None else max(last, t_ready)
+            if k < len(sizes) and not pend:
+                time.sleep(max(0.0, min(arrive[k] - (time.perf_counter() - t0), 0.002)))
+            else:
+                time.sleep(0.0002)
+        srv.close()
+        lat.sort()
+        results.append({"rate_per_s": rate, "requests": n_req, "p50_ms": statistics.median(lat),
+                        "p99_ms": lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))],
+                        "mpts_per_s": done_pts / max(last - first, 1e-9) / 1e6,
+                        "offered_mpts_per_s": float(sizes[warm:].mean()) * rate / 1e6})
+    # the same request mix built one after another with the plain call
+    sizes = synth.tile_sizes(args.requests, 1e5, 5e7, seed=5000)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for kk, m in enumerate(sizes):
+        r = lod.build(base[kk % 2][:int(m)], T, lod.FILTER if (kk // 2) % 2 == 0 else lod.PICK, stream=stream)
+        r.free()
+    b.record(stream)
+    torch.cuda.synchronize()
+    single = float(sizes.sum()) / (a.elapsed_time(b) * 1e-3) / 1e6
+    if rank == 0:
+        best = max(results, key=lambda x: x["mpts_per_s"])
+        line = {
+            "metric": METRIC, "suite": "serve", "value": best["mpts_per_s"], "unit": "M points/s",
+            "n_gpus": world, "steps": args.requests, "warmup": 20, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/u64",
+            "data": "synthetic (sphere drawn on the device, aerial from the seeded generator)",
+            "config": {"workload": "Poisson arrivals, sizes log-uniform in [1e5, 5e7] points, sphere / aerial "
+                                   "alternating, filtered / pick alternating, T=50000",
+                       "hbm_budget_gb": args.budget_gb, "max_inflight": args.inflight},
+            "rates": results, "single_calls_mpts_per_s": single,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -216,11 +416,25 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-fraction", type=float, default=1.0 / 64)
+    ap.add_argument("--suite", default="single", choices=["single", "batched", "serve"],
+                    help="single: the headline line; batched: many independent tiles per launch "
+                         "(lod_build_batched); serve: Poisson request stream through lod_submit/lod_poll")
+    ap.add_argument("--tiles", type=int, default=2048, help="batched: number of tiles")
+    ap.add_argument("--tile-max", type=float, default=2e7, help="batched: largest tile size (points)")
+    ap.add_argument("--wave-points", type=float, default=1e9, help="batched: points built per wave")
+    ap.add_argument("--rates", default="10,20,50,100,200,500", help="serve: arrival rates (requests/s)")
+    ap.add_argument("--requests", type=int, default=200, help="serve: timed requests per rate")
+    ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: HBM budget")
+    ap.add_argument("--inflight", type=int, default=8, help="serve: concurrent builds")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.suite == "batched":
+        return run_batched(args)
+    if args.suite == "serve":
+        return run_serve(args)
 
     import torch
     world, rank, local = dist_setup()
@@ -236,8 +450,12 @@ def main():
 
     name = args.workload
     _, n, _, T = WORKLOADS[name]
-    pts = gen(name, seed_offset=rank)
-    d = torch.from_numpy(pts).cuda()
+    if on_device(name):
+        d = gen_device(name, seed_offset=rank)
+        pts = None  # host copy only if the e2e leg or the CPU baseline asks for it
+    else:
+        pts = gen(name, seed_offset=rank)
+        d = torch.from_numpy(pts).cuda()
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
 
@@ -341,7 +559,7 @@ def main():
     # end to end through the host-buffer call: H2D of the input + build + D2H of the octree
     e2e = None
     if not args.no_e2e:
-        hp = torch.from_numpy(pts).pin_memory()
+        hp = (d.cpu() if pts is None else torch.from_numpy(pts)).pin_memory()
         h2d = d2h = 0
         t_e2e = []
         for it in range(args.warmup + max(1, args.steps // 2)):
@@ -367,16 +585,17 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample(pts, T)
+        cpu = cpu_oracle_sample(d.cpu().numpy() if pts is None else pts, T)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "M points/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32/u64", "data": "synthetic",
-            "config": {"workload": f"{name}: {n} points (seeded synthetic), T={T}, 128^3 grid; "
+            "config": {"workload": f"{name}: {n} points (seeded synthetic"
+                                   f"{', drawn on the device' if on_device(name) else ''}), T={T}, 128^3 grid; "
                                    "step = 1 filtered + 1 pick build, input resident in HBM",
-                       "l2": "inputs (800 MB) larger than L2; no flush", "replicas": world},
+                       "l2": f"inputs ({n * 16 / 1e6:.0f} MB) larger than L2; no flush", "replicas": world},
             "modes": per_mode, "roofline": roof, "kernels": kern, "gpu_launches": launches,
             "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
         }

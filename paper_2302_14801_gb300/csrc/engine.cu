@@ -844,7 +844,7 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
   DevBuf d_nodes(st);  // result
   DevBuf d_aux(st, ws), d_lvl(st, ws), d_nn(st, ws), d_leafcap(st, ws);
   std::vector<uint32_t> n_nodes(nt), lvl((size_t)nt * (kMaxLevels + 1));
-  // [0, L): per level sum of min(leaf points, 64^3); [L, 2L): exact leaf points
+  // [0, L): per level sum over all nodes of min(points, 64^3); [L, 2L): exact leaf points
   std::vector<unsigned long long> leaf_cap(2 * (kMaxLevels + 1));
   uint64_t total_cap = 0;
   for (int attempt = 0;; ++attempt) {
@@ -898,8 +898,8 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
   d_tmpi1.release();
 
   // ---- voxel levels, bottom-up (Section 4.2).  Every level is enqueued
-  // without a host round trip: the staging of one level holds at most one
-  // record per point under its items (so M records always suffice), each
+  // without a host round trip: the staging of one level holds at most
+  // min(points, 64^3) records per item (known from the node pass), each
   // level's place in the voxel array is kept on the device, and the voxel
   // array starts at an estimate; if the levels need more, the phase is run
   // once more with the exact size (every step of it is idempotent).
@@ -923,7 +923,9 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
   }
   LOD_CK(d_pref.alloc(pref.size() * 4));
   LOD_CK(up_.put(d_pref.p, pref.data(), pref.size() * 4));
-  const uint64_t stage_cap = M + 1;
+  // one level's staging holds at most min(points, 64^3) records per item
+  uint64_t stage_cap = 1;
+  for (int l = 0; l < n_vlev; ++l) stage_cap = std::max<uint64_t>(stage_cap, leaf_cap[l + 1] + 1);
   if (n_vlev > 0) {
     LOD_CK(d_stage0.alloc(stage_cap * 16));
     LOD_CK(d_stage1.alloc(stage_cap * 16));

@@ -824,10 +824,10 @@ __global__ void __launch_bounds__(kBlock) k_nodes(BuildArgs a, lod_node_t* __res
         nd[i].child_mask = (uint8_t)mask;
         nd[i].flags = split ? 0 : (LOD_NODE_LEAF | (cnt > a.T ? LOD_NODE_OVERFULL : 0));
         nd[i].first_child = split ? next + pos : kNone;
-        if (!split) {
-          atomicAdd(&leaf_cap[lvl], (unsigned long long)umin64(cnt, kOctCells));
-          atomicAdd(&leaf_cap[kMaxLevels + 1 + lvl], (unsigned long long)cnt);
-        }
+        // per level: bound on the voxel records the node's octant can
+        // contribute to its parent (all nodes), and the exact leaf points
+        atomicAdd(&leaf_cap[lvl], (unsigned long long)umin64(cnt, kOctCells));
+        if (!split) atomicAdd(&leaf_cap[kMaxLevels + 1 + lvl], (unsigned long long)cnt);
         if (split) {
           const uint32_t half = lg - 1;
           uint32_t r = 0;
