@@ -15,7 +15,6 @@ constexpr uint32_t kChunk = 4096;      // points per work chunk of the streaming
 constexpr uint32_t kChunkLog2 = 12;
 constexpr uint32_t kMaxLevels = 34;    // levels 0..32 plus one sentinel slot
 constexpr uint32_t kRootMaxD = 8;      // depth of the largest first counting grid (256^3 cells)
-constexpr uint32_t kSegMaxD = 4;       // depth of a refinement grid (16^3 cells, as in Section 4.1.5)
 constexpr uint32_t kSmemBins = 4096;   // grids up to 8^4 bins are counted in shared memory
 constexpr uint32_t kOctCells = 1u << 18;  // 64^3 cells of one child octant (Section 4.2)
 constexpr uint32_t kBlock = 1024;
@@ -90,6 +89,7 @@ struct BuildArgs {
 };
 
 constexpr uint32_t kPrivSlots = 16384;  // per-CTA table of distinct cells (128 KB)
+constexpr uint32_t kListCap = kPrivSlots / 4 * 3;  // listed cells per CTA (the scatter's table stays <= 3/4 full)
 constexpr uint32_t kPrivProbe = 32;     // longest probe sequence before a cell counts as not fitting
 
 // Per-node internal bookkeeping of the voxel pass, indexed by absolute node.

@@ -124,15 +124,21 @@ __device__ __forceinline__ void stage_chunk(const BuildArgs& a, const uint32_t* 
   cp_async_commit();
 }
 
-// Depth of a refinement grid for a cell of n points (surfaces shrink by
-// about 4x per level): enough levels to reach T, capped at 4 (16^3 cells).
+// Depth of a refinement grid for a cell of n points: the levels that reach
+// T if every level spreads the points over four children (surfaces), plus
+// one level of slack for clustered data, so that one more round resolves
+// most cells; capped at 8 and at 8^d <= 1.25 n cells (the grid's pyramids
+// then take about as many bytes as its points).
 __device__ __forceinline__ uint32_t choose_seg_depth(uint64_t n, uint32_t T, uint32_t level,
                                                      uint32_t log2size, uint32_t max_depth) {
-  uint32_t d = 1;
-  while (d < kSegMaxD && (n >> (2 * d)) > T) ++d;
+  uint32_t need = 1;
+  while (need < kRootMaxD && (n >> (2 * need)) > T) ++need;
+  uint32_t dmem = 1;
+  while (dmem < kRootMaxD && (1ull << (3 * (dmem + 1))) <= n + n / 4) ++dmem;
+  uint32_t d = min(need + 1, dmem);
   d = min(d, max_depth - level);
   d = min(d, log2size);
-  return d;
+  return max(d, 1u);
 }
 
 }  // namespace
@@ -296,12 +302,28 @@ __global__ void __launch_bounds__(kBlock, 1) k_count(BuildArgs a, const uint32_t
   bool smem = false;
   uint32_t nbins = 0;
 
+  uint2* list = a.lists + (uint64_t)blockIdx.x * kPrivSlots;
   auto flush = [&]() {
     __syncthreads();  // every thread's shared-memory increments are done
     if (smem) {
+      // one global add per non-empty cell, and the (cell, count) pair into
+      // the CTA's list while it has room, so that the scatter can claim the
+      // cell's block at once
       uint32_t* dst = s.cnt + pyr_off(s.d);
-      for (uint32_t b = threadIdx.x; b < nbins; b += blockDim.x)
-        if (hist[b]) atomicAdd(dst + b, hist[b]);
+      const uint32_t kbase = (uint32_t)(dst - a.cnt_base);
+      const uint32_t lane = lane_id();
+      for (uint32_t b0 = 0; b0 < nbins; b0 += blockDim.x) {
+        const uint32_t b = b0 + threadIdx.x;
+        const uint32_t h = b < nbins ? hist[b] : 0u;
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, h != 0u);
+        uint32_t wbase = 0;
+        if (lane == 0 && bal) wbase = atomicAdd(&s_list, (uint32_t)__popc(bal));
+        wbase = __shfl_sync(0xFFFFFFFFu, wbase, 0);
+        if (!h) continue;
+        atomicAdd(dst + b, h);
+        const uint32_t at = wbase + __popc(bal & ((1u << lane) - 1u));
+        if (at < kListCap) list[at] = make_uint2(kbase + b, h);
+      }
     }
     __syncthreads();
   };
@@ -366,8 +388,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_count(BuildArgs a, const uint32_t
   }
   if (cur != kNone) flush();
   // publish the table: one global add per distinct cell, and the CTA's list
+  // (cells beyond its capacity are found by the scatter through the global
+  // cursors instead)
   __syncthreads();
-  uint2* list = a.lists + (uint64_t)blockIdx.x * kPrivSlots;
   const uint32_t lane = threadIdx.x & 31u;
   for (uint32_t i0 = 0; i0 < kPrivSlots; i0 += blockDim.x) {
     const uint32_t i = i0 + threadIdx.x;
@@ -379,11 +402,12 @@ __global__ void __launch_bounds__(kBlock, 1) k_count(BuildArgs a, const uint32_t
     wbase = __shfl_sync(0xFFFFFFFFu, wbase, 0);
     if (!occ) continue;
     atomicAdd(a.cnt_base + key1 - 1u, pcnt[i]);
-    list[wbase + __popc(bal & ((1u << lane) - 1u))] = make_uint2(key1 - 1u, pcnt[i]);
+    const uint32_t at = wbase + __popc(bal & ((1u << lane) - 1u));
+    if (at < kListCap) list[at] = make_uint2(key1 - 1u, pcnt[i]);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    a.list_len[blockIdx.x] = s_list;
+    a.list_len[blockIdx.x] = min(s_list, kListCap);
     if (a.diag) atomicAdd(&a.diag[1], (unsigned long long)s_list);
   }
 }
@@ -526,7 +550,7 @@ __global__ void __launch_bounds__(512) k_pyr_down(BuildArgs a, const PyrJob* __r
     ns.pt_off = sta[1 + lo[k] + q];
     ns.n = n;
     ns.chunk0 = 0;
-    ns.priv = 0;  // refinement grids are counted in dense shared histograms
+    ns.priv = (1u << (3 * ns.d)) > kSmemBins ? 1u : 0u;  // too large for a dense shared histogram
     ns.pad = 0;
     a.srcs[g] = ns;
     s.map[c] = g;
@@ -646,29 +670,22 @@ __global__ void __launch_bounds__(kBlock) k_scatter(BuildArgs a, const uint32_t*
       pb[k] = 0;
       if (!v) continue;
       const uint32_t bin = bins[k];
-      if (priv) {
-        const int slot = priv_find(pkeys, kbase + bin + 1u);
-        const int leader = __ffs(m) - 1;
-        const int s0 = __shfl_sync(m, slot, leader);
-        if (__all_sync(m, slot == s0) && s0 >= 0) {
-          agg |= 1u << k;  // one claim for the whole warp
-          if ((int)lane == leader) pb[k] = atomicAdd(&pcur[s0], (uint32_t)__popc(m));
-        } else {
-          pb[k] = slot >= 0 ? atomicAdd(&pcur[slot], 1u) : atomicAdd(cursor + bin, 1u);
-        }
-        const uint32_t f = slot >= 0 ? (uint32_t)pflag[slot] : (s.ovf[bin >> 5] >> (bin & 31u)) & 1u;
-        ovf_bits |= f << k;
+      // the CTA's block of the cell (claimed from its list), else the
+      // cell's global cursor (cells the list had no room for)
+      const int slot = priv_find(pkeys, kbase + bin + 1u);
+      const int leader = __ffs(m) - 1;
+      const int s0 = __shfl_sync(m, slot, leader);
+      const uint32_t b0 = __shfl_sync(m, bin, leader);
+      if (__all_sync(m, slot == s0 && bin == b0)) {
+        agg |= 1u << k;  // the whole warp's points share one cell: one claim
+        if ((int)lane == leader)
+          pb[k] = s0 >= 0 ? atomicAdd(&pcur[s0], (uint32_t)__popc(m)) : atomicAdd(cursor + bin, (uint32_t)__popc(m));
       } else {
-        const int leader = __ffs(m) - 1;
-        const uint32_t b0 = __shfl_sync(m, bin, leader);
-        if (__all_sync(m, bin == b0)) {
-          agg |= 1u << k;
-          if ((int)lane == leader) pb[k] = atomicAdd(cursor + bin, (uint32_t)__popc(m));
-        } else {
-          pb[k] = atomicAdd(cursor + bin, 1u);
-        }
+        pb[k] = slot >= 0 ? atomicAdd(&pcur[slot], 1u) : atomicAdd(cursor + bin, 1u);
       }
-      if (!priv) ovf_bits |= ((s_ovf[bin >> 5] >> (bin & 31u)) & 1u) << k;
+      const uint32_t* om = priv ? s.ovf : s_ovf;
+      const uint32_t f = slot >= 0 ? (uint32_t)pflag[slot] : (om[bin >> 5] >> (bin & 31u)) & 1u;
+      ovf_bits |= f << k;
     }
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
