@@ -62,6 +62,9 @@ def _load():
         lib.oracle_free.restype = None
         lib.oracle_splitmix64.argtypes = [ctypes.c_uint64]
         lib.oracle_splitmix64.restype = ctypes.c_uint64
+        lib.oracle_cube_voxels.argtypes = [ctypes.c_void_p, u32p, ctypes.c_uint64, i32p, ctypes.c_uint32,
+                                           ctypes.c_uint32, u32p]
+        lib.oracle_cube_voxels.restype = ctypes.c_int64
         _lib = lib
     return _lib
 
@@ -126,3 +129,21 @@ def build(points: np.ndarray, leaf_threshold: int = 50000, mode: int = FILTER,
     finally:
         lib.oracle_free(h)
     return out
+
+
+def cube_voxels(points: np.ndarray, index: np.ndarray, cube_min, log2_size: int, mode: int = FILTER) -> np.ndarray:
+    """Voxels of one cube from every input point inside it (rows of
+    (cell, rgba, count, pick_index), sorted by cell); ``index`` holds the
+    points' input indices.  Used to check single nodes of builds too large
+    for ``build``."""
+    lib = _load()
+    pts = np.ascontiguousarray(points, dtype=np.int32).reshape(-1, 4)
+    idx = np.ascontiguousarray(index, dtype=np.uint32)
+    assert len(idx) == len(pts)
+    mn = np.ascontiguousarray(np.asarray(cube_min, dtype=np.int32).reshape(3))
+    out = np.empty((max(len(pts), 1), 4), np.uint32)
+    nv = lib.oracle_cube_voxels(pts.ctypes.data if len(pts) else None, _ptr(idx, ctypes.c_uint32), len(pts),
+                                _ptr(mn, ctypes.c_int32), int(log2_size), int(mode), _ptr(out, ctypes.c_uint32))
+    if nv < 0:
+        raise ValueError("oracle_cube_voxels: invalid arguments (a point outside the cube?)")
+    return out[:nv].copy()

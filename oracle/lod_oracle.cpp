@@ -95,6 +95,7 @@ inline uint32_t grid_coord(int64_t d, uint32_t L) {
 
 struct Builder {
   const OPoint* pts;
+  const uint32_t* input_index = nullptr;  // input index of pts[i] when pts is a subset, else i
   uint64_t n;
   uint32_t T, mode, max_depth;
   std::vector<ONode> nodes;
@@ -102,6 +103,8 @@ struct Builder {
   std::vector<OVoxel> voxels;
   std::vector<OPoint> leaf_points;
   std::vector<uint32_t> leaf_index;
+
+  uint32_t in_index(uint32_t i) const { return input_index ? input_index[i] : i; }
 
   // Section 4.2 + 4.2.3 / replacement of 4.2.2: the voxels of one inner node
   // computed directly from every original point inside its cube.
@@ -144,16 +147,16 @@ struct Builder {
         // Sample pick: the one point of the cell whose splitmix64(index) is
         // smallest (splitmix64 is a bijection, so the minimum is unique).
         uint32_t best = keyed[a].second;
-        uint64_t best_h = splitmix64(best);
+        uint64_t best_h = splitmix64(in_index(best));
         for (size_t j = a + 1; j < b; ++j) {
-          uint64_t h = splitmix64(keyed[j].second);
+          uint64_t h = splitmix64(in_index(keyed[j].second));
           if (h < best_h) {
             best_h = h;
             best = keyed[j].second;
           }
         }
         v.rgba = pts[best].rgba;
-        v.pick_index = best;
+        v.pick_index = in_index(best);
       }
       voxels.push_back(v);
       a = b;
@@ -338,6 +341,41 @@ void oracle_get_points(const oracle_result* r, int32_t* out4, uint32_t* index) {
 }
 
 void oracle_free(oracle_result* r) { delete r; }
+
+// The voxels of one cube (min corner min3, edge 2^log2_size) computed from
+// the n points given, which must be every input point inside that cube;
+// index[i] is the input index of points[i] (the pick's argument).  Rows of
+// (cell, rgba, count, pick_index) sorted by cell go to out4, which holds
+// at least n rows; returns the number of rows, or -1 on invalid arguments
+// (a point outside the cube, log2_size > 32).
+int64_t oracle_cube_voxels(const void* points, const uint32_t* index, uint64_t n, const int32_t* min3,
+                           uint32_t log2_size, uint32_t mode, uint32_t* out4) {
+  if ((n > 0 && (!points || !index || !out4)) || !min3 || log2_size > 32 || mode > 1) return -1;
+  const OPoint* p = static_cast<const OPoint*>(points);
+  for (uint64_t i = 0; i < n; ++i) {
+    const int64_t d[3] = {rel(p[i].x, min3[0]), rel(p[i].y, min3[1]), rel(p[i].z, min3[2])};
+    for (int a = 0; a < 3; ++a)
+      if (d[a] < 0 || d[a] >= (int64_t(1) << log2_size)) return -1;
+  }
+  Builder b;
+  b.pts = p;
+  b.input_index = index;
+  b.n = n;
+  b.mode = mode;
+  ONode nd{};
+  for (int a = 0; a < 3; ++a) nd.min[a] = min3[a];
+  nd.log2_size = log2_size;
+  std::vector<uint32_t> all(n);
+  for (uint64_t i = 0; i < n; ++i) all[i] = (uint32_t)i;
+  b.voxelize(nd, all);
+  for (size_t i = 0; i < b.voxels.size(); ++i) {
+    out4[4 * i + 0] = b.voxels[i].cell;
+    out4[4 * i + 1] = b.voxels[i].rgba;
+    out4[4 * i + 2] = b.voxels[i].count;
+    out4[4 * i + 3] = b.voxels[i].pick_index;
+  }
+  return (int64_t)b.voxels.size();
+}
 
 uint64_t oracle_splitmix64(uint64_t x) { return splitmix64(x); }
 

@@ -353,3 +353,34 @@ def test_bruteforce_pick_catches_wrong_argmin():
     with pytest.raises(AssertionError):
         check(pts, bad, 10, 1, 21)
     assert splitmix64_py(0) == 0xE220A8397B1DCDAF
+
+
+def _in_cube(pts, mn, lg):
+    d = pts[:, :3].astype(np.int64) - np.asarray(mn, np.int64)
+    return np.all((d >= 0) & (d < (1 << int(lg))), axis=1)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_cube_voxels_equals_every_inner_node(seed):
+    # the single-cube entry point (used to check nodes of builds too large for
+    # the whole-cloud oracle) gives each inner node's voxels from the points of
+    # its cube and their input indices, in any row order
+    rng = np.random.default_rng(2000 + seed)
+    n = int(rng.integers(50, 600))
+    pts = _random_cloud(rng, n, int(rng.integers(3, 20)))
+    T = int(rng.integers(2, 30))
+    for mode in (0, 1):
+        r = oracle.build(pts, T, mode)
+        inner = np.nonzero((r["flags"] & 1) == 0)[0]
+        for i in inner:
+            sel = np.nonzero(_in_cube(pts, r["min"][i], r["log2_size"][i]))[0]
+            perm = rng.permutation(len(sel))
+            got = oracle.cube_voxels(pts[sel[perm]], sel[perm], r["min"][i], r["log2_size"][i], mode)
+            a, c = int(r["voxel_offset"][i]), int(r["voxel_count"][i])
+            assert np.array_equal(got, r["voxels"][a:a + c]), (mode, i)
+
+
+def test_cube_voxels_rejects_points_outside():
+    pts = P([(0, 0, 0, 1, 2, 3), (8, 0, 0, 1, 2, 3)])
+    with pytest.raises(ValueError):
+        oracle.cube_voxels(pts, np.arange(2), (0, 0, 0), 3, 0)
