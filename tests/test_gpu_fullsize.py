@@ -64,3 +64,127 @@ def test_aerial_50m_full_parity(lod, aerial, mode):
     invariants(got, N)
     want = oracle.build(aerial, T, mode, 21)
     compare(got, want, inp=aerial)
+
+
+# --------------------------------------------------------------------------
+# The billion-point indoor scan (drawn on the device with the same recipe as
+# synth.indoor), built exactly as the bench times it.  The whole-cloud oracle
+# would take tens of minutes, so every node is checked against the tree's
+# size-independent invariants and sampled nodes against the oracle one by
+# one: inner nodes through the single-cube oracle (the cube's points and
+# their input indices gathered on the device), leaves by their point
+# multiset.
+
+N1B = 1_000_000_000
+
+
+@pytest.fixture(scope="module")
+def indoor1b():
+    from paper_2302_14801_gb300 import synth_gpu
+    return synth_gpu.indoor(N1B, seed=3)
+
+
+def cube_points(dev_pts, mn, lg):
+    import torch
+    lo = torch.tensor([int(v) for v in mn], dtype=torch.int64, device=dev_pts.device)
+    d = dev_pts[:, :3].to(torch.int64) - lo
+    inside = ((d >= 0) & (d < (1 << int(lg)))).all(dim=1)
+    idx = torch.nonzero(inside).squeeze(1)
+    return dev_pts[idx].cpu().numpy(), idx.cpu().numpy().astype(np.uint32)
+
+
+def sorted_rows(a):
+    a = np.asarray(a)
+    return a[np.lexsort(a.T[::-1])]
+
+
+def check_sampled_nodes(got, dev_pts, mode, rng, n_inner=6, n_leaf=6, max_pts=3_000_000):
+    cnt = got["point_count"].astype(np.int64)
+    leaf = (got["flags"] & 1) == 1
+    inner_ok = np.nonzero(~leaf & (cnt <= max_pts))[0]
+    leaf_ok = np.nonzero(leaf & (cnt > 0))[0]
+    picks = list(rng.choice(inner_ok, size=min(n_inner, len(inner_ok)), replace=False))
+    picks.append(int(inner_ok[np.argmax(cnt[inner_ok])]))  # the largest checkable inner node
+    vox = got["voxels"].reshape(-1, 4)
+    for i in picks:
+        pts, idx = cube_points(dev_pts, got["min"][i], got["log2_size"][i])
+        assert len(pts) == cnt[i]
+        want = oracle.cube_voxels(pts, idx, got["min"][i], got["log2_size"][i], mode)
+        a, c = int(got["voxel_offset"][i]), int(got["voxel_count"][i])
+        have = vox[a:a + c]
+        have = have[np.argsort(have[:, 0], kind="stable")]
+        assert np.array_equal(have, want), f"node {i}"
+    for i in rng.choice(leaf_ok, size=min(n_leaf, len(leaf_ok)), replace=False):
+        pts, idx = cube_points(dev_pts, got["min"][i], got["log2_size"][i])
+        a, c = int(got["point_offset"][i]), int(got["point_count"][i])
+        assert np.array_equal(sorted_rows(got["points"][a:a + c]), sorted_rows(pts)), f"leaf {i}"
+        if got.get("index") is not None:
+            assert np.array_equal(np.sort(got["index"][a:a + c]), np.sort(idx)), f"leaf {i} indices"
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_indoor_1b_invariants_and_sampled_nodes(lod, indoor1b, mode):
+    import torch
+    r = lod.build(indoor1b, T, mode, 21, stream=torch.cuda.current_stream())
+    got = r.to_host()
+    r.free()
+    invariants(got, N1B)
+    check_sampled_nodes(got, indoor1b, mode, np.random.default_rng(77 + mode))
+
+
+# --------------------------------------------------------------------------
+# Batched tiles as the bench builds them: the first wave (<= 1e9 points) of
+# 2048 tiles with sizes log-uniform in [1e4, 2e7], each a sphere with its own
+# seed and bbox, one lod_build_batched call, filtered mode.  Tiles up to a
+# few million points are compared with the whole-cloud oracle, every tile
+# with the invariants.
+
+def test_batched_first_wave_of_2048_tiles(lod):
+    import torch
+    from paper_2302_14801_gb300 import synth_gpu
+    sizes = synth.tile_sizes(2048, 1e4, 2e7, seed=4)
+    wave, acc = [], 0
+    for t, m in enumerate(sizes):
+        if wave and acc + int(m) > 1e9:
+            break
+        wave.append(t)
+        acc += int(m)
+    tiles = []
+    for t in wave:
+        off = np.random.default_rng((1000 + t) ^ 0x5EED).integers(0, (1 << 30) - (1 << 21), size=3)
+        tiles.append(synth_gpu.sphere(int(sizes[t]), seed=1000 + t, offset=tuple(int(o) for o in off)))
+    rs = lod.build_batched(tiles, T, 0, stream=torch.cuda.current_stream())
+    small = [k for k in range(len(wave)) if sizes[wave[k]] <= 3_000_000]
+    check = set(small[:: max(1, len(small) // 4)][:4])
+    for k, r in enumerate(rs):
+        got = r.to_host()
+        r.free()
+        invariants(got, int(sizes[wave[k]]))
+        if k in check:
+            pts = tiles[k].cpu().numpy()
+            compare(got, oracle.build(pts, T, 0, 21), inp=pts)
+
+
+# --------------------------------------------------------------------------
+# Serving at full request size: the 50M-point aerial cloud submitted while
+# smaller requests are in flight gives the same octree as the plain call
+# (which the full-size parity test above checks against the oracle).
+
+def test_server_full_size_request_in_a_mix(lod, aerial):
+    import torch
+    d = torch.from_numpy(aerial).cuda()
+    ref = lod.build(d, T, 1, 21)
+    want = ref.to_host()
+    ref.free()
+    srv = lod.Server(120 * 10**9, 4)
+    small = [d[:m] for m in (100_000, 2_000_000, 7_000_000)]
+    tks = [srv.submit(x, T, 0) for x in small[:2]] + [srv.submit(d, T, 1)] + [srv.submit(small[2], T, 1)]
+    res = [srv.wait(tk) for tk in tks]
+    got = res[2].to_host()
+    for r in res:
+        r.free()
+    srv.close()
+    for k in ("min", "level", "log2_size", "child_mask", "flags", "parent", "first_child", "point_offset",
+              "point_count", "voxel_count"):
+        assert np.array_equal(got[k], want[k]), k
+    compare(got, want, inp=aerial)
