@@ -271,8 +271,14 @@ struct lod_server {
     cudaSetDevice(device);
     cudaStream_t st = nullptr;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return;
+    // Each worker builds on its own stream and keeps that stream's scratch
+    // workspace between builds; the workspace's bytes stay counted against
+    // the budget (ws_acc), so a request only needs what exceeds them.
+    uint64_t ws_acc = 0, need = 0;
+    int blocked = 0;
     for (;;) {
       std::shared_ptr<Request> rq;
+      bool trim = false;
       {
         // admission: FIFO head, once it fits into what the budget has left
         std::unique_lock<std::mutex> lk(budget->mu);
@@ -281,10 +287,16 @@ struct lod_server {
             std::lock_guard<std::mutex> qk(mu);
             if (!queue.empty()) {
               auto& h = queue.front();
-              if (budget->in_use + h->est <= budget->limit) {
+              need = h->est > ws_acc ? h->est - ws_acc : 0;
+              if (budget->in_use + need <= budget->limit) {
                 rq = h;
                 queue.pop_front();
-                budget->in_use += rq->est;
+                budget->in_use += need;
+                blocked = 0;
+              } else if (ws_acc && ++blocked >= 2) {
+                // the budget is short and this worker's idle workspace holds
+                // part of it: give the workspace back
+                trim = true;
               } else if (stop) {
                 // shutting down and the budget is held by resident results
                 h->status = LOD_ERR_BUDGET;
@@ -297,24 +309,36 @@ struct lod_server {
               break;
             }
           }
-          if (rq) break;
+          if (rq || trim) break;
           budget->cv.wait_for(lk, std::chrono::milliseconds(50));
         }
+      }
+      if (trim) {
+        cudaStreamSynchronize(st);
+        lodk::release_workspace(st);
+        budget->release(ws_acc);
+        ws_acc = 0;
+        blocked = 0;
+        continue;
       }
       if (!rq) break;
       lodk::TileInput ti{rq->d_points, rq->n};
       std::shared_ptr<lodk::SharedBuffers> sh;
       std::vector<lodk::TileResult> tr;
-      int rc = lodk::run_build(&ti, 1, rq->params, st, &sh, &tr, nullptr, /*use_workspace=*/false);
+      int rc = lodk::run_build(&ti, 1, rq->params, st, &sh, &tr, nullptr);
       lod_result_t* res = nullptr;
       if (rc == LOD_OK) {
         res = make_result(sh, tr[0], rq->params.mode, sh->bytes);
         if (!res) rc = LOD_ERR_OOM;
       }
-      // the build's transient footprint is returned, the result stays counted
+      // the build's transient footprint is returned; the result and the
+      // worker's workspace stay counted
+      const uint64_t ws_now = lodk::workspace_bytes(st);
       {
         std::lock_guard<std::mutex> lk(budget->mu);
-        budget->in_use -= std::min(budget->in_use, rq->est);
+        budget->in_use -= std::min(budget->in_use, need + ws_acc);
+        budget->in_use += ws_now;
+        ws_acc = ws_now;
         if (res) {
           budget->in_use += res->bytes;
           res->budget = budget;
@@ -329,6 +353,9 @@ struct lod_server {
       }
       cv_done.notify_all();
     }
+    cudaStreamSynchronize(st);
+    lodk::release_workspace(st);
+    budget->release(ws_acc);
     cudaStreamDestroy(st);
   }
 };

@@ -88,7 +88,7 @@ struct BuildArgs {
   unsigned long long* diag;  // [0] points counted outside the tables, [1] table inserts
 };
 
-constexpr uint32_t kPrivSlots = 16384;  // per-CTA table of distinct cells (128 KB)
+constexpr uint32_t kPrivSlots = 24576;  // per-CTA table of distinct cells (192 KB counting, 216 KB scatter)
 constexpr uint32_t kListCap = kPrivSlots / 4 * 3;  // listed cells per CTA (the scatter's table stays <= 3/4 full)
 constexpr uint32_t kPrivProbe = 32;     // longest probe sequence before a cell counts as not fitting
 

@@ -413,6 +413,36 @@ bool debug_stats() {
 
 }  // namespace
 
+// Device bytes held by the workspace of (current device, st).
+uint64_t workspace_bytes(cudaStream_t st) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  auto it = g_ws.find({dev, st});
+  if (it == g_ws.end() || !it->second) return 0;
+  uint64_t b = 0;
+  for (auto& k : it->second->blocks) b += k.p ? k.bytes : 0;
+  return b;
+}
+
+// Free the workspace of (current device, st); the stream must be idle.
+void release_workspace(cudaStream_t st) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  Workspace* w = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    auto it = g_ws.find({dev, st});
+    if (it == g_ws.end() || !it->second || it->second->busy) return;
+    w = it->second;
+    g_ws.erase(it);
+  }
+  for (auto& k : w->blocks)
+    if (k.p) cudaFree(k.p);
+  delete w;
+}
+
+
 int set_tuning(const lod_tuning_t& t) {
   if (t.root_depth > kRootMaxD || t.stream_ctas_per_sm > 8) return LOD_ERR_INVALID_ARG;
   g_tune_root_depth.store(t.root_depth);

@@ -46,11 +46,15 @@ struct TileInput {
 // Runs the complete build of n_tiles independent tiles on stream st.
 // On LOD_OK fills *shared and tiles_out (one entry per tile).  With
 // use_workspace the build's scratch comes from device memory kept for the
-// stream between builds (the serving path, which budgets device memory per
-// request, passes false).
+// stream between builds (see workspace_bytes).
 int run_build(const TileInput* tiles, uint32_t n_tiles, const lod_params_t& params, cudaStream_t st,
               std::shared_ptr<SharedBuffers>* shared, std::vector<TileResult>* tiles_out, BuildStats* stats,
               bool use_workspace = true);
+
+// Device bytes kept for stream st's builds between builds, and their release
+// (the stream must be idle).
+uint64_t workspace_bytes(cudaStream_t st);
+void release_workspace(cudaStream_t st);
 
 // Rough device footprint (bytes) of building n points (result + temporaries).
 uint64_t estimate_build_bytes(uint64_t n, const lod_params_t& params);

@@ -62,14 +62,6 @@ __device__ __forceinline__ const int4* src_points(const BuildArgs& a, const SrcD
   return (s.buf == 1 ? a.tmp[0] : a.tmp[1]) + t.pt_base + s.pt_off;
 }
 
-// ------------------------------------------------------- chunk staging
-// Each thread copies its own records of the NEXT chunk from global to
-// shared memory with asynchronous copies (cp.async, L2 only) while it
-// works on the current one, so the DRAM latency of one chunk hides behind
-// the atomics and stores of the previous one.  A thread only ever reads
-// the staging slots it wrote itself, so no CTA barrier is needed: the
-// wait_group of the issuing thread makes its copies visible to it.
-
 // L2 policies: the streamed input is evicted first, so that the partly
 // written sectors of the scatter's output runs stay in L2 until they are
 // complete (a sector evicted half written costs a DRAM read-modify-write).
@@ -89,39 +81,13 @@ __device__ __forceinline__ void st_keep(int4* p, const int4& q, uint64_t pol) {
                : "memory");
 }
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t dep, uint64_t pol) {
-  // `dep` is an opaque zero computed from the values this thread last read
-  // from the same slots; as an operand it makes the copy wait for those
-  // reads (no write-after-read on the slot)
-  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2, %3;\n" ::"r"(
-                   (uint32_t)__cvta_generic_to_shared(dst)),
-               "l"(src), "r"(16u + dep), "l"(pol)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-// An opaque zero that depends on v (the compiler cannot fold it away).
-__device__ __forceinline__ uint32_t opaque_zero(uint32_t v) {
-  uint32_t z;
-  asm volatile("and.b32 %0, %1, 0;" : "=r"(z) : "r"(v));
-  return z;
-}
-
-// Issue the staging copies of this thread's records of chunk c.
-__device__ __forceinline__ void stage_chunk(const BuildArgs& a, const uint32_t* __restrict__ chunk_src, uint64_t c,
-                                            int4* stage, uint32_t dep, uint64_t pol) {
-  const SrcDesc& s = a.srcs[chunk_src[c]];
-  const TileDesc& td = a.tiles[s.tile];
-  const int4* pts = src_points(a, s, td);
-  const uint64_t first = (c - s.chunk0) << kChunkLog2;
-  const uint64_t end = min(first + kChunk, (uint64_t)s.n);
-#pragma unroll
-  for (uint32_t k = 0; k < kChunk / kBlock; ++k) {
-    const uint64_t i = first + threadIdx.x + (uint64_t)k * kBlock;
-    if (i < end) cp_async16(stage + k * kBlock + threadIdx.x, pts + i, dep, pol);
-  }
-  cp_async_commit();
+// 16-byte streaming load with an L2 policy.
+__device__ __forceinline__ int4 ld_policy(const int4* p, uint64_t pol) {
+  int4 q;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(q.x), "=r"(q.y), "=r"(q.z), "=r"(q.w)
+               : "l"(p), "l"(pol));
+  return q;
 }
 
 // Depth of a refinement grid for a cell of n points: the levels that reach
@@ -263,11 +229,12 @@ __device__ __forceinline__ int priv_insert(uint32_t* keys, uint32_t key1) {
   return -1;
 }
 
-// Slot of key1 if present, -1 otherwise (the table is read-only here; the
-// search ends at an empty slot or after visiting every slot).
+// Slot of key1 if present, -1 otherwise (the table is read-only here; keys
+// are placed within kPrivProbe slots of their home, so the search ends
+// there or at an empty slot).
 __device__ __forceinline__ int priv_find(const uint32_t* keys, uint32_t key1) {
   uint32_t slot = priv_home(key1);
-  for (uint32_t probe = 0; probe < kPrivSlots; ++probe) {
+  for (uint32_t probe = 0; probe < kPrivProbe; ++probe) {
     const uint32_t k = keys[slot];
     if (k == key1) return (int)slot;
     if (k == 0u) return -1;
@@ -283,10 +250,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_count(BuildArgs a, const uint32_t
   __shared__ uint32_t hist[kSmemBins];
   __shared__ SrcDesc s;
   __shared__ uint32_t s_list;
-  extern __shared__ __align__(16) uint32_t ptab[];  // kPrivSlots keys, kPrivSlots counts, chunk stage
+  extern __shared__ __align__(16) uint32_t ptab[];  // kPrivSlots keys, then kPrivSlots counts
   uint32_t* pkeys = ptab;
   uint32_t* pcnt = ptab + kPrivSlots;
-  int4* stage = reinterpret_cast<int4*>(ptab + 2 * kPrivSlots);
   const uint64_t n_chunks = *n_chunks_p;
   const uint64_t per = (n_chunks + gridDim.x - 1) / gridDim.x;
   const uint64_t c0 = (uint64_t)blockIdx.x * per;
@@ -330,7 +296,6 @@ __global__ void __launch_bounds__(kBlock, 1) k_count(BuildArgs a, const uint32_t
 
   constexpr int kPer = (int)(kChunk / kBlock);
   const uint64_t pol_in = l2_evict_first();
-  if (c0 < c1) stage_chunk(a, chunk_src, c0, stage, 0u, pol_in);
   for (uint64_t c = c0; c < c1; ++c) {
     const uint32_t sid = chunk_src[c];
     if (sid != cur) {
@@ -348,14 +313,19 @@ __global__ void __launch_bounds__(kBlock, 1) k_count(BuildArgs a, const uint32_t
     const uint64_t end = min(first + kChunk, (uint64_t)s.n);
     const int32_t mx = s.min[0], my = s.min[1], mz = s.min[2];
     const uint32_t lg = s.log2size, d = s.d;
-    uint32_t bin[kPer];
-    cp_async_wait_all();
+    const int4* pts = src_points(a, s, a.tiles[s.tile]);
+    int4 p[kPer];
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       const uint64_t i = first + threadIdx.x + (uint64_t)k * kBlock;
-      bin[k] = i < end ? src_bin(stage[k * kBlock + threadIdx.x], mx, my, mz, lg, d) : 0u;
+      if (i < end) p[k] = ld_policy(pts + i, pol_in);
     }
-    if (c + 1 < c1) stage_chunk(a, chunk_src, c + 1, stage, opaque_zero(bin[0] ^ bin[1] ^ bin[2] ^ bin[3]), pol_in);
+    uint32_t bin[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const uint64_t i = first + threadIdx.x + (uint64_t)k * kBlock;
+      bin[k] = i < end ? src_bin(p[k], mx, my, mz, lg, d) : 0u;
+    }
     if (smem) {
 #pragma unroll
       for (int k = 0; k < kPer; ++k) {
@@ -415,11 +385,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_count(BuildArgs a, const uint32_t
 cudaError_t launch_count(const BuildArgs& a, const uint32_t* chunk_src, const unsigned long long* n_chunks,
                          int grid, cudaStream_t st) {
   static bool once = [] {
-    cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * kPrivSlots + 16 * kChunk));
+    cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * kPrivSlots));
     return true;
   }();
   (void)once;
-  k_count<<<grid, kBlock, 8 * kPrivSlots + 16 * kChunk, st>>>(a, chunk_src, n_chunks);
+  k_count<<<grid, kBlock, 8 * kPrivSlots, st>>>(a, chunk_src, n_chunks);
   return cudaGetLastError();
 }
 
@@ -580,12 +550,11 @@ __global__ void __launch_bounds__(kBlock) k_scatter(BuildArgs a, const uint32_t*
                                                     uint32_t round) {
   __shared__ SrcDesc s;
   __shared__ uint32_t s_ovf[kSmemBins / 32];  // overflow mask of a dense grid
-  // kPrivSlots keys, kPrivSlots cursors, the chunk stage, kPrivSlots overflow flags
+  // kPrivSlots keys, kPrivSlots cursors, kPrivSlots overflow flags
   extern __shared__ __align__(16) uint32_t ptab[];
   uint32_t* pkeys = ptab;
   uint32_t* pcur = ptab + kPrivSlots;
-  int4* stage = reinterpret_cast<int4*>(ptab + 2 * kPrivSlots);
-  uint8_t* pflag = reinterpret_cast<uint8_t*>(stage + kChunk);
+  uint8_t* pflag = reinterpret_cast<uint8_t*>(ptab + 2 * kPrivSlots);
   const uint64_t n_chunks = *n_chunks_p;
   const uint64_t per = (n_chunks + gridDim.x - 1) / gridDim.x;
   const uint64_t c0 = (uint64_t)blockIdx.x * per;
@@ -605,8 +574,19 @@ __global__ void __launch_bounds__(kBlock) k_scatter(BuildArgs a, const uint32_t*
     const uint32_t sid_lo = c0 < c1 ? chunk_src[c0] : 0u, sid_hi = c0 < c1 ? chunk_src[c1 - 1] : 0u;
     for (uint32_t j = threadIdx.x; j < len; j += blockDim.x) {
       const uint2 e = list[j];
+      // bounded probing, as in the counting pass: a cell that does not find
+      // a slot near its home claims nothing here, and its points take
+      // positions from the cell's global cursor instead
       uint32_t slot = priv_home(e.x + 1u);
-      while (atomicCAS(&pkeys[slot], 0u, e.x + 1u) != 0u) slot = (slot + 1 == kPrivSlots) ? 0u : slot + 1;
+      bool placed = false;
+      for (uint32_t probe = 0; probe < kPrivProbe; ++probe) {
+        if (atomicCAS(&pkeys[slot], 0u, e.x + 1u) == 0u) {
+          placed = true;
+          break;
+        }
+        slot = (slot + 1 == kPrivSlots) ? 0u : slot + 1;
+      }
+      if (!placed) continue;
       pcur[slot] = atomicAdd(a.cnt_base + e.x + a.cursor_delta, e.y);
       uint32_t lo = sid_lo, hi = sid_hi;  // last source whose count region starts at or before e.x
       while (lo < hi) {
@@ -624,7 +604,6 @@ __global__ void __launch_bounds__(kBlock) k_scatter(BuildArgs a, const uint32_t*
 
   constexpr int kPer = (int)(kChunk / kBlock);
   const uint64_t pol_in = l2_evict_first(), pol_out = l2_evict_last();
-  if (c0 < c1) stage_chunk(a, chunk_src, c0, stage, 0u, pol_in);
   for (uint64_t c = c0; c < c1; ++c) {
     const uint32_t sid = chunk_src[c];
     if (sid != cur) {
@@ -646,20 +625,17 @@ __global__ void __launch_bounds__(kBlock) k_scatter(BuildArgs a, const uint32_t*
     const uint32_t lg = s.log2size, d = s.d;
     const bool priv = s.priv != 0;
     const uint32_t kbase = (uint32_t)(s.cnt + pyr_off(d) - a.cnt_base);
+    const int4* pts = src_points(a, s, td);
     int4 p[kPer];
     uint32_t bins[kPer];
-    cp_async_wait_all();
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       const uint64_t i = first + threadIdx.x + (uint64_t)k * kBlock;
       p[k] = make_int4(0, 0, 0, 0);
-      if (i < end) p[k] = stage[k * kBlock + threadIdx.x];
-      bins[k] = src_bin(p[k], mx, my, mz, lg, d);
+      if (i < end) p[k] = ld_policy(pts + i, pol_in);
     }
-    if (c + 1 < c1)
-      stage_chunk(a, chunk_src, c + 1, stage,
-                  opaque_zero(bins[0] ^ bins[1] ^ bins[2] ^ bins[3] ^ (uint32_t)(p[0].w ^ p[1].w ^ p[2].w ^ p[3].w)),
-                  pol_in);
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) bins[k] = src_bin(p[k], mx, my, mz, lg, d);
     // claim every position before the first store that needs one
     uint32_t pb[kPer], ovf_bits = 0, agg = 0;
 #pragma unroll
@@ -715,11 +691,11 @@ __global__ void __launch_bounds__(kBlock) k_scatter(BuildArgs a, const uint32_t*
 cudaError_t launch_scatter(const BuildArgs& a, const uint32_t* chunk_src, const unsigned long long* n_chunks,
                            uint32_t round, int grid, cudaStream_t st) {
   static bool once = [] {
-    cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(9 * kPrivSlots + 16 * kChunk));
+    cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(9 * kPrivSlots));
     return true;
   }();
   (void)once;
-  k_scatter<<<grid, kBlock, 9 * kPrivSlots + 16 * kChunk, st>>>(a, chunk_src, n_chunks, round);
+  k_scatter<<<grid, kBlock, 9 * kPrivSlots, st>>>(a, chunk_src, n_chunks, round);
   return cudaGetLastError();
 }
 
