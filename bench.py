@@ -560,6 +560,14 @@ def main():
     e2e = None
     if not args.no_e2e:
         hp = (d.cpu() if pts is None else torch.from_numpy(pts)).pin_memory()
+        # page-locked result buffers, sized by the warm-up builds
+        vmax = max(i["voxels"] for i in info.values())
+        nmax = max(i["nodes"] for i in info.values())
+        hout = {"points": torch.empty((n, 4), dtype=torch.int32, pin_memory=True).numpy(),
+                "index": torch.empty(n, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32),
+                "voxels": torch.empty((vmax, 4), dtype=torch.int32, pin_memory=True).numpy().view(np.uint32),
+                "nodes": torch.empty(nmax * lod.NODE_DTYPE.itemsize, dtype=torch.uint8,
+                                     pin_memory=True).numpy().view(lod.NODE_DTYPE)}
         h2d = d2h = 0
         t_e2e = []
         for it in range(args.warmup + max(1, args.steps // 2)):
@@ -570,7 +578,7 @@ def main():
             bytes_out = 0
             for mode in (lod.FILTER, lod.PICK):
                 r = lod.build_from_host(hp, T, mode, 21, stream=stream)
-                h = r.to_host(stream=stream)
+                h = r.to_host(stream=stream, out=hout)
                 bytes_out += sum(x.nbytes for x in (h["points"], h["voxels"]) if x is not None)
                 bytes_out += (h["index"].nbytes if h["index"] is not None else 0) + len(h["level"]) * 56
                 r.free()

@@ -231,13 +231,24 @@ class Result:
                         if v.point_index else None)
         return out
 
-    def to_host(self, stream=None) -> dict:
-        """Copy to host; returns numpy arrays keyed like the CPU oracle."""
+    def to_host(self, stream=None, out=None) -> dict:
+        """Copy to host; returns numpy arrays keyed like the CPU oracle.
+
+        ``out`` may hold preallocated host arrays (page-locked ones make the
+        copy run at full link speed): ``nodes`` (NODE_DTYPE), ``points``
+        ((N, 4) int32), ``index`` (uint32) and ``voxels`` ((V, 4) uint32), each
+        at least as long as the result; their leading parts are filled."""
         v = self.view()
-        nodes = np.empty(v.n_nodes, NODE_DTYPE)
-        pts = np.empty((v.n_points, 4), np.int32)
-        idx = np.empty(v.n_points, np.uint32) if v.point_index else None
-        vox = np.empty((v.n_voxels, 4), np.uint32)
+        out = out or {}
+        nodes = out["nodes"][:v.n_nodes] if "nodes" in out else np.empty(v.n_nodes, NODE_DTYPE)
+        pts = out["points"][:v.n_points] if "points" in out else np.empty((v.n_points, 4), np.int32)
+        idx = None
+        if v.point_index:
+            idx = out["index"][:v.n_points] if "index" in out else np.empty(v.n_points, np.uint32)
+        vox = out["voxels"][:v.n_voxels] if "voxels" in out else np.empty((v.n_voxels, 4), np.uint32)
+        for a in (nodes, pts, vox) + ((idx,) if idx is not None else ()):
+            if not a.flags.c_contiguous:
+                raise ValueError("to_host: output arrays must be contiguous")
         _check(lib().lod_result_copy_to_host(
             self._h, nodes.ctypes.data, pts.ctypes.data if v.n_points else None,
             idx.ctypes.data if (idx is not None and v.n_points) else None,
