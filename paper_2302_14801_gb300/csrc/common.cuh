@@ -112,7 +112,7 @@ struct DevCounters {
   unsigned int error;                 // nonzero: a kernel detected a problem
   unsigned int units;                 // voxel partition units queued this level
   unsigned int unit_head;             // units taken by the partition kernel
-  unsigned int pad;
+  unsigned int item_head;             // items taken by the first-attempt kernel
 };
 
 enum : uint32_t {

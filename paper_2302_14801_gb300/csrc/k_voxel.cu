@@ -157,6 +157,7 @@ int vox_smem_bytes() { return kSmemBytes; }
 // Shared state of one voxel CTA.
 struct VoxShared {
   uint32_t used, out, fail, sp, seen, queued;
+  uint32_t clean;  // the table holds no entry (set by a complete extraction)
   unsigned long long base;  // first staging record of the current pass's output
   ItemInfo I;
   uint2 stack[48];          // pending {partition, log2 partitions} of the item
@@ -258,18 +259,18 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
     if (S.sp == 0) break;
     const uint2 pm = S.stack[S.sp - 1];
     const uint32_t part = pm.x, mlog = pm.y;
-    for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) {
-      keys[i] = 0u;
+    if (!S.clean) {
+      // an empty entry is all zero bytes in filtered mode whatever the
+      // table's layout, so a clean table serves every item
       if (MODE == LOD_PICK) {
-        E[i] = make_ulonglong2(~0ull, 0ull);
-        cnt32[i] = 0u;
-      } else {
-        A0[i] = 0ull;
-        A1[i] = 0ull;
-        if (!narrow) {
-          A2[i] = 0ull;
+        for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) {
+          keys[i] = 0u;
+          E[i] = make_ulonglong2(~0ull, 0ull);
           cnt32[i] = 0u;
         }
+      } else {
+        uint4* z = reinterpret_cast<uint4*>(smem);
+        for (uint32_t i = threadIdx.x; i < (uint32_t)kSmemBytes / 16u; i += blockDim.x) z[i] = make_uint4(0, 0, 0, 0);
       }
     }
     __syncthreads();
@@ -278,6 +279,7 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
       S.used = 0;
       S.fail = 0;
       S.seen = 0;
+      S.clean = 0;
     }
     __syncthreads();
     ++passes;
@@ -506,34 +508,49 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
       uint32_t wbase = 0;
       if (lane == 0 && bal) wbase = atomicAdd(&S.out, (uint32_t)__popc(bal));
       wbase = __shfl_sync(0xFFFFFFFFu, wbase, 0);
-      if (!occ || !room) continue;
+      if (!occ) continue;
+      // read the entry and leave it empty for the next pass or item
+      keys[i] = 0u;
+      ulonglong2 e = make_ulonglong2(0ull, 0ull);
+      uint32_t c32 = 0;
+      uint64_t sr = 0, sg = 0, sb = 0, n = 0;
+      if (MODE == LOD_PICK) {
+        e = E[i];
+        c32 = cnt32[i];
+        E[i] = make_ulonglong2(~0ull, 0ull);
+        cnt32[i] = 0u;
+      } else if (narrow) {
+        sr = A0[i] & 0xFFFFFFFFull;
+        sg = A0[i] >> 32;
+        sb = A1[i] & 0xFFFFFFFFull;
+        n = A1[i] >> 32;
+        A0[i] = 0ull;
+        A1[i] = 0ull;
+      } else {
+        sr = A0[i];
+        sg = A1[i];
+        sb = A2[i];
+        n = cnt32[i];
+        A0[i] = 0ull;
+        A1[i] = 0ull;
+        A2[i] = 0ull;
+        cnt32[i] = 0u;
+      }
+      if (!room) continue;
       const uint64_t o = S.base + wbase + __popc(bal & ((1u << lane) - 1u));
       const uint32_t cell = key_to_cell(key1, I);
       int4 rec;
       rec.x = (int)cell;
       if (MODE == LOD_PICK) {
-        const ulonglong2 e = E[i];
         const uint32_t best = (uint32_t)(e.y >> 32);
         if (best >= td.n || splitmix64(best) != e.x) {  // cannot happen for a cell that received a sample
           atomicOr(&ctr->error, kErrInternal);
           continue;
         }
         rec.y = (int)(uint32_t)e.y;
-        rec.z = (int)cnt32[i];
+        rec.z = (int)c32;
         rec.w = (int)best;
       } else {
-        uint64_t sr, sg, sb, n;
-        if (narrow) {
-          sr = A0[i] & 0xFFFFFFFFull;
-          sg = A0[i] >> 32;
-          sb = A1[i] & 0xFFFFFFFFull;
-          n = A1[i] >> 32;
-        } else {
-          sr = A0[i];
-          sg = A1[i];
-          sb = A2[i];
-          n = cnt32[i];
-        }
         rec.y = (int)mean_rgba(sr, sg, sb, n);
         rec.z = (int)n;
         rec.w = (int)kNone;
@@ -544,6 +561,8 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
       }
       v.stage_out[o] = rec;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) S.clean = 1;
   }
   if (threadIdx.x == 0) {
     atomicAdd(&ctr->vox_passes, (unsigned long long)passes);
@@ -552,12 +571,23 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
   __syncthreads();
 }
 
-// First attempt: one CTA per item.
+// First attempt of every item, taken in order by persistent CTAs (one per
+// SM: the table fills the shared memory).  A table left empty by the last
+// extraction is not cleared again.
 template <int MODE>
 __global__ void __launch_bounds__(kBlock, 1) k_vox(BuildArgs a, VoxLevel v, DevCounters* __restrict__ ctr) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ VoxShared S;
-  vox_item<MODE>(a, v, ctr, smem, S, blockIdx.x, 0u, 0u, true);
+  __shared__ uint32_t s_item;
+  if (threadIdx.x == 0) S.clean = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(&ctr->item_head, 1u);
+    __syncthreads();
+    const uint32_t it = s_item;
+    __syncthreads();
+    if (it >= v.n_items) break;
+    vox_item<MODE>(a, v, ctr, smem, S, it, 0u, 0u, true);
+  }
 }
 
 // Partitions of the items that overflowed their first attempt, taken from
@@ -568,6 +598,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_vox_units(BuildArgs a, VoxLevel v
   __shared__ VoxShared S;
   __shared__ uint32_t s_unit;
   const uint32_t n_units = min(ctr->units, v.unit_cap);
+  if (threadIdx.x == 0) S.clean = 0;
   for (;;) {
     if (threadIdx.x == 0) s_unit = atomicAdd(&ctr->unit_head, 1u);
     __syncthreads();
@@ -589,7 +620,7 @@ static cudaError_t launch_vox_mode(const BuildArgs& a, const VoxLevel& v, DevCou
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     return n > 0 ? n : 1;
   }();
-  k_vox<MODE><<<v.n_items, kBlock, kSmemBytes, st>>>(a, v, ctr);
+  k_vox<MODE><<<v.n_items < (uint32_t)sms ? v.n_items : (uint32_t)sms, kBlock, kSmemBytes, st>>>(a, v, ctr);
   if (v.units) k_vox_units<MODE><<<sms, kBlock, kSmemBytes, st>>>(a, v, ctr);
   return cudaGetLastError();
 }
