@@ -154,7 +154,7 @@ __host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 // 128^3 grid coordinate of an offset d (0 <= d < 2^L) inside a cube of edge
 // 2^L (Section 4.2: every node samples onto a 128^3 grid).
 __device__ __forceinline__ uint32_t grid_coord(uint32_t d, uint32_t L) {
-  return L >= 7 ? (uint32_t)((uint64_t)d >> (L - 7)) : (d << (7 - L));
+  return L >= 7 ? d >> (L - 7) : (d << (7 - L));  // L <= 32, so L - 7 < 32
 }
 
 __device__ __forceinline__ int4 ldg_stream(const int4* p) { return __ldcs(p); }

@@ -292,34 +292,39 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
       // order follows the scan in real data, so whole warps often hit one
       // cell); one leader per distinct cell then probes and updates the
       // table.  All sums stay exact: at most 32 samples are merged.
-      auto accumulate = [&](uint32_t key1, const int4& q, uint32_t ix) {
+      // merge(): lanes of a warp whose points share a cell add up their
+      // colours; returns whether this lane carries the update (a leader, or
+      // any lane with a sample in pick mode).
+      auto merge = [&](uint32_t key1, const int4& q, uint32_t& r, uint32_t& g, uint32_t& b,
+                       uint32_t& n_same) -> bool {
         const unsigned act = __ballot_sync(0xFFFFFFFFu, key1 != 0u);
-        if (key1 == 0u) return;
         const uint32_t rgba = (uint32_t)q.w;
-        uint64_t h = 0;
-        uint32_t r = rgba & 255u, g = (rgba >> 8) & 255u, b = (rgba >> 16) & 255u;
-        uint32_t n_same = 1;
-        if (MODE == LOD_PICK) {
-          // most updates lose the comparison against the entry they read,
-          // so pick mode skips the merge
-          h = splitmix64(ix);
-        } else {
-          const unsigned peers = __match_any_sync(act, key1);
-          n_same = __popc(peers);
-          if (n_same > 1) {
-            r = __reduce_add_sync(peers, r);
-            g = __reduce_add_sync(peers, g);
-            b = __reduce_add_sync(peers, b);
-          }
-          if ((int)lane != __ffs(peers) - 1) return;
+        r = rgba & 255u;
+        g = (rgba >> 8) & 255u;
+        b = (rgba >> 16) & 255u;
+        n_same = 1;
+        if (key1 == 0u) return false;
+        // most pick updates lose the comparison against the entry they
+        // read, so pick mode skips the merge
+        if (MODE == LOD_PICK) return true;
+        const unsigned peers = __match_any_sync(act, key1);
+        n_same = __popc(peers);
+        if (n_same > 1) {
+          r = __reduce_add_sync(peers, r);
+          g = __reduce_add_sync(peers, g);
+          b = __reduce_add_sync(peers, b);
         }
-        const int slot = find_or_insert(keys, H, key1);
+        return (int)lane == __ffs(peers) - 1;
+      };
+      auto update = [&](int slot, uint32_t key1, const int4& q, uint32_t ix, uint32_t r, uint32_t g, uint32_t b,
+                        uint32_t n_same) {
         if (slot < 0) {
           S.fail = 1;
           return;
         }
         if (MODE == LOD_PICK) {
-          if (!pick_update(&E[slot], h, (uint64_t)rgba | ((uint64_t)ix << 32))) atomicOr(&ctr->error, kErrInternal);
+          if (!pick_update(&E[slot], splitmix64(ix), (uint64_t)(uint32_t)q.w | ((uint64_t)ix << 32)))
+            atomicOr(&ctr->error, kErrInternal);
           atomicAdd(&cnt32[slot], n_same);
         } else if (narrow) {
           atomicAdd(&A0[slot], (uint64_t)r | ((uint64_t)g << 32));
@@ -330,6 +335,25 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
           atomicAdd(&A2[slot], (uint64_t)b);
           atomicAdd(&cnt32[slot], n_same);
         }
+      };
+      // both samples of a pair are merged, then both home slots are read
+      // before either probe is resolved, so their shared-memory latencies
+      // overlap
+      auto accumulate2 = [&](uint32_t k0, const int4& q0, uint32_t x0, uint32_t k1, const int4& q1, uint32_t x1) {
+        uint32_t r0, g0, b0, n0, r1, g1, b1, n1;
+        const bool l0 = merge(k0, q0, r0, g0, b0, n0);
+        const bool l1 = merge(k1, q1, r1, g1, b1, n1);
+        uint32_t h0 = 0, h1 = 0, e0 = 0, e1 = 0;
+        if (l0) {
+          h0 = home_slot(k0, H);
+          e0 = ((volatile uint32_t*)keys)[h0];
+        }
+        if (l1) {
+          h1 = home_slot(k1, H);
+          e1 = ((volatile uint32_t*)keys)[h1];
+        }
+        if (l0) update(resolve_slot(keys, H, k0, h0, e0), k0, q0, x0, r0, g0, b0, n0);
+        if (l1) update(resolve_slot(keys, H, k1, h1, e1), k1, q1, x1, r1, g1, b1, n1);
       };
       // Software pipeline over pairs of points: the loads of the next pair
       // are in flight while the current pair is hashed and accumulated.
@@ -380,8 +404,7 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
           k1 = point_key1(q1, I);
           if (part_of(k1, mlog) != part) k1 = 0u;
         }
-        accumulate(k0, q0, x0);
-        accumulate(k1, q1, x1);
+        accumulate2(k0, q0, x0, k1, q1, x1);
         q0 = r0;
         q1 = r1;
         x0 = y0;
