@@ -172,6 +172,21 @@ def cpu_oracle_sample(pts: np.ndarray, T: int, budget_s: float = 12.0, seed: int
                       f"one filtered + one pick build, single-threaded, {dt:.2f} s"}
 
 
+def max_over_ranks(x: float, dist) -> float:
+    """The slowest rank's time (all ranks call this with their own)."""
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_points_per_s(world: int, n_per_rank: int, ms_step: float) -> float:
+    """Whole-job throughput (M points/s): every rank builds its own replica of
+    n points in both modes per step; the step takes the slowest rank's time."""
+    return world * 2.0 * n_per_rank / (ms_step * 1e-3) / 1e6
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -517,10 +532,8 @@ def main():
     prof = lod.profile_read()
     ms_step = e0.elapsed_time(e1) / args.steps
     if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * 2.0 * n / (ms_step * 1e-3) / 1e6
+        ms_step = max_over_ranks(ms_step, dist)
+    value = job_points_per_s(world, n, ms_step)
 
     pk = peaks()
     per_mode = {}
