@@ -718,6 +718,44 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
     A.diag = d_diag.as<unsigned long long>();
   }
 
+  // ---- node table (Section 4.1.3): enqueued right after the first round's
+  // scatter, before its counters are read, so that a build without
+  // refinement needs no extra round trip (the table is redone if rounds
+  // follow)
+  std::vector<uint32_t> node_cap(nt);
+  for (uint32_t t = 0; t < nt; ++t) node_cap[t] = (uint32_t)std::min<uint64_t>(64 + 16 * ((td[t].n + T - 1) / T), 0x7FFFFFFFull);
+  DevBuf d_nodes(st);  // result
+  DevBuf d_aux(st, ws), d_lvl(st, ws), d_nn(st, ws), d_leafcap(st, ws), d_nctr(st, ws);
+  std::vector<uint32_t> n_nodes(nt), lvl((size_t)nt * (kMaxLevels + 1));
+  // [0, L): per level sum over all nodes of min(points, 64^3); [L, 2L): exact leaf points
+  std::vector<unsigned long long> leaf_cap(2 * (kMaxLevels + 1));
+  uint64_t total_cap = 0;
+  auto enqueue_nodes = [&]() -> int {
+    total_cap = 0;
+    for (uint32_t t = 0; t < nt; ++t) {
+      td[t].node_base = total_cap;
+      td[t].node_cap = node_cap[t];
+      total_cap += node_cap[t];
+    }
+    LOD_CK(up_.put(d_tiles.p, td.data(), nt * sizeof(TileDesc)));
+    LOD_CK(d_nodes.alloc(total_cap * sizeof(lod_node_t)));
+    LOD_CK(d_aux.alloc(total_cap * sizeof(NodeAux)));
+    LOD_CK(d_lvl.alloc(lvl.size() * 4));
+    LOD_CK(d_nn.alloc(nt * 4));
+    LOD_CK(d_leafcap.alloc(leaf_cap.size() * 8));
+    LOD_CK(d_nctr.alloc(sizeof(DevCounters)));
+    LOD_CK(cudaMemsetAsync(d_leafcap.p, 0, leaf_cap.size() * 8, st));
+    LOD_CK(cudaMemsetAsync(d_nctr.p, 0, sizeof(DevCounters), st));
+    LOD_LAUNCH("nodes", 0,
+               launch_nodes(A, d_nodes.as<lod_node_t>(), d_aux.as<NodeAux>(), d_lvl.as<uint32_t>(),
+                            d_nn.as<uint32_t>(), d_leafcap.as<unsigned long long>(), d_nctr.as<DevCounters>(), st));
+    LOD_CK(cudaMemcpyAsync(n_nodes.data(), d_nn.p, nt * 4, cudaMemcpyDeviceToHost, st));
+    LOD_CK(cudaMemcpyAsync(lvl.data(), d_lvl.p, lvl.size() * 4, cudaMemcpyDeviceToHost, st));
+    LOD_CK(cudaMemcpyAsync(leaf_cap.data(), d_leafcap.p, leaf_cap.size() * 8, cudaMemcpyDeviceToHost, st));
+    return LOD_OK;
+  };
+  bool nodes_enqueued = false;
+
   uint32_t round_first = 0, round_n = nt, n_src = nt;
   uint64_t round_chunks = n_chunks0;
   for (uint32_t round = 0;; ++round) {
@@ -821,6 +859,11 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
     }
     LOD_LAUNCH("scatter", 32.0 * round_points,
                launch_scatter(A, d_chunk_src.as<uint32_t>(), d_nchunks.as<unsigned long long>(), round, cgrid, st));
+    if (round == 0) {
+      const int rc = enqueue_nodes();
+      if (rc != LOD_OK) return rc;
+      nodes_enqueued = true;
+    }
     DevCounters* hc = static_cast<DevCounters*>(tl_stage.get(sizeof(DevCounters)));
     if (!hc) return LOD_ERR_OOM;
     LOD_CK(cudaMemcpyAsync(hc, d_ctr.p, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
@@ -840,6 +883,7 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
     const uint32_t new_srcs = (uint32_t)hc->new_srcs;
     const uint64_t new_points = hc->new_points;
     if (!new_srcs) break;
+    nodes_enqueued = false;  // the table must follow the refinement rounds
 
     // next round: the new grids, their chunk space
     srcs.resize(n_src + new_srcs);
@@ -868,41 +912,19 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
     LOD_CK(up_.put(d_chunk_src.p, cs.data(), round_chunks * 4));
   }
 
-  // ---- node tables
-  std::vector<uint32_t> node_cap(nt);
-  for (uint32_t t = 0; t < nt; ++t) node_cap[t] = (uint32_t)std::min<uint64_t>(64 + 16 * ((td[t].n + T - 1) / T), 0x7FFFFFFFull);
-  DevBuf d_nodes(st);  // result
-  DevBuf d_aux(st, ws), d_lvl(st, ws), d_nn(st, ws), d_leafcap(st, ws);
-  std::vector<uint32_t> n_nodes(nt), lvl((size_t)nt * (kMaxLevels + 1));
-  // [0, L): per level sum over all nodes of min(points, 64^3); [L, 2L): exact leaf points
-  std::vector<unsigned long long> leaf_cap(2 * (kMaxLevels + 1));
-  uint64_t total_cap = 0;
+  // ---- node tables: check the table enqueued with the first round (or
+  // build it now), growing the capacity of tiles that overflowed
   for (int attempt = 0;; ++attempt) {
-    total_cap = 0;
-    for (uint32_t t = 0; t < nt; ++t) {
-      td[t].node_base = total_cap;
-      td[t].node_cap = node_cap[t];
-      total_cap += node_cap[t];
+    if (!nodes_enqueued) {
+      const int rc = enqueue_nodes();
+      if (rc != LOD_OK) return rc;
+      LOD_CK(cudaStreamSynchronize(st));
+      clk.tick("nodes");
+      up_.recycle();
+      prof.resolve();
+      ++S.host_syncs;
     }
-    LOD_CK(up_.put(d_tiles.p, td.data(), nt * sizeof(TileDesc)));
-    LOD_CK(d_nodes.alloc(total_cap * sizeof(lod_node_t)));
-    LOD_CK(d_aux.alloc(total_cap * sizeof(NodeAux)));
-    LOD_CK(d_lvl.alloc(lvl.size() * 4));
-    LOD_CK(d_nn.alloc(nt * 4));
-    LOD_CK(d_leafcap.alloc(leaf_cap.size() * 8));
-    LOD_CK(cudaMemsetAsync(d_leafcap.p, 0, leaf_cap.size() * 8, st));
-    LOD_CK(cudaMemsetAsync(d_ctr.p, 0, sizeof(DevCounters), st));
-    LOD_LAUNCH("nodes", 0,
-               launch_nodes(A, d_nodes.as<lod_node_t>(), d_aux.as<NodeAux>(), d_lvl.as<uint32_t>(),
-                            d_nn.as<uint32_t>(), d_leafcap.as<unsigned long long>(), d_ctr.as<DevCounters>(), st));
-    LOD_CK(cudaMemcpyAsync(n_nodes.data(), d_nn.p, nt * 4, cudaMemcpyDeviceToHost, st));
-    LOD_CK(cudaMemcpyAsync(lvl.data(), d_lvl.p, lvl.size() * 4, cudaMemcpyDeviceToHost, st));
-    LOD_CK(cudaMemcpyAsync(leaf_cap.data(), d_leafcap.p, leaf_cap.size() * 8, cudaMemcpyDeviceToHost, st));
-    LOD_CK(cudaStreamSynchronize(st));
-    clk.tick("nodes");
-    up_.recycle();
-    prof.resolve();
-    ++S.host_syncs;
+    nodes_enqueued = false;
     bool retry = false;
     for (uint32_t t = 0; t < nt; ++t)
       if (n_nodes[t] == kNone) {
@@ -1076,8 +1098,9 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
                  launch_unwide(A, d_units.as<uint32_t>(), (uint32_t)leaf_roots.size(), max_n, st));
     }
   }
-  // keep the voxel array at its exact size when the estimate was generous
-  if (dense_cap > V + V / 2 + 4096) {
+  // trim the voxel array when the estimate was more than three times too
+  // generous (a copy of the voxels; smaller slack is cheaper to keep)
+  if (dense_cap > 3 * V + 65536) {
     DevBuf exact(st);
     LOD_CK(exact.alloc(std::max<uint64_t>(V, 1) * 16));
     if (V) LOD_CK(cudaMemcpyAsync(exact.p, d_dense.p, V * 16, cudaMemcpyDeviceToDevice, st));

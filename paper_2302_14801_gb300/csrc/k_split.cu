@@ -767,12 +767,20 @@ __global__ void __launch_bounds__(kBlock) k_nodes(BuildArgs a, lod_node_t* __res
         split = cnt > a.T && lvl < a.max_depth && lg > 0;
         if (split && j == a.srcs[sid].d) {
           // bottom cell of its grid: continue in the cell's refinement grid
-          sid = a.srcs[sid].map[c];
-          j = 0;
-          c = 0;
-          ax[i].src = sid;
-          ax[i].j = 0;
-          ax[i].c = 0;
+          // (not counted yet when this pass runs before the next round; the
+          // host then discards the table and builds it after the rounds)
+          const uint32_t child = a.srcs[sid].map[c];
+          if (a.srcs[child].cnt == nullptr) {
+            split = false;
+            s_fail = 2;
+          } else {
+            sid = child;
+            j = 0;
+            c = 0;
+            ax[i].src = sid;
+            ax[i].j = 0;
+            ax[i].c = 0;
+          }
         }
         if (split) {
           const uint32_t* ch = a.srcs[sid].cnt + pyr_off(j + 1) + 8ull * c;
@@ -865,7 +873,7 @@ __global__ void __launch_bounds__(kBlock) k_nodes(BuildArgs a, lod_node_t* __res
     ls[level] = begin;
     for (uint32_t l = level + 1; l <= kMaxLevels; ++l) ls[l] = begin;
     n_nodes[t] = s_fail ? kNone : end;
-    if (s_fail) atomicOr(&ctr->error, kErrNodeCap);
+    if (s_fail == 1) atomicOr(&ctr->error, kErrNodeCap);
   }
 }
 
