@@ -246,6 +246,19 @@ typedef struct lod_tuning {
 int lod_set_tuning(const lod_tuning_t* t);
 int lod_get_tuning(lod_tuning_t* t);
 
+/* Autotuner: times lod_build of the caller's cloud (device pointer, n points,
+ * params; on `stream`) under each candidate tuning — root_depth the default,
+ * one less and one more; stream_ctas_per_sm 1, 2 and 3 — two builds each
+ * (the first untimed), keeps the fastest with lod_set_tuning and returns it
+ * in *best (and its build time in *best_ms when not NULL).  Results are
+ * freed; nothing else is kept.  Costs about 18 builds; like lod_set_tuning
+ * it changes process-wide state, so call it while no other build runs.
+ * Returns LOD_ERR_INVALID_ARG for n == 0 or a missing pointer, or the first
+ * build error (the previous tuning is then restored).  The paper has no
+ * counterpart (it uses one fixed configuration, Section 4.1.6). */
+int lod_autotune(const lod_point_t* d_points, uint64_t n, const lod_params_t* params, void* stream,
+                 lod_tuning_t* best, float* best_ms);
+
 /* ------------------------------------------------------------ profiling */
 
 /* Per-kernel statistics accumulated by the library while profiling is on:

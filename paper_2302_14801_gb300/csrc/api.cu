@@ -214,6 +214,63 @@ void lod_free(lod_result_t* r) {
 int lod_set_tuning(const lod_tuning_t* t) { return t ? lodk::set_tuning(*t) : LOD_ERR_INVALID_ARG; }
 int lod_get_tuning(lod_tuning_t* t) { return t ? lodk::get_tuning(t) : LOD_ERR_INVALID_ARG; }
 
+int lod_autotune(const lod_point_t* d_points, uint64_t n, const lod_params_t* params, void* stream,
+                 lod_tuning_t* best, float* best_ms) {
+  if (!d_points || n == 0 || !best) return LOD_ERR_INVALID_ARG;
+  const lod_params_t p = params ? *params : defaults();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  lod_tuning_t before;
+  lodk::get_tuning(&before);
+  const uint32_t d0 = lodk::default_root_depth(n, p.leaf_threshold, p.max_depth);
+  std::vector<uint32_t> depths = {0};
+  if (d0 > 1) depths.push_back(d0 - 1);
+  if (d0 >= 1 && d0 < 8) depths.push_back(d0 + 1);
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    if (a) cudaEventDestroy(a);
+    return LOD_ERR_CUDA;
+  }
+  lod_tuning_t win = before;
+  float win_ms = -1.f;
+  int rc = LOD_OK;
+  for (uint32_t d : depths) {
+    for (uint32_t cps : {1u, 2u, 3u}) {
+      lod_tuning_t t;
+      std::memset(&t, 0, sizeof(t));
+      t.root_depth = d;
+      t.stream_ctas_per_sm = cps;
+      if ((rc = lodk::set_tuning(t)) != LOD_OK) break;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2 && rc == LOD_OK; ++rep) {
+        lod_result_t* r = nullptr;
+        if (rep == 1) cudaEventRecord(a, st);
+        rc = lod_build(d_points, n, &p, stream, &r);
+        if (rep == 1) cudaEventRecord(b, st);
+        if (rc == LOD_OK) {
+          lod_free(r);
+          if (rep == 1 && cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+        }
+      }
+      if (rc != LOD_OK) break;
+      if (win_ms < 0.f || ms < win_ms) {
+        win_ms = ms;
+        win = t;
+      }
+    }
+    if (rc != LOD_OK) break;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc != LOD_OK) {
+    lodk::set_tuning(before);
+    return rc;
+  }
+  lodk::set_tuning(win);
+  *best = win;
+  if (best_ms) *best_ms = win_ms;
+  return LOD_OK;
+}
+
 int lod_profile_enable(int on) { return lodk::profile_enable(on != 0); }
 int lod_profile_reset(void) { return lodk::profile_reset(); }
 int lod_profile_read(lod_kernel_stat_t* stats, uint32_t capacity, uint32_t* n_stats) {

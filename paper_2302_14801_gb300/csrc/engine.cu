@@ -443,6 +443,14 @@ void release_workspace(cudaStream_t st) {
 }
 
 
+uint32_t default_root_depth(uint64_t n, uint32_t T, uint32_t max_depth) {
+  if (n <= T || max_depth == 0 || T == 0) return 0;
+  uint32_t d = ceil_log4((double)n / (double)T) + 1;
+  d = std::min(d, kRootMaxD);
+  d = std::min(d, max_depth);
+  return std::max(d, 1u);
+}
+
 int set_tuning(const lod_tuning_t& t) {
   if (t.root_depth > kRootMaxD || t.stream_ctas_per_sm > 8) return LOD_ERR_INVALID_ARG;
   g_tune_root_depth.store(t.root_depth);

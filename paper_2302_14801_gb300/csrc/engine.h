@@ -61,6 +61,10 @@ uint64_t estimate_build_bytes(uint64_t n, const lod_params_t& params);
 // Rough device footprint of a finished result of n points.
 uint64_t estimate_result_bytes(uint64_t n, const lod_params_t& params);
 
+// Default depth of a tile's first counting grid (8^d cells) for n points,
+// before the cap by the cube's size (a set root_depth is ignored here).
+uint32_t default_root_depth(uint64_t n, uint32_t T, uint32_t max_depth);
+
 // Process-wide tuning (see lod_set_tuning in lod.h).
 int set_tuning(const lod_tuning_t& t);
 int get_tuning(lod_tuning_t* t);

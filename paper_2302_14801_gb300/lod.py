@@ -34,7 +34,7 @@ EXPORTED = [
     "lod_result_copy_to_host", "lod_result_device_bytes", "lod_free", "lod_error_string",
     "lod_server_create", "lod_submit", "lod_poll", "lod_wait", "lod_server_bytes_in_use",
     "lod_server_destroy", "lod_profile_enable", "lod_profile_reset", "lod_profile_read", "lod_launch_count",
-    "lod_root_cubes_noalloc", "lod_set_tuning", "lod_get_tuning",
+    "lod_root_cubes_noalloc", "lod_set_tuning", "lod_get_tuning", "lod_autotune",
 ]
 
 
@@ -115,6 +115,7 @@ def _load():
         "lod_root_cubes_noalloc": (i, [P(vp), P(u64), u32, vp, vp]),
         "lod_set_tuning": (i, [P(Tuning)]),
         "lod_get_tuning": (i, [P(Tuning)]),
+        "lod_autotune": (i, [vp, u64, P(Params), vp, P(Tuning), P(ctypes.c_float)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -184,6 +185,18 @@ def get_tuning() -> dict:
     t = Tuning()
     _check(lib().lod_get_tuning(ctypes.byref(t)), "lod_get_tuning")
     return {"root_depth": t.root_depth, "stream_ctas_per_sm": t.stream_ctas_per_sm}
+
+
+def autotune(points, leaf_threshold=50000, mode=FILTER, max_depth=21, stream=None) -> dict:
+    """lod_autotune on a CUDA int32 (N, 4) tensor: applies and returns the
+    fastest tuning (``root_depth``, ``stream_ctas_per_sm``, ``ms``)."""
+    ptr, n = _dev_ptr(points)
+    p = make_params(leaf_threshold, mode, max_depth, False)
+    t = Tuning()
+    ms = ctypes.c_float()
+    _check(lib().lod_autotune(ptr if n else None, n, ctypes.byref(p), _stream_handle(stream), ctypes.byref(t),
+                              ctypes.byref(ms)), "lod_autotune")
+    return {"root_depth": t.root_depth, "stream_ctas_per_sm": t.stream_ctas_per_sm, "ms": ms.value}
 
 
 def launch_count() -> int:

@@ -138,6 +138,34 @@ def test_threshold_boundary(lod, mode, extra):
     assert (len(got["level"]) == 1) == (extra == 0)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_tuning_never_changes_results(lod, mode):
+    # root depth and CTAs per SM are speed knobs: every setting gives the
+    # oracle's result (a shallow first grid forces refinement rounds, a deep
+    # one a sparse first grid)
+    pts = synth.aerial(600_000, seed=12, n_buildings=40)
+    want = oracle.build(pts, 5000, mode, 21)
+    try:
+        for rd, cps in ((1, 1), (3, 0), (5, 3), (8, 2)):
+            lod.set_tuning(rd, cps)
+            compare(gpu_build(lod, pts, 5000, mode), want, inp=pts)
+    finally:
+        lod.set_tuning(0, 0)
+
+
+def test_autotune_picks_a_candidate_and_keeps_results(lod):
+    import torch
+    pts = synth.aerial(400_000, seed=13, n_buildings=30)
+    d = torch.from_numpy(pts).cuda()
+    try:
+        best = lod.autotune(d, 5000, 0)
+        assert best["stream_ctas_per_sm"] in (1, 2, 3) and best["ms"] > 0
+        assert lod.get_tuning()["stream_ctas_per_sm"] == best["stream_ctas_per_sm"]
+        compare(gpu_build(lod, pts, 5000, 0), oracle.build(pts, 5000, 0, 21), inp=pts)
+    finally:
+        lod.set_tuning(0, 0)
+
+
 # --------------------------------------------------- workload-shaped inputs
 
 @pytest.mark.parametrize("mode", [0, 1])
