@@ -86,6 +86,10 @@ struct BuildArgs {
   uint2* lists;            // kPrivSlots entries per CTA
   uint32_t* list_len;      // per CTA
   unsigned long long* diag;  // [0] points counted outside the tables, [1] table inserts
+  // nonzero: a root grid's depth chosen before the bounding box was known
+  // exceeds its cube; the split kernels then do nothing and the host
+  // restarts with the depths fixed
+  const unsigned int* abort;
 };
 
 constexpr uint32_t kPrivSlots = 24576;  // per-CTA table of distinct cells (192 KB counting, 216 KB scatter)

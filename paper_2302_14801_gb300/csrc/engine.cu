@@ -578,9 +578,30 @@ struct PhaseClock {
   }
 };
 
+namespace {
+constexpr int kRetryWithRoots = -100;  // internal: redo the build with root cubes read back first
+}
+
+static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaStream_t st,
+                          std::shared_ptr<SharedBuffers>* shared_out, std::vector<TileResult>* tiles_out,
+                          BuildStats* stats, bool use_workspace, bool sync_roots);
+
+// Builds normally go without a host round trip after the bounding box: the
+// root cubes are set on the device and the first grids' depths chosen from
+// the point counts alone.  When a cloud's cube turns out smaller than such
+// a depth allows (a tiny spatial extent), the build is redone with the
+// cubes read back first.
 int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaStream_t st,
               std::shared_ptr<SharedBuffers>* shared_out, std::vector<TileResult>* tiles_out, BuildStats* stats,
               bool use_workspace) {
+  const int rc = run_build_impl(tin, nt, prm, st, shared_out, tiles_out, stats, use_workspace, false);
+  if (rc != kRetryWithRoots) return rc;
+  return run_build_impl(tin, nt, prm, st, shared_out, tiles_out, stats, use_workspace, true);
+}
+
+static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaStream_t st,
+                          std::shared_ptr<SharedBuffers>* shared_out, std::vector<TileResult>* tiles_out,
+                          BuildStats* stats, bool use_workspace, bool sync_roots) {
   BuildStats S;
   PhaseClock clk;
   WsLease lease(st, use_workspace);  // declared first: outlives every scratch buffer
@@ -656,16 +677,34 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
              launch_bbox(d_tiles.as<TileDesc>(), d_chunk_src.as<uint32_t>(), n_chunks0, d_chunk0.as<uint64_t>(),
                          d_bbox.as<int>(), grid, st));
   std::vector<int> bbox(6 * nt);
-  LOD_CK(cudaMemcpyAsync(bbox.data(), d_bbox.p, bbox.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
-  LOD_CK(cudaStreamSynchronize(st));
-  clk.tick("bbox");
-  up_.recycle();
-  prof.resolve();
-  ++S.host_syncs;
+  DevBuf d_abort(st, ws);
+  if (sync_roots) {
+    LOD_CK(cudaMemcpyAsync(bbox.data(), d_bbox.p, bbox.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+    LOD_CK(cudaStreamSynchronize(st));
+    clk.tick("bbox");
+    up_.recycle();
+    prof.resolve();
+    ++S.host_syncs;
+  } else {
+    LOD_CK(d_abort.alloc(sizeof(unsigned int)));
+    LOD_CK(cudaMemsetAsync(d_abort.p, 0, sizeof(unsigned int), st));
+  }
 
   std::vector<SrcDesc> srcs(nt);
   uint64_t src_bound0 = 0;
   for (uint32_t t = 0; t < nt; ++t) {
+    if (!sync_roots) {
+      // cube unknown yet (set on the device); depth from the counts alone
+      SrcDesc& s = srcs[t];
+      std::memset(&s, 0, sizeof(SrcDesc));
+      s.tile = t;
+      s.d = choose_root_depth(td[t].n, T, 32, prm.max_depth);
+      s.n = td[t].n;
+      s.chunk0 = chunk0[t];
+      s.priv = ipow8(s.d) > kSmemBins ? 1u : 0u;
+      src_bound0 += td[t].n / (T + 1ull);
+      continue;
+    }
     if (td[t].n == 0) {
       td[t].min[0] = td[t].min[1] = td[t].min[2] = 0;
       td[t].log2S = 0;
@@ -713,6 +752,7 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
   A.out_idx = want_idx ? d_index.as<uint32_t>() : nullptr;
   A.lists = d_lists.as<uint2>();
   A.list_len = d_llen.as<uint32_t>();
+  A.abort = sync_roots ? nullptr : d_abort.as<unsigned int>();
   // modes that keep input indices stage each leaf point as one 32-byte record
   DevBuf d_wide(st, ws);
   if (want_idx) {
@@ -787,6 +827,10 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
     }
     LOD_CK(up_.put(d_srcs.as<SrcDesc>() + round_first, srcs.data() + round_first,
                            round_n * sizeof(SrcDesc)));
+    if (round == 0 && !sync_roots)
+      LOD_LAUNCH("roots", 0,
+                 launch_roots(d_tiles.as<TileDesc>(), d_bbox.as<int>(), d_srcs.as<SrcDesc>(), nt, T,
+                              prm.max_depth, d_abort.as<unsigned int>(), st));
     LOD_CK(up_.put(d_nchunks.p, &round_chunks, sizeof(round_chunks)));
     A.tiles = d_tiles.as<TileDesc>();
     A.srcs = d_srcs.as<SrcDesc>();
@@ -872,11 +916,19 @@ int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaSt
       if (rc != LOD_OK) return rc;
       nodes_enqueued = true;
     }
-    DevCounters* hc = static_cast<DevCounters*>(tl_stage.get(sizeof(DevCounters)));
+    DevCounters* hc = static_cast<DevCounters*>(tl_stage.get(sizeof(DevCounters) + sizeof(unsigned int)));
     if (!hc) return LOD_ERR_OOM;
+    unsigned int* h_abort = reinterpret_cast<unsigned int*>(hc + 1);
+    *h_abort = 0;
     LOD_CK(cudaMemcpyAsync(hc, d_ctr.p, sizeof(DevCounters), cudaMemcpyDeviceToHost, st));
+    if (round == 0 && !sync_roots)
+      LOD_CK(cudaMemcpyAsync(h_abort, d_abort.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
     LOD_CK(cudaStreamSynchronize(st));
     clk.tick("round");
+    if (*h_abort) {
+      prof.resolve();
+      return kRetryWithRoots;
+    }
     up_.recycle();
     prof.resolve();
     ++S.host_syncs;

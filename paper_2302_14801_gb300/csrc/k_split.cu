@@ -187,6 +187,43 @@ __global__ void __launch_bounds__(kBlock) k_bbox(const TileDesc* __restrict__ ti
   if (cur != kNone) flush(cur);
 }
 
+// Root cubes from the bounding boxes (see the reading of Section 4 in the
+// oracle): min corner = bbox min, edge = the smallest power of two above the
+// largest extent.  Written into each tile's first counting grid on the
+// device, so the host need not wait for the boxes; a grid depth the host
+// chose before knowing the cube that exceeds it raises *abort.
+__global__ void k_roots(const TileDesc* __restrict__ tiles, const int* __restrict__ bbox, SrcDesc* srcs,
+                        uint32_t n_tiles, uint32_t T, uint32_t max_depth, unsigned int* abort) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tiles) return;
+  const uint32_t n = tiles[t].n;
+  int32_t mn[3] = {0, 0, 0};
+  uint32_t L = 0;
+  if (n) {
+    int64_t ext = 0;
+    for (int k = 0; k < 3; ++k) {
+      mn[k] = bbox[6 * t + k];
+      const int64_t e = (int64_t)bbox[6 * t + 3 + k] - (int64_t)bbox[6 * t + k];
+      ext = e > ext ? e : ext;
+    }
+    while (L < 33 && (int64_t(1) << L) <= ext) ++L;
+  }
+  SrcDesc& s = srcs[t];
+  s.min[0] = mn[0];
+  s.min[1] = mn[1];
+  s.min[2] = mn[2];
+  s.log2size = L;
+  const uint32_t want = (n <= T || L == 0 || max_depth == 0) ? 0u : min(s.d, L);
+  if (want != s.d) atomicOr(abort, 1u);
+}
+
+cudaError_t launch_roots(const TileDesc* tiles, const int* bbox, SrcDesc* srcs, uint32_t n_tiles, uint32_t T,
+                         uint32_t max_depth, unsigned int* abort, cudaStream_t st) {
+  if (!n_tiles) return cudaSuccess;
+  k_roots<<<(n_tiles + 255) / 256, 256, 0, st>>>(tiles, bbox, srcs, n_tiles, T, max_depth, abort);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bbox(const TileDesc* tiles, const uint32_t* chunk_tile, uint64_t n_chunks,
                         const uint64_t* tile_chunk0, int* bbox, int grid, cudaStream_t st) {
   if (n_chunks == 0) return cudaSuccess;
@@ -247,6 +284,7 @@ __device__ __forceinline__ int priv_find(const uint32_t* keys, uint32_t key1) {
 
 __global__ void __launch_bounds__(kBlock, 1) k_count(BuildArgs a, const uint32_t* __restrict__ chunk_src,
                                                   const unsigned long long* __restrict__ n_chunks_p) {
+  if (a.abort && *a.abort) return;
   __shared__ uint32_t hist[kSmemBins];
   __shared__ SrcDesc s;
   __shared__ uint32_t s_list;
@@ -399,6 +437,7 @@ cudaError_t launch_count(const BuildArgs& a, const uint32_t* chunk_src, const un
 // bottom histogram, 4 levels per CTA in shared memory.
 
 __global__ void __launch_bounds__(512) k_pyr_up(BuildArgs a, const PyrJob* __restrict__ jobs) {
+  if (a.abort && *a.abort) return;
   __shared__ uint32_t sm[4096 + 512 + 64 + 8];
   const PyrJob job = jobs[blockIdx.x];
   const SrcDesc& s = a.srcs[job.src];
@@ -442,6 +481,7 @@ cudaError_t launch_pyr_up(const BuildArgs& a, const PyrJob* jobs, uint32_t n_job
 __global__ void __launch_bounds__(512) k_pyr_down(BuildArgs a, const PyrJob* __restrict__ jobs,
                                                   uint32_t next_base, uint32_t next_cap, uint32_t next_buf,
                                                   DevCounters* __restrict__ ctr) {
+  if (a.abort && *a.abort) return;
   __shared__ uint32_t cnt[8 + 64 + 512 + 4096];
   __shared__ uint32_t sta[1 + 8 + 64 + 512 + 4096];
   const PyrJob job = jobs[blockIdx.x];
@@ -548,6 +588,7 @@ cudaError_t launch_pyr_down(const BuildArgs& a, const PyrJob* jobs, uint32_t n_j
 __global__ void __launch_bounds__(kBlock) k_scatter(BuildArgs a, const uint32_t* __restrict__ chunk_src,
                                                     const unsigned long long* __restrict__ n_chunks_p,
                                                     uint32_t round) {
+  if (a.abort && *a.abort) return;
   __shared__ SrcDesc s;
   __shared__ uint32_t s_ovf[kSmemBins / 32];  // overflow mask of a dense grid
   // kPrivSlots keys, kPrivSlots cursors, kPrivSlots overflow flags
@@ -713,6 +754,7 @@ __global__ void __launch_bounds__(kBlock) k_nodes(BuildArgs a, lod_node_t* __res
                                                   uint32_t* __restrict__ n_nodes,
                                                   unsigned long long* __restrict__ leaf_cap,
                                                   DevCounters* __restrict__ ctr) {
+  if (a.abort && *a.abort) return;
   __shared__ uint32_t warp_sum[32];
   __shared__ uint32_t s_total;
   __shared__ int s_fail;
@@ -723,11 +765,12 @@ __global__ void __launch_bounds__(kBlock) k_nodes(BuildArgs a, lod_node_t* __res
   uint32_t* ls = lvl_start + (uint64_t)t * (kMaxLevels + 1);
   if (threadIdx.x == 0) {
     lod_node_t r;
-    r.min[0] = td.min[0];
-    r.min[1] = td.min[1];
-    r.min[2] = td.min[2];
+    const SrcDesc& rs = a.srcs[t];  // the tile's first counting grid covers the root cube
+    r.min[0] = rs.min[0];
+    r.min[1] = rs.min[1];
+    r.min[2] = rs.min[2];
     r.level = 0;
-    r.log2_size = (uint8_t)td.log2S;
+    r.log2_size = (uint8_t)rs.log2size;
     r.child_mask = 0;
     r.flags = 0;
     r.parent = kNone;

@@ -14,6 +14,8 @@ struct PyrJob {
 // ----- split (Section 4.1) -----
 cudaError_t launch_bbox(const TileDesc* tiles, const uint32_t* chunk_tile, uint64_t n_chunks,
                         const uint64_t* tile_chunk0, int* bbox, int grid, cudaStream_t st);
+cudaError_t launch_roots(const TileDesc* tiles, const int* bbox, SrcDesc* srcs, uint32_t n_tiles, uint32_t T,
+                         uint32_t max_depth, unsigned int* abort, cudaStream_t st);
 cudaError_t launch_count(const BuildArgs& a, const uint32_t* chunk_src, const unsigned long long* n_chunks,
                          int grid, cudaStream_t st);
 cudaError_t launch_pyr_up(const BuildArgs& a, const PyrJob* jobs, uint32_t n_jobs, cudaStream_t st);
