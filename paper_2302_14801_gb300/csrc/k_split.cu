@@ -6,15 +6,17 @@
 // 128-bit loads in 4096-point chunks; each CTA owns a contiguous run of
 // chunks so that per-source state (a shared-memory histogram, a reduction)
 // is flushed only when the source changes.  Counting grids of up to 8^4
-// cells use a dense shared-memory histogram; larger first grids (up to
-// 256^3 cells) count through a per-CTA shared-memory hash table of the
-// cells the CTA's chunks touch, whose (cell, count) list is flushed with
-// one global atomic per distinct cell and reused by the scatter to claim
-// one block of positions per cell.  Points of cells that miss the table
-// fall back to warp-aggregated global atomics.  Grid pyramids (per-level
-// sums and exclusive-scan starts) are built in 4-level blocks in shared
-// memory.  With kept input indices the scatter writes one full 32-byte
-// sector per point.  No kernel ever waits on another CTA.
+// cells use a dense shared-memory histogram; larger grids (first grids up
+// to 256^3 cells, deep refinement grids) count through a per-CTA
+// shared-memory hash table of the cells the CTA's chunks touch.  Every
+// counted cell is published with one global atomic and listed as (cell,
+// count), so that the scatter claims one block of positions per listed
+// cell; cells that miss the table or the list use warp-aggregated global
+// atomics on their cursor.  Grid pyramids (per-level sums and
+// exclusive-scan starts) are built in 4-level blocks in shared memory.
+// With kept input indices the scatter writes one full 32-byte sector per
+// point.  The root cubes are computed on the device (no host round trip
+// after the bounding box).  No kernel ever waits on another CTA.
 #include <climits>
 
 #include "common.cuh"
