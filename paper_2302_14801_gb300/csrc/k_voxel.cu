@@ -633,6 +633,31 @@ __global__ void __launch_bounds__(kBlock, 1) k_vox_units(BuildArgs a, VoxLevel v
   }
 }
 
+// Levels with few items (the top of the tree) would leave most SMs idle
+// with one CTA per item: every item is split up front into 2^m hash
+// partitions (its staging block reserved here) and the partition kernel
+// spreads them over the SMs.
+__global__ void k_vox_split(BuildArgs a, VoxLevel v, DevCounters* __restrict__ ctr, uint32_t m) {
+  const uint32_t it = blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= v.n_items) return;
+  const uint32_t t = find_tile(v.item_prefix, a.n_tiles, it);
+  const uint32_t* ls = v.lvl_start + (uint64_t)t * (kMaxLevels + 1);
+  const uint64_t g = a.tiles[t].node_base + ls[v.level + 1] + (it - v.item_prefix[t]);
+  const lod_node_t& c = v.nodes[g];
+  const uint64_t n = (c.flags & LOD_NODE_LEAF) ? c.point_count : c.voxel_count;
+  const uint64_t bound = umin64(n, kOctCells);
+  const unsigned long long base = atomicAdd(v.stage_used, (unsigned long long)bound);
+  if (base + bound > v.stage_cap) atomicOr(&ctr->error, kErrStageCap);
+  v.aux[g].stage = base;
+  v.aux[g].occ = 0u;
+  const uint32_t q = atomicAdd(&ctr->units, 1u << m);
+  if (q + (1u << m) > v.unit_cap) {
+    atomicOr(&ctr->error, kErrInternal);
+    return;
+  }
+  for (uint32_t j = 0; j < (1u << m); ++j) v.units[q + j] = make_uint4(it, j, m, 0u);
+}
+
 template <int MODE>
 static cudaError_t launch_vox_mode(const BuildArgs& a, const VoxLevel& v, DevCounters* ctr, cudaStream_t st) {
   static int sms = [] {
@@ -643,6 +668,13 @@ static cudaError_t launch_vox_mode(const BuildArgs& a, const VoxLevel& v, DevCou
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     return n > 0 ? n : 1;
   }();
+  if (v.units && v.n_items * 4u <= (uint32_t)sms) {
+    uint32_t m = 0;
+    while (m < 3 && (v.n_items << (m + 1)) <= (uint32_t)sms) ++m;
+    k_vox_split<<<(v.n_items + 127) / 128, 128, 0, st>>>(a, v, ctr, m);
+    k_vox_units<MODE><<<sms, kBlock, kSmemBytes, st>>>(a, v, ctr);
+    return cudaGetLastError();
+  }
   k_vox<MODE><<<v.n_items < (uint32_t)sms ? v.n_items : (uint32_t)sms, kBlock, kSmemBytes, st>>>(a, v, ctr);
   if (v.units) k_vox_units<MODE><<<sms, kBlock, kSmemBytes, st>>>(a, v, ctr);
   return cudaGetLastError();
