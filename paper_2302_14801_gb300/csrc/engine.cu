@@ -366,7 +366,6 @@ struct Prof {
     if (a) cudaEventRecord(a, st);
   }
   void end(const char* name, double bytes) {
-    g_launches.fetch_add(1);
     if (!on || !a) return;
     cudaEvent_t b = pool_event();
     if (!b) return;
@@ -495,6 +494,7 @@ int profile_read(lod_kernel_stat_t* out, uint32_t cap, uint32_t* n) {
 }
 
 uint64_t launch_count() { return g_launches.load(); }
+void note_launch() { g_launches.fetch_add(1); }
 
 static std::mutex g_free_mu;
 static cudaStream_t g_free_streams[64] = {};

@@ -223,6 +223,7 @@ cudaError_t launch_roots(const TileDesc* tiles, const int* bbox, SrcDesc* srcs, 
                          uint32_t max_depth, unsigned int* abort, cudaStream_t st) {
   if (!n_tiles) return cudaSuccess;
   k_roots<<<(n_tiles + 255) / 256, 256, 0, st>>>(tiles, bbox, srcs, n_tiles, T, max_depth, abort);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -231,6 +232,7 @@ cudaError_t launch_bbox(const TileDesc* tiles, const uint32_t* chunk_tile, uint6
   if (n_chunks == 0) return cudaSuccess;
   grid = (int)umin64((uint64_t)grid, n_chunks);
   k_bbox<<<grid, kBlock, 0, st>>>(tiles, chunk_tile, n_chunks, tile_chunk0, bbox);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -430,6 +432,7 @@ cudaError_t launch_count(const BuildArgs& a, const uint32_t* chunk_src, const un
   }();
   (void)once;
   k_count<<<grid, kBlock, 8 * kPrivSlots, st>>>(a, chunk_src, n_chunks);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -470,6 +473,7 @@ __global__ void __launch_bounds__(512) k_pyr_up(BuildArgs a, const PyrJob* __res
 cudaError_t launch_pyr_up(const BuildArgs& a, const PyrJob* jobs, uint32_t n_jobs, cudaStream_t st) {
   if (!n_jobs) return cudaSuccess;
   k_pyr_up<<<n_jobs, 512, 0, st>>>(a, jobs);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -574,6 +578,7 @@ cudaError_t launch_pyr_down(const BuildArgs& a, const PyrJob* jobs, uint32_t n_j
                             uint32_t next_cap, uint32_t next_buf, DevCounters* ctr, cudaStream_t st) {
   if (!n_jobs) return cudaSuccess;
   k_pyr_down<<<n_jobs, 512, 0, st>>>(a, jobs, next_base, next_cap, next_buf, ctr);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -739,6 +744,7 @@ cudaError_t launch_scatter(const BuildArgs& a, const uint32_t* chunk_src, const 
   }();
   (void)once;
   k_scatter<<<grid, kBlock, 9 * kPrivSlots, st>>>(a, chunk_src, n_chunks, round);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -925,6 +931,7 @@ __global__ void __launch_bounds__(kBlock) k_nodes(BuildArgs a, lod_node_t* __res
 cudaError_t launch_nodes(const BuildArgs& a, lod_node_t* nodes, NodeAux* aux, uint32_t* lvl_start,
                          uint32_t* n_nodes, unsigned long long* leaf_cap, DevCounters* ctr, cudaStream_t st) {
   k_nodes<<<a.n_tiles, kBlock, 0, st>>>(a, nodes, aux, lvl_start, n_nodes, leaf_cap, ctr);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -672,11 +672,15 @@ static cudaError_t launch_vox_mode(const BuildArgs& a, const VoxLevel& v, DevCou
     uint32_t m = 0;
     while (m < 3 && (v.n_items << (m + 1)) <= (uint32_t)sms) ++m;
     k_vox_split<<<(v.n_items + 127) / 128, 128, 0, st>>>(a, v, ctr, m);
+    note_launch();
     k_vox_units<MODE><<<sms, kBlock, kSmemBytes, st>>>(a, v, ctr);
+    note_launch();
     return cudaGetLastError();
   }
   k_vox<MODE><<<v.n_items < (uint32_t)sms ? v.n_items : (uint32_t)sms, kBlock, kSmemBytes, st>>>(a, v, ctr);
+  note_launch();
   if (v.units) k_vox_units<MODE><<<sms, kBlock, kSmemBytes, st>>>(a, v, ctr);
+  if (v.units) note_launch();
   return cudaGetLastError();
 }
 
@@ -762,6 +766,7 @@ cudaError_t launch_level_scan(const BuildArgs& a, const VoxLevel& v, const uint3
                               uint32_t n_parents, unsigned long long* tile_voxels, DevCounters* ctr,
                               cudaStream_t st) {
   k_level_scan<<<1, kBlock, 0, st>>>(a, v, parent_prefix, n_parents, tile_voxels, ctr);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -780,6 +785,7 @@ __global__ void __launch_bounds__(256) k_copy_items(BuildArgs a, VoxLevel v) {
 cudaError_t launch_copy_items(const BuildArgs& a, const VoxLevel& v, cudaStream_t st) {
   if (!v.n_items) return cudaSuccess;
   k_copy_items<<<v.n_items, 256, 0, st>>>(a, v);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -804,6 +810,7 @@ cudaError_t launch_unwide(const BuildArgs& a, const uint32_t* tiles, uint32_t n_
   for (uint32_t t0 = 0; t0 < n_tiles; t0 += 65535) {
     const uint32_t m = n_tiles - t0 < 65535 ? n_tiles - t0 : 65535;
     k_unwide<<<dim3(gx ? gx : 1, m), 256, 0, st>>>(a, tiles + t0);
+    note_launch();
   }
   return cudaGetLastError();
 }
@@ -822,6 +829,7 @@ cudaError_t launch_gather_voxels(const lod_node_t* nodes, uint32_t n_nodes, cons
                                  const int4* src, int4* dst, cudaStream_t st) {
   if (!n_nodes) return cudaSuccess;
   k_gather_voxels<<<n_nodes, 256, 0, st>>>(nodes, new_off, src, dst);
+  note_launch();
   return cudaGetLastError();
 }
 

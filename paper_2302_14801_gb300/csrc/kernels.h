@@ -5,6 +5,10 @@
 
 namespace lodk {
 
+// Counts kernel launches of the library (lod_launch_count); every launch
+// site calls it once per kernel it launches.
+void note_launch();
+
 struct PyrJob {
   uint32_t src;    // source id
   uint32_t lvl;    // up: bottom level of the block; down: top level of the block

@@ -21,6 +21,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "kernels.h"
 
 namespace lodk {
 namespace {
@@ -155,13 +156,16 @@ extern "C" int lod_root_cubes_noalloc(const lod_point_t* const* d_tiles, const u
     if (e != cudaSuccess) return LOD_ERR_CUDA;
   }
   k_na_clear<<<(n_tiles + 255) / 256, 256, 0, st>>>(s, n_tiles);
+  lodk::note_launch();
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   uint64_t gx = (max_n + 256 * 16 - 1) / (256 * 16);
   gx = gx < 1 ? 1 : (gx > (uint64_t)(4 * sms) ? (uint64_t)(4 * sms) : gx);
   k_na_bbox<<<dim3((unsigned)gx, n_tiles), 256, 0, st>>>(s);
+  lodk::note_launch();
   k_na_cube<<<(n_tiles + 255) / 256, 256, 0, st>>>(s, n_tiles, d_cubes);
+  lodk::note_launch();
   e = cudaGetLastError();
   return e == cudaSuccess ? LOD_OK : LOD_ERR_CUDA;
 }
