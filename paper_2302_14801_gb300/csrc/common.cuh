@@ -110,7 +110,6 @@ struct DevCounters {
   unsigned long long new_points;      // points inside them
   unsigned long long stage_used[2];   // staging records bump allocators
   unsigned long long level_voxels;    // voxels of the level just scanned
-  unsigned long long next_cap;        // staging bound of the next level
   unsigned long long vox_retries;     // voxel items that needed more table passes
   unsigned long long vox_passes;      // table passes over all voxel items
   unsigned int error;                 // nonzero: a kernel detected a problem
@@ -129,22 +128,6 @@ enum : uint32_t {
 // ----------------------------------------------------------- device helpers
 
 __host__ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
-
-// Spread the low 10 bits of v so that bit b lands on bit 3b.
-__host__ __device__ __forceinline__ uint32_t spread3(uint32_t v) {
-  v &= 0x3FFu;
-  v = (v | (v << 16)) & 0x030000FFu;
-  v = (v | (v << 8)) & 0x0300F00Fu;
-  v = (v | (v << 4)) & 0x030C30C3u;
-  v = (v | (v << 2)) & 0x09249249u;
-  return v;
-}
-
-// Morton index of a cell; within every bit triple x is the most significant,
-// so the low triple is the octant index k = 4*bx + 2*by + bz.
-__host__ __device__ __forceinline__ uint32_t morton3(uint32_t x, uint32_t y, uint32_t z) {
-  return (spread3(x) << 2) | (spread3(y) << 1) | spread3(z);
-}
 
 // splitmix64 (Steele, Lea & Flood, OOPSLA 2014): first output of a generator
 // whose state is x.

@@ -30,6 +30,8 @@ __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
 // Morton cell of point p inside a source grid (8^d cells under a cube of
 // edge 2^log2size with min corner mn).
+// Morton index of a grid cell: within every bit triple x is the most
+// significant, so the low triple is the octant index k = 4*bx + 2*by + bz.
 // Grids have d <= 8, so each coordinate has at most 8 bits and the shift
 // log2size - d is at most 31.
 __device__ __forceinline__ uint32_t spread3_8(uint32_t v) {

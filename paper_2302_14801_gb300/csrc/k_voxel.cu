@@ -755,7 +755,6 @@ __global__ void __launch_bounds__(kBlock) k_level_scan(BuildArgs a, VoxLevel v, 
     const uint64_t cnt = v.aux[l].dense + v.aux[l].occ - off;
     p.voxel_offset = off;
     p.voxel_count = (uint32_t)cnt;
-    atomicAdd(&ctr->next_cap, (unsigned long long)umin64(cnt, kOctCells));
     atomicAdd(&tile_voxels[t], (unsigned long long)cnt);
   }
   __syncthreads();  // every thread has read vstate[0]
