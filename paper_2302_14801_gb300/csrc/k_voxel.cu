@@ -482,7 +482,7 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
             // occupied cells projected from the part seen so far
             const uint64_t sn = S.seen ? S.seen : 1u;
             const uint64_t est = umin64(bound, (uint64_t)used * I.n / sn + (uint64_t)used / 4 + 1);
-            const uint64_t per = table_capacity(H) / 4 * 3;
+            const uint64_t per = table_capacity(H);
             uint32_t m = 1;
             while (m < kMaxQueuedLog && (est >> m) > per) ++m;
             uint32_t q0 = 0;
