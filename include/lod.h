@@ -203,6 +203,23 @@ void lod_free(lod_result_t* r);
 /* Static description of a status code. */
 const char* lod_error_string(int status);
 
+/* ------------------------------------------------------ device memory */
+
+/* Every build keeps its scratch buffers (counting pools, ping-pong and
+ * staging arrays: up to about 100 bytes per input point) in a workspace
+ * tied to (current device, stream), reused by the next build on that stream
+ * without allocator calls; results come from the device's stream-ordered
+ * pool, which the library sets to keep freed memory for reuse.  The paper
+ * has no counterpart (its buffers are allocated once, Section 4.1.6).
+ * lod_scratch_bytes: device bytes the workspace of `stream` holds now.
+ * lod_trim: waits for `stream` to finish its work, frees its workspace and
+ *   returns the pool's unused memory to the device.  Results stay valid;
+ *   the next build on the stream allocates its scratch again.  A workspace
+ *   that a build on another thread is using at that moment is left alone.
+ *   Returns LOD_ERR_CUDA if the synchronisation reports an error. */
+uint64_t lod_scratch_bytes(void* stream);
+int lod_trim(void* stream);
+
 /* ------------------------------------------------------- no allocation */
 
 /* Root cube of each of n_tiles point clouds, computed without allocating

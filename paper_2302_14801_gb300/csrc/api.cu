@@ -211,6 +211,20 @@ void lod_free(lod_result_t* r) {
   delete r;
 }
 
+uint64_t lod_scratch_bytes(void* stream) { return lodk::workspace_bytes(static_cast<cudaStream_t>(stream)); }
+
+int lod_trim(void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return to_status(e);
+  lodk::release_workspace(st);
+  int dev = 0;
+  cudaMemPool_t pool;
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess)
+    e = cudaMemPoolTrimTo(pool, 0);
+  return to_status(e);
+}
+
 int lod_set_tuning(const lod_tuning_t* t) { return t ? lodk::set_tuning(*t) : LOD_ERR_INVALID_ARG; }
 int lod_get_tuning(lod_tuning_t* t) { return t ? lodk::get_tuning(t) : LOD_ERR_INVALID_ARG; }
 

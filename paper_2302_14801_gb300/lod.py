@@ -34,7 +34,8 @@ EXPORTED = [
     "lod_result_copy_to_host", "lod_result_device_bytes", "lod_free", "lod_error_string",
     "lod_server_create", "lod_submit", "lod_poll", "lod_wait", "lod_server_bytes_in_use",
     "lod_server_destroy", "lod_profile_enable", "lod_profile_reset", "lod_profile_read", "lod_launch_count",
-    "lod_root_cubes_noalloc", "lod_set_tuning", "lod_get_tuning", "lod_autotune",
+    "lod_root_cubes_noalloc", "lod_set_tuning", "lod_get_tuning", "lod_autotune", "lod_scratch_bytes",
+    "lod_trim",
 ]
 
 
@@ -116,6 +117,8 @@ def _load():
         "lod_set_tuning": (i, [P(Tuning)]),
         "lod_get_tuning": (i, [P(Tuning)]),
         "lod_autotune": (i, [vp, u64, P(Params), vp, P(Tuning), P(ctypes.c_float)]),
+        "lod_scratch_bytes": (u64, [vp]),
+        "lod_trim": (i, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -201,6 +204,17 @@ def autotune(points, leaf_threshold=50000, mode=FILTER, max_depth=21, stream=Non
 
 def launch_count() -> int:
     return int(lib().lod_launch_count())
+
+
+def scratch_bytes(stream=None) -> int:
+    """Device bytes of build scratch kept for ``stream`` (lod_scratch_bytes)."""
+    return int(lib().lod_scratch_bytes(_stream_handle(stream)))
+
+
+def trim(stream=None) -> None:
+    """lod_trim: wait for ``stream``, free its kept scratch and return the
+    pool's unused memory to the device; results stay valid."""
+    _check(lib().lod_trim(_stream_handle(stream)), "lod_trim")
 
 
 class _DevArray:

@@ -219,6 +219,27 @@ def test_build_from_host(lod):
     compare(got, oracle.build(pts, 4000, 1, 21), inp=pts)
 
 
+def test_trim_frees_scratch_and_keeps_results(lod):
+    import torch
+    pts = synth.aerial(400_000, seed=23, n_buildings=10)
+    want = oracle.build(pts, 5000, 0, 21)
+    st = torch.cuda.Stream()
+    d = torch.from_numpy(pts).cuda()
+    torch.cuda.synchronize()
+    r = lod.build(d, 5000, 0, stream=st)
+    assert lod.scratch_bytes(st) > 0  # the stream keeps its workspace
+    lod.trim(st)
+    assert lod.scratch_bytes(st) == 0
+    compare(r.to_host(stream=st), want, inp=pts)  # a result outlives the trim
+    r.free()
+    r = lod.build(d, 5000, 0, stream=st)  # the next build allocates again
+    assert lod.scratch_bytes(st) > 0
+    compare(r.to_host(stream=st), want, inp=pts)
+    r.free()
+    lod.trim(st)
+    assert lod.scratch_bytes(st) == 0
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_batched_equals_single(lod, mode):
     import torch
