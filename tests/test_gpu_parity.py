@@ -286,3 +286,14 @@ def test_server_budget_rejects_oversized(lod):
         assert e.value.status == lod.LOD_ERR_BUDGET
     finally:
         srv.close()
+
+
+# ---------------------------------------------------------------- golden
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_hand_worked_examples(lod, mode):
+    import golden
+    for path in golden.fixtures():
+        fx = golden.load(path)
+        got = gpu_build(lod, fx["input"], fx["T"], mode, fx["max_depth"])
+        golden.check(got, fx, mode)

@@ -10,10 +10,13 @@ definitions and by mathematics, not by the oracle itself.
 * An independent brute-force checker (tests/bruteforce.py) on random tiny
   clouds with small T (deep trees), in both modes.
 * Cross-mode identities: identical cells and counts in both modes.
+* Hand-worked examples under tests/golden/ (whole results in both modes,
+  each derivation written out in its file).
 """
 import numpy as np
 import pytest
 
+import golden
 import oracle
 from bruteforce import check, splitmix64_py
 from paper_2302_14801_gb300 import synth
@@ -384,3 +387,29 @@ def test_cube_voxels_rejects_points_outside():
     pts = P([(0, 0, 0, 1, 2, 3), (8, 0, 0, 1, 2, 3)])
     with pytest.raises(ValueError):
         oracle.cube_voxels(pts, np.arange(2), (0, 0, 0), 3, 0)
+
+
+# ------------------------------------------------------------------ golden
+# Hand-derived worked examples (tests/golden/): the oracle reproduces every
+# node, leaf and voxel in both modes.
+
+
+@pytest.mark.parametrize("path", golden.fixtures(), ids=lambda p: p.rsplit("/", 1)[-1])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_oracle_reproduces_hand_worked_examples(path, mode):
+    fx = golden.load(path)
+    res = oracle.build(fx["input"], fx["T"], mode, fx["max_depth"])
+    golden.check(res, fx, mode)
+
+
+def test_golden_check_catches_planted_mistakes():
+    # a wrong rounding, a dropped count and a wrong pick are all caught
+    fx = golden.load(golden.fixtures()[0])
+    res = oracle.build(fx["input"], fx["T"], 0, fx["max_depth"])
+    for mutate in (lambda v: v.__setitem__((0, 1), v[0, 1] + 1), lambda v: v.__setitem__((0, 2), v[0, 2] - 1),
+                   lambda v: v.__setitem__((0, 3), 7)):
+        bad = dict(res)
+        bad["voxels"] = np.array(res["voxels"], copy=True).reshape(-1, 4)
+        mutate(bad["voxels"])
+        with pytest.raises(AssertionError):
+            golden.check(bad, fx, 0)
