@@ -5,8 +5,8 @@
 // shares no code, header, table or helper with the CUDA library.
 //
 // It is a plain, single-threaded restatement of what the method computes,
-// written top-down per node from the definitions, with no blocking, fusion
-// or bottom-up merging:
+// written from the definitions with no blocking or fusion; the average and
+// pick modes are computed top-down per node, without bottom-up merging:
 //
 //  * Root cube (Section 4 with the reading that the paper's float coordinates
 //    become int32): the bounding box minimum is the cube's min corner and
@@ -31,13 +31,23 @@
 //    exact u64 sums over all original points of the cube and a rounded-half-
 //    up integer mean, alpha 255; sample pick (replacing the random pick of
 //    Section 4.2.2, Listing 1) keeps the point of minimal splitmix64(index).
+//  * Neighbourhood-weighted average (Section 4.2.4; mode 2) follows the
+//    paper's own order instead, since its result depends on it: inner nodes
+//    deepest level first, each sampling its children's samples (the points
+//    of leaf children, the voxels of inner children at their cell centres).
+//    A sample adds weight max(0, 1 - distance to the cell centre, in cells)
+//    times its colour to the cells of the 2x2x2 block around it and marks
+//    the cell it lies in as occupied; an occupied cell's colour is its
+//    weighted sum over its weight sum.  Arithmetic in double precision.
 //
 // Function-level citations are beside each function.
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <new>
 #include <utility>
 #include <vector>
@@ -68,6 +78,7 @@ struct OVoxel {
 };
 
 constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint32_t kModeWeighted = 2u;
 constexpr uint32_t kLeaf = 1u;
 constexpr uint32_t kOverfull = 2u;
 
@@ -164,6 +175,105 @@ struct Builder {
     nd.voxel_count = (uint32_t)(voxels.size() - nd.voxel_offset);
   }
 
+  // Section 4.2.4: one inner node's voxels under the neighbourhood-weighted
+  // average, from its children's samples (their voxels must exist already).
+  // Positions are in units of the node's grid cells, so the node's cube is
+  // [0, 128)^3 and cell j has its centre at j + 1/2.
+  struct WCell {
+    double r = 0, g = 0, b = 0, w = 0;  // weighted colour sums, weight sum
+    uint64_t count = 0;                 // original points in the cell
+    bool occupied = false;
+  };
+  static void add_weighted(std::map<uint32_t, WCell>& cells, const double pos[3], const uint32_t own[3],
+                           uint32_t rgba, uint64_t count) {
+    WCell& home = cells[own[0] | (own[1] << 7) | (own[2] << 14)];
+    home.occupied = true;
+    home.count += count;
+    // the cells whose centres lie within one cell width along every axis:
+    // floor(pos - 1/2) and the next one, inside the grid
+    int64_t lo[3];
+    for (int a = 0; a < 3; ++a) lo[a] = (int64_t)std::floor(pos[a] - 0.5);
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+          const int64_t j[3] = {lo[0] + dx, lo[1] + dy, lo[2] + dz};
+          bool inside = true;
+          double d2 = 0;
+          for (int a = 0; a < 3; ++a) {
+            if (j[a] < 0 || j[a] > 127) inside = false;
+            const double e = pos[a] - ((double)j[a] + 0.5);
+            d2 += e * e;
+          }
+          if (!inside) continue;
+          const double w = 1.0 - std::sqrt(d2);  // linear weight, zero beyond one cell
+          if (w <= 0) continue;
+          WCell& c = cells[(uint32_t)j[0] | ((uint32_t)j[1] << 7) | ((uint32_t)j[2] << 14)];
+          c.r += w * (double)(rgba & 0xFFu);
+          c.g += w * (double)((rgba >> 8) & 0xFFu);
+          c.b += w * (double)((rgba >> 16) & 0xFFu);
+          c.w += w;
+        }
+  }
+
+  void voxelize_weighted(uint32_t id) {
+    ONode& nd = nodes[id];
+    std::map<uint32_t, WCell> cells;
+    const double scale = std::ldexp(1.0, 7 - (int)nd.log2_size);  // grid cells per unit of length
+    uint32_t c = nd.first_child;
+    for (uint32_t k = 0; k < 8; ++k) {
+      if (!(nd.child_mask & (1u << k))) continue;
+      const ONode& ch = nodes[c];
+      if (ch.flags & kLeaf) {
+        // a leaf child's samples are its points
+        for (uint32_t i : leaf_lists[c]) {
+          const OPoint& p = pts[i];
+          const int64_t d[3] = {rel(p.x, nd.min[0]), rel(p.y, nd.min[1]), rel(p.z, nd.min[2])};
+          double pos[3];
+          uint32_t own[3];
+          for (int a = 0; a < 3; ++a) {
+            pos[a] = (double)d[a] * scale;
+            own[a] = grid_coord(d[a], nd.log2_size);
+          }
+          add_weighted(cells, pos, own, p.rgba, 1);
+        }
+      } else {
+        // an inner child's samples are its voxels, each at the centre of its
+        // cell; the child is one octant (half the edge) of this node
+        const uint32_t b[3] = {(k >> 2) & 1u, (k >> 1) & 1u, k & 1u};
+        for (uint32_t v = 0; v < ch.voxel_count; ++v) {
+          const OVoxel& vx = voxels[ch.voxel_offset + v];
+          const uint32_t q[3] = {vx.cell & 127u, (vx.cell >> 7) & 127u, (vx.cell >> 14) & 127u};
+          double pos[3];
+          uint32_t own[3];
+          for (int a = 0; a < 3; ++a) {
+            pos[a] = 64.0 * b[a] + ((double)q[a] + 0.5) / 2.0;
+            own[a] = 64u * b[a] + (q[a] >> 1);
+          }
+          add_weighted(cells, pos, own, vx.rgba, vx.count);
+        }
+      }
+      ++c;
+    }
+    // occupied cells only, in cell order; colour = weighted mean rounded to
+    // the nearest integer (halves up), alpha 255
+    nd.voxel_offset = voxels.size();
+    for (const auto& kv : cells) {
+      const WCell& wc = kv.second;
+      if (!wc.occupied) continue;
+      auto channel = [&](double sum) {
+        const double m = std::floor(sum / wc.w + 0.5);
+        return (uint32_t)std::min(255.0, std::max(0.0, m));
+      };
+      OVoxel v;
+      v.cell = kv.first;
+      v.rgba = channel(wc.r) | (channel(wc.g) << 8) | (channel(wc.b) << 16) | (255u << 24);
+      v.count = (uint32_t)wc.count;
+      v.pick_index = kNone;
+      voxels.push_back(v);
+    }
+    nd.voxel_count = (uint32_t)(voxels.size() - nd.voxel_offset);
+  }
+
   // Depth-first leaf layout: each node's point_offset is where its subtree
   // starts; a leaf copies its points there in input order.
   uint64_t layout(uint32_t id, uint64_t offset) {
@@ -252,9 +362,14 @@ struct Builder {
           leaf_lists.emplace_back();
           next.emplace_back((uint32_t)(nodes.size() - 1), std::move(part[k]));
         }
-        voxelize(nodes[id], idx);
+        if (mode != kModeWeighted) voxelize(nodes[id], idx);
       }
       std::swap(cur, next);
+    }
+    if (mode == kModeWeighted) {
+      // bottom up: breadth-first ids put every child after its parent
+      for (size_t id = nodes.size(); id-- > 0;)
+        if (!(nodes[id].flags & kLeaf)) voxelize_weighted((uint32_t)id);
     }
     leaf_points.resize(n);
     leaf_index.resize(n);
@@ -270,10 +385,12 @@ struct oracle_result {
 
 extern "C" {
 
-// Returns 0 on success, 1 on invalid arguments, 2 on allocation failure.
+// mode 0: cell-wise average, 1: sample pick, 2: neighbourhood-weighted
+// average.  Returns 0 on success, 1 on invalid arguments, 2 on allocation
+// failure.
 int oracle_build(const void* points, uint64_t n, uint32_t leaf_threshold, uint32_t mode,
                  uint32_t max_depth, oracle_result** out) {
-  if (!out || (n > 0 && !points) || leaf_threshold == 0 || mode > 1 || max_depth > 32 ||
+  if (!out || (n > 0 && !points) || leaf_threshold == 0 || mode > kModeWeighted || max_depth > 32 ||
       n > 0xFFFFFFFFull)
     return 1;
   oracle_result* r = new (std::nothrow) oracle_result();

@@ -1,7 +1,9 @@
 """Hand-derived worked examples under tests/golden/ and the check of a LOD
 result against them.
 
-Each fixture holds a tiny input, the leaf threshold and depth cap, and the
+Each fixture holds a tiny input, the leaf threshold and depth cap, the
+sampling modes it covers (filtered, pick, and the neighbourhood-weighted
+average of Section 4.2.4, which only the oracle computes so far), and the
 whole expected result worked out by hand from the method's definitions
 (every file's header shows the derivation and cites the sections and
 readings it follows).  The expected values come from neither the oracle
@@ -15,7 +17,7 @@ import numpy as np
 
 HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 NONE = 0xFFFFFFFF
-MODES = {"filtered": 0, "pick": 1}
+MODES = {"filtered": 0, "pick": 1, "weighted": 2}
 
 
 def pack(r, g, b, a):
@@ -27,7 +29,7 @@ def u32(v):
 
 
 def load(path):
-    fx = {"points": [], "nodes": [], "leaves": {}, "voxels": {0: {}, 1: {}}, "name": os.path.basename(path)}
+    fx = {"points": [], "nodes": [], "leaves": {}, "voxels": {0: {}, 1: {}, 2: {}}, "name": os.path.basename(path)}
     for line in open(path):
         line = line.split("#", 1)[0].strip()
         if not line:
@@ -38,6 +40,8 @@ def load(path):
             fx["T"] = int(v[0])
         elif tag == "max_depth":
             fx["max_depth"] = int(v[0])
+        elif tag == "modes":  # the modes whose voxels the file states
+            fx["modes"] = sorted(MODES[t] for t in v)
         elif tag == "point":
             x, y, z, r, g, b = (int(t) for t in v)
             fx["points"].append((x, y, z, pack(r, g, b, 255)))
@@ -59,6 +63,11 @@ def load(path):
 
 def fixtures():
     return sorted(glob.glob(os.path.join(HERE, "*.txt")))
+
+
+def cases(modes=(0, 1, 2)):
+    """(path, mode) for every fixture and every stated mode among ``modes``."""
+    return [(p, m) for p in fixtures() for m in load(p)["modes"] if m in modes]
 
 
 def check(res: dict, fx: dict, mode: int) -> None:

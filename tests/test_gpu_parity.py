@@ -293,7 +293,7 @@ def test_server_budget_rejects_oversized(lod):
 @pytest.mark.parametrize("mode", [0, 1])
 def test_hand_worked_examples(lod, mode):
     import golden
-    for path in golden.fixtures():
+    for path, m in golden.cases(modes=(mode,)):
         fx = golden.load(path)
-        got = gpu_build(lod, fx["input"], fx["T"], mode, fx["max_depth"])
-        golden.check(got, fx, mode)
+        got = gpu_build(lod, fx["input"], fx["T"], m, fx["max_depth"])
+        golden.check(got, fx, m)

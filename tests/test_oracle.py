@@ -10,8 +10,12 @@ definitions and by mathematics, not by the oracle itself.
 * An independent brute-force checker (tests/bruteforce.py) on random tiny
   clouds with small T (deep trees), in both modes.
 * Cross-mode identities: identical cells and counts in both modes.
-* Hand-worked examples under tests/golden/ (whole results in both modes,
-  each derivation written out in its file).
+* Hand-worked examples under tests/golden/ (whole results in every mode
+  each file states, each derivation written out in its file).
+* Neighbourhood-weighted average (Section 4.2.4, oracle mode 2): the mean
+  of the corner samples on cubes of edge <= 128 (equal weights), cells and
+  counts equal to the average mode's, constant colours exact, channels
+  within the input's range.
 """
 import numpy as np
 import pytest
@@ -304,7 +308,7 @@ def test_rejects_bad_arguments():
     with pytest.raises(ValueError):
         oracle.build(pts, 0, 0)
     with pytest.raises(ValueError):
-        oracle.build(pts, 10, 2)
+        oracle.build(pts, 10, 3)  # modes: 0 average, 1 pick, 2 weighted
     with pytest.raises(ValueError):
         oracle.build(pts, 10, 0, 33)
 
@@ -394,8 +398,8 @@ def test_cube_voxels_rejects_points_outside():
 # node, leaf and voxel in both modes.
 
 
-@pytest.mark.parametrize("path", golden.fixtures(), ids=lambda p: p.rsplit("/", 1)[-1])
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("path,mode", golden.cases(),
+                         ids=lambda v: v.rsplit("/", 1)[-1] if isinstance(v, str) else str(v))
 def test_oracle_reproduces_hand_worked_examples(path, mode):
     fx = golden.load(path)
     res = oracle.build(fx["input"], fx["T"], mode, fx["max_depth"])
@@ -413,3 +417,132 @@ def test_golden_check_catches_planted_mistakes():
         mutate(bad["voxels"])
         with pytest.raises(AssertionError):
             golden.check(bad, fx, 0)
+
+
+# ----------------------------------------------- neighbourhood-weighted mode
+# Pins of the oracle's neighbourhood-weighted average (Section 4.2.4, mode
+# 2), beside the hand-worked examples above.
+
+
+def clustered_corner_cloud(L, seed, n_clusters=8, per=60, box=6):
+    """Points on integer positions of a cube of edge 2^L (L <= 7), in small
+    clusters spread over all eight octants so that the root is inner and
+    all its children are leaves (T = 100)."""
+    rng = np.random.default_rng(seed)
+    edge = 1 << L
+    half = edge // 2
+    rows = [(0, 0, 0), (edge - 1, edge - 1, edge - 1)]  # fix the cube
+    for k in range(n_clusters):
+        o = np.array([(k >> 2) & 1, (k >> 1) & 1, k & 1]) * half
+        c = o + rng.integers(0, half - box, size=3)
+        rows += [tuple(int(t) for t in c + rng.integers(0, box, size=3)) for _ in range(per)]
+    xyz = np.array(rows, np.int64)
+    col = rng.integers(0, 256, size=(len(rows), 3))
+    return P(np.concatenate([xyz, col], axis=1))
+
+
+def check_corner_means(pts, res, L):
+    """The root's weighted voxels against the corner rule (see the test
+    below): cells, colours (rounded half up; either neighbour on an exact
+    half, where the double-precision sum may fall on either side) and
+    counts.  Returns the number of cells with more than one sample."""
+    scale = 1 << (7 - L)
+    g = (pts[:, :3].astype(np.int64) - res["min"][0]) * scale
+    rgb = np.stack([(pts[:, 3].view(np.uint32) >> s) & 255 for s in (0, 8, 16)], axis=1).astype(np.int64)
+    by_pos = {}
+    for pos, c in zip(map(tuple, g), rgb):
+        by_pos.setdefault(pos, []).append(c)
+    a, n = int(res["voxel_offset"][0]), int(res["voxel_count"][0])
+    vox = res["voxels"][a:a + n]
+    assert set(int(v) for v in vox[:, 0]) == {x | y << 7 | z << 14 for x, y, z in by_pos}
+    multi = 0
+    for cell, rgba, cnt, pick in vox:
+        j = (int(cell) & 127, (int(cell) >> 7) & 127, int(cell) >> 14)
+        samples = [c for d in np.ndindex(2, 2, 2) for c in by_pos.get(tuple(j[i] + d[i] for i in range(3)), [])]
+        k = len(samples)
+        multi += k > 1
+        s = np.sum(samples, axis=0)
+        got = [(int(rgba) >> sh) & 255 for sh in (0, 8, 16)]
+        for ch in range(3):
+            up = (2 * int(s[ch]) + k) // (2 * k)  # s / k rounded half up
+            ok = {up, up - 1} if k > 1 and (2 * int(s[ch])) % (2 * k) == k else {up}
+            assert got[ch] in ok, (j, ch, got[ch], s[ch], k)
+        assert int(rgba) >> 24 == 255 and int(pick) == NONE
+        assert int(cnt) == len(by_pos[j])
+    return multi
+
+
+@pytest.mark.parametrize("L", [7, 6])
+def test_weighted_on_cell_corners_is_the_mean_of_the_corner_samples(L):
+    """On a cube of edge <= 128 every point sits on a grid-cell corner, at
+    distance sqrt(3)/2 from the centres of the eight cells sharing that
+    corner (and farther than one cell from all others), so every weight is
+    the same and an occupied cell's colour is the plain mean of the samples
+    on its eight corners, rounded half up.  The cell a point lies in is the
+    one whose lowest corner it is."""
+    pts = clustered_corner_cloud(L, seed=40 + L)
+    res = oracle.build(pts, 100, 2, 21)
+    assert res["flags"][0] == 0 and np.all(res["flags"][1:] & 1 == 1)  # root inner, children leaves
+    assert check_corner_means(pts, res, L) > 20  # the cloud does exercise shared corners
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_weighted_cells_and_counts_equal_the_average_modes(seed):
+    """Occupancy and counts do not depend on the colour rule: an inner
+    node's occupied cells are the cells holding its points (a child voxel's
+    centre lies in the parent cell that nests the child cell), so every
+    node's cells and counts equal those of the cell average, over trees
+    several levels deep."""
+    pts = synth.sphere(20_000, seed=seed, radius_log2=11)
+    avg = oracle.build(pts, 300, 0, 21)
+    wtd = oracle.build(pts, 300, 2, 21)
+    assert avg["level"].max() >= 3
+    for k in ("min", "level", "log2_size", "child_mask", "flags", "parent", "first_child",
+              "point_offset", "point_count", "voxel_count"):
+        assert np.array_equal(avg[k], wtd[k]), k
+    for i in np.nonzero((avg["flags"] & 1) == 0)[0]:
+        a, b = int(avg["voxel_offset"][i]), int(wtd["voxel_offset"][i])
+        c = int(avg["voxel_count"][i])
+        assert np.array_equal(avg["voxels"][a:a + c][:, [0, 2]], wtd["voxels"][b:b + c][:, [0, 2]])
+
+
+def test_weighted_constant_colour_and_bounds():
+    """A weighted mean of one colour is that colour at every level; with
+    random colours every voxel channel stays within the input's range."""
+    pts = synth.sphere(8_000, seed=9, radius_log2=9)
+    const = pts.copy()
+    const[:, 3] = synth.pack_rgba(np.full(len(pts), 17), np.full(len(pts), 200), np.full(len(pts), 93))
+    res = oracle.build(const, 150, 2, 21)
+    assert len(res["voxels"]) > 0 and np.all(res["voxels"][:, 1] == np.uint32(const[0, 3].view(np.uint32)))
+    res = oracle.build(pts, 150, 2, 21)
+    u = pts[:, 3].view(np.uint32)
+    for sh in (0, 8, 16):
+        ch = (res["voxels"][:, 1] >> sh) & 255
+        src = (u >> sh) & 255
+        assert ch.min() >= src.min() and ch.max() <= src.max()
+    assert np.all(res["voxels"][:, 3] == NONE)
+
+
+def test_weighted_check_catches_planted_mistakes():
+    """The corner rule rejects plausible mistakes, planted in copies of a
+    correct result: a colour off by one in a cell with several samples, a
+    wrong count, a cell moved by one."""
+    pts = clustered_corner_cloud(7, seed=47)
+    res = oracle.build(pts, 100, 2, 21)
+    a, n = int(res["voxel_offset"][0]), int(res["voxel_count"][0])
+    g = pts[:, :3].astype(np.int64) - res["min"][0]  # edge 128: grid position = offset
+    shared = []
+    for r in range(a, a + n):
+        c = int(res["voxels"][r, 0])
+        j = np.array([c & 127, (c >> 7) & 127, c >> 14])
+        if np.sum(np.all((g - j >= 0) & (g - j <= 1), axis=1)) > 1:
+            shared.append(r)
+    assert shared
+    r = shared[0]
+    for mutate in (lambda v: v.__setitem__((r, 1), v[r, 1] ^ 1), lambda v: v.__setitem__((r, 2), v[r, 2] + 1),
+                   lambda v: v.__setitem__((r, 0), v[r, 0] ^ 1)):
+        bad = dict(res)
+        bad["voxels"] = np.array(res["voxels"], copy=True)
+        mutate(bad["voxels"])
+        with pytest.raises(AssertionError):
+            check_corner_means(pts, bad, 7)
