@@ -245,9 +245,10 @@ class Result:
         return int(lib().lod_result_device_bytes(self._h))
 
     def tensors(self):
-        """Zero-copy torch views: nodes (n,14) int32, points (N,4) int32,
-        index (N,) int32 or None, voxels (V_buffer, 4) int32 — valid while
-        this Result is alive."""
+        """Zero-copy torch views: nodes (n,14) int32 (the 56-byte node
+        records), points (N,4) int32, index (N,) int32 or None — valid while
+        this Result is alive.  Voxels: ``view().voxels`` is the device base
+        that the nodes' voxel_offset indexes; ``to_host()`` gathers them."""
         import torch
         v = self.view()
         out = {}
