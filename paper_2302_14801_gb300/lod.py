@@ -326,11 +326,15 @@ def build_from_host(points, leaf_threshold=50000, mode=FILTER, max_depth=21, kee
                     stream=None) -> Result:
     """lod_build_from_host on host memory: a numpy array or a (pinned) CPU tensor."""
     if isinstance(points, np.ndarray):
-        arr = np.ascontiguousarray(points, dtype=np.int32).reshape(-1, 4)
+        if points.ndim != 2 or points.shape[1] != 4:
+            raise TypeError("host points must have shape (N, 4)")
+        arr = np.ascontiguousarray(points, dtype=np.int32)
         ptr, n, keep = arr.ctypes.data, arr.shape[0], arr
     else:
-        if points.is_cuda or points.dtype.__str__() != "torch.int32" or not points.is_contiguous():
-            raise TypeError("host points must be a contiguous int32 CPU tensor")
+        import torch
+        if not isinstance(points, torch.Tensor) or points.is_cuda or points.dtype != torch.int32 \
+                or points.dim() != 2 or points.shape[1] != 4 or not points.is_contiguous():
+            raise TypeError("host points must be a numpy array or a contiguous int32 CPU tensor of shape (N, 4)")
         ptr, n, keep = points.data_ptr(), points.shape[0], points
     p = make_params(leaf_threshold, mode, max_depth, keep_index)
     h = ctypes.c_void_p()

@@ -63,3 +63,18 @@ def test_invalid_arguments_rejected_on_host(lodmod):
     L.lod_free(None)  # no-op
     cfg = lodmod.ServerConfig(0, 1, 0)
     assert L.lod_server_create(ctypes.byref(cfg), ctypes.byref(h)) == lodmod.LOD_ERR_INVALID_ARG
+
+
+def test_binding_rejects_malformed_point_arrays(lodmod):
+    # the binding checks shapes and types before any call into the library
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    for bad in (np.zeros((4, 3), np.int32), np.zeros(16, np.int32), torch.zeros((4, 3), dtype=torch.int32),
+                torch.zeros((4, 4), dtype=torch.int64), [[0, 0, 0, 0]]):
+        with pytest.raises(TypeError):
+            lodmod.build_from_host(bad)
+    for bad in (np.zeros((4, 4), np.int32), torch.zeros((4, 4), dtype=torch.int32)):
+        with pytest.raises(TypeError):  # lod_build wants device memory
+            lodmod.build(bad)
+    with pytest.raises(TypeError):
+        lodmod.build_batched([np.zeros((4, 4), np.int32)])
