@@ -63,6 +63,37 @@ def test_invalid_arguments_rejected_on_host(lodmod):
     L.lod_free(None)  # no-op
     cfg = lodmod.ServerConfig(0, 1, 0)
     assert L.lod_server_create(ctypes.byref(cfg), ctypes.byref(h)) == lodmod.LOD_ERR_INVALID_ARG
+    # checked before any device work: alignment, point count, parameters
+    dev = ctypes.c_void_p(1 << 20)  # never dereferenced: every call below fails its checks first
+    odd = ctypes.c_void_p((1 << 20) + 8)
+    assert L.lod_build(odd, 1, ctypes.byref(p), None, ctypes.byref(h)) == lodmod.LOD_ERR_INVALID_ARG
+    assert L.lod_build(dev, 1 << 32, ctypes.byref(p), None, ctypes.byref(h)) == lodmod.LOD_ERR_INVALID_ARG
+    for bad in (lodmod.make_params(mode=2), lodmod.make_params(max_depth=33), lodmod.make_params(leaf_threshold=0)):
+        assert L.lod_build(dev, 1, ctypes.byref(bad), None, ctypes.byref(h)) == lodmod.LOD_ERR_INVALID_ARG
+    tiles = (ctypes.c_void_p * 2)(dev, odd)
+    ns = (ctypes.c_uint64 * 2)(5, 5)
+    outs = (ctypes.c_void_p * 2)()
+    assert L.lod_build_batched(tiles, ns, 2, ctypes.byref(p), None, outs) == lodmod.LOD_ERR_INVALID_ARG
+    assert L.lod_root_cubes_noalloc(tiles, ns, 2, dev, None) == lodmod.LOD_ERR_INVALID_ARG  # tile 1 misaligned
+    assert L.lod_root_cubes_noalloc(tiles, ns, 0, dev, None) == lodmod.LOD_ERR_INVALID_ARG
+    assert L.lod_root_cubes_noalloc(tiles, ns, 1, ctypes.c_void_p((1 << 20) + 2), None) == lodmod.LOD_ERR_INVALID_ARG
+    assert L.lod_autotune(None, 10, None, None, None, None) == lodmod.LOD_ERR_INVALID_ARG
+    assert L.lod_profile_read(None, 0, None) == lodmod.LOD_ERR_INVALID_ARG
+
+
+def test_tuning_is_checked_and_restorable(lodmod):
+    L = lodmod.lib()
+    before = lodmod.get_tuning()
+    for bad in ((9, 0), (0, 9)):
+        assert L.lod_set_tuning(ctypes.byref(lodmod.Tuning(*bad))) == lodmod.LOD_ERR_INVALID_ARG
+    assert lodmod.get_tuning() == before  # a rejected setting changes nothing
+    try:
+        lodmod.set_tuning(root_depth=5, stream_ctas_per_sm=3)
+        assert lodmod.get_tuning() == {"root_depth": 5, "stream_ctas_per_sm": 3}
+    finally:
+        lodmod.set_tuning(**before)
+    assert lodmod.get_tuning() == before
+    assert L.lod_get_tuning(None) == lodmod.LOD_ERR_INVALID_ARG
 
 
 def test_binding_rejects_malformed_point_arrays(lodmod):
