@@ -167,7 +167,8 @@ def cpu_oracle_sample(pts: np.ndarray, T: int, budget_s: float = 12.0, seed: int
             break
         frac = min(1.0, frac * 4)
     n, dt, frac = best
-    return {"value": 2.0 * n / dt / 1e6, "unit": "M points/s", "cores": 1, "kind": "oracle",
+    return {"value": 2.0 * n / dt / 1e6, "unit": "M points/s", "cores": 1, "host_cores": os.cpu_count(),
+            "kind": "oracle",
             "sample": f"{n} points in an x-y window covering {frac * 100:.3g}% of the cloud's area; "
                       f"one filtered + one pick build, single-threaded, {dt:.2f} s"}
 
@@ -228,7 +229,8 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "int32/u64", "data": "synthetic",
         "config": {"workload": f"{name}: {n} points, T={T}, 128^3 grid, filtered + pick; "
                                f"oracle on a {ns}-point x-y window sample ({frac * 100:.3g}% of the area)"},
-        "cpu_baseline": {"value": value, "unit": "M points/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "M points/s", "cores": 1, "host_cores": os.cpu_count(),
+                         "kind": "oracle",
                          "sample": f"{ns} points (x-y window, {frac * 100:.3g}% of the area) per step"},
         "e2e": {"value": value, "unit": "M points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }

@@ -30,6 +30,7 @@ def test_reference_arm_prints_one_contract_line():
     assert d["impl"] == "reference" and d["higher_is_better"] is True and d["unit"] == "M points/s"
     assert d["steps"] == 2 and d["warmup"] == 3 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] == 1 and d["cpu_baseline"]["host_cores"] >= 1
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
     assert "workload" in d["config"]
 
