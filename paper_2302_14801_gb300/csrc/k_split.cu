@@ -28,18 +28,19 @@ namespace {
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
-// Morton cell of point p inside a source grid (8^d cells under a cube of
-// edge 2^log2size with min corner mn).
-// Morton index of a grid cell: within every bit triple x is the most
-// significant, so the low triple is the octant index k = 4*bx + 2*by + bz.
-// Grids have d <= 8, so each coordinate has at most 8 bits and the shift
-// log2size - d is at most 31.
+// Spread the low 8 bits of v to every third bit (bit i to bit 3i).
 __device__ __forceinline__ uint32_t spread3_8(uint32_t v) {
   v = (v | (v << 8)) & 0x0000F00Fu;
   v = (v | (v << 4)) & 0x000C30C3u;
   v = (v | (v << 2)) & 0x00249249u;
   return v;
 }
+
+// Morton cell of point p inside a source grid (8^d cells under a cube of
+// edge 2^log2size with min corner (mx, my, mz)): within every bit triple x
+// is the most significant, so the low triple is the octant index
+// k = 4*bx + 2*by + bz.  Grids have d <= 8, so each coordinate has at most
+// 8 bits and the shift log2size - d is at most 31.
 __device__ __forceinline__ uint32_t src_bin(const int4& p, int32_t mx, int32_t my, int32_t mz, uint32_t log2size,
                                             uint32_t d) {
   if (d == 0) return 0;
