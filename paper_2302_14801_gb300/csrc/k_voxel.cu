@@ -5,7 +5,7 @@
 // CTA handles one (parent, child octant) pair: the child's samples (its
 // leaf points, or the voxels the child itself received one level below)
 // all fall into one 64^3 octant of the parent's 128^3 grid (the observation
-// of Section 4.2), and their cells are accumulated in a ~200 KB
+// of Section 4.2), and their cells are accumulated in a 224 KB
 // shared-memory open-addressing hash table instead of a dense grid.  An
 // octant whose occupied cells exceed the table is processed in several
 // hash-partitioned passes.  Colour sums are exact integers (32-bit lanes
