@@ -24,6 +24,7 @@ _lib = None
 FILTER = 0
 PICK = 1
 WEIGHTED = 2  # neighbourhood-weighted average (Section 4.2.4); oracle only so far
+FIRST = 3     # first come in input order (Section 4.2.1); oracle only so far
 
 
 def compile_oracle(force: bool = False) -> str:
@@ -82,8 +83,9 @@ def build(points: np.ndarray, leaf_threshold: int = 50000, mode: int = FILTER,
           max_depth: int = 21) -> dict:
     """Run the oracle on an (N, 4) int32 point array; return numpy arrays.
 
-    ``mode``: FILTER (cell average), PICK (minimal-hash sample) or WEIGHTED
-    (neighbourhood-weighted average, computed bottom-up as the paper does).
+    ``mode``: FILTER (cell average), PICK (minimal-hash sample), WEIGHTED
+    (neighbourhood-weighted average, computed bottom-up as the paper does)
+    or FIRST (the cell's first point in input order).
 
     Keys: ``min`` (n,3) int32, ``level``, ``log2_size``, ``child_mask``,
     ``flags`` (uint8), ``parent``, ``first_child`` (uint32),

@@ -30,7 +30,9 @@
 //    of a 128^3 grid over its cube.  Cell-wise average (Section 4.2.3) with
 //    exact u64 sums over all original points of the cube and a rounded-half-
 //    up integer mean, alpha 255; sample pick (replacing the random pick of
-//    Section 4.2.2, Listing 1) keeps the point of minimal splitmix64(index).
+//    Section 4.2.2, Listing 1) keeps the point of minimal splitmix64(index);
+//    first come (Section 4.2.1; mode 3) keeps the first point of the cell in
+//    input order.
 //  * Neighbourhood-weighted average (Section 4.2.4; mode 2) follows the
 //    paper's own order instead, since its result depends on it: inner nodes
 //    deepest level first, each sampling its children's samples (the points
@@ -79,6 +81,7 @@ struct OVoxel {
 
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint32_t kModeWeighted = 2u;
+constexpr uint32_t kModeFirst = 3u;
 constexpr uint32_t kLeaf = 1u;
 constexpr uint32_t kOverfull = 2u;
 
@@ -157,10 +160,14 @@ struct Builder {
       } else {
         // Sample pick: the one point of the cell whose splitmix64(index) is
         // smallest (splitmix64 is a bijection, so the minimum is unique).
+        // First come (Section 4.2.1, mode 3): the first sample of the cell
+        // in input order, i.e. the smallest input index; a child voxel
+        // carries its own first point, so bottom up gives the same point.
+        auto key = [&](uint32_t i) -> uint64_t { return mode == kModeFirst ? in_index(i) : splitmix64(in_index(i)); };
         uint32_t best = keyed[a].second;
-        uint64_t best_h = splitmix64(in_index(best));
+        uint64_t best_h = key(best);
         for (size_t j = a + 1; j < b; ++j) {
-          uint64_t h = splitmix64(in_index(keyed[j].second));
+          uint64_t h = key(keyed[j].second);
           if (h < best_h) {
             best_h = h;
             best = keyed[j].second;
@@ -386,11 +393,11 @@ struct oracle_result {
 extern "C" {
 
 // mode 0: cell-wise average, 1: sample pick, 2: neighbourhood-weighted
-// average.  Returns 0 on success, 1 on invalid arguments, 2 on allocation
-// failure.
+// average, 3: first come.  Returns 0 on success, 1 on invalid arguments, 2
+// on allocation failure.
 int oracle_build(const void* points, uint64_t n, uint32_t leaf_threshold, uint32_t mode,
                  uint32_t max_depth, oracle_result** out) {
-  if (!out || (n > 0 && !points) || leaf_threshold == 0 || mode > kModeWeighted || max_depth > 32 ||
+  if (!out || (n > 0 && !points) || leaf_threshold == 0 || mode > kModeFirst || max_depth > 32 ||
       n > 0xFFFFFFFFull)
     return 1;
   oracle_result* r = new (std::nothrow) oracle_result();
@@ -467,7 +474,10 @@ void oracle_free(oracle_result* r) { delete r; }
 // (a point outside the cube, log2_size > 32).
 int64_t oracle_cube_voxels(const void* points, const uint32_t* index, uint64_t n, const int32_t* min3,
                            uint32_t log2_size, uint32_t mode, uint32_t* out4) {
-  if ((n > 0 && (!points || !index || !out4)) || !min3 || log2_size > 32 || mode > 1) return -1;
+  // the weighted average depends on the children's voxels: not defined per cube
+  if ((n > 0 && (!points || !index || !out4)) || !min3 || log2_size > 32 || mode == kModeWeighted ||
+      mode > kModeFirst)
+    return -1;
   const OPoint* p = static_cast<const OPoint*>(points);
   for (uint64_t i = 0; i < n; ++i) {
     const int64_t d[3] = {rel(p[i].x, min3[0]), rel(p[i].y, min3[1]), rel(p[i].z, min3[2])};

@@ -13,8 +13,9 @@ oracle's dictionary layout) against the definitions:
 * leaves tile the points: each leaf's range holds exactly the points of its
   cube; ranges follow depth-first (ascending Morton key of the min corner);
 * every inner node's voxels are exactly the occupied 128^3 cells, with the
-  exact count, the rounded-half-up mean colour (filtered) or the member of
-  minimal splitmix64(index) (pick).
+  exact count, the rounded-half-up mean colour (filtered), the member of
+  minimal splitmix64(index) (pick) or the first member in input order
+  (first come).
 """
 from __future__ import annotations
 
@@ -160,6 +161,9 @@ def check(points: np.ndarray, res: dict, T: int, mode: int, max_depth: int) -> N
                     ch.append((2 * tot + cnt) // (2 * cnt))
                 want_rgba = ch[0] | (ch[1] << 8) | (ch[2] << 16) | (255 << 24)
                 assert r[1] == want_rgba and r[3] == NONE
+            elif mode == 3:
+                best = min(members)  # first come: the first member in input order
+                assert r[3] == best and r[1] == int(rgba[best])
             else:
                 best = min(members, key=splitmix64_py)
                 assert r[3] == best and r[1] == int(rgba[best])

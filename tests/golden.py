@@ -3,7 +3,8 @@ result against them.
 
 Each fixture holds a tiny input, the leaf threshold and depth cap, the
 sampling modes it covers (filtered, pick, and the neighbourhood-weighted
-average of Section 4.2.4, which only the oracle computes so far), and the
+average of Section 4.2.4 and first come of Section 4.2.1, which only the
+oracle computes so far), and the
 whole expected result worked out by hand from the method's definitions
 (every file's header shows the derivation and cites the sections and
 readings it follows).  The expected values come from neither the oracle
@@ -17,7 +18,7 @@ import numpy as np
 
 HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 NONE = 0xFFFFFFFF
-MODES = {"filtered": 0, "pick": 1, "weighted": 2}
+MODES = {"filtered": 0, "pick": 1, "weighted": 2, "first": 3}
 
 
 def pack(r, g, b, a):
@@ -29,7 +30,7 @@ def u32(v):
 
 
 def load(path):
-    fx = {"points": [], "nodes": [], "leaves": {}, "voxels": {0: {}, 1: {}, 2: {}}, "name": os.path.basename(path)}
+    fx = {"points": [], "nodes": [], "leaves": {}, "voxels": {0: {}, 1: {}, 2: {}, 3: {}}, "name": os.path.basename(path)}
     for line in open(path):
         line = line.split("#", 1)[0].strip()
         if not line:
@@ -65,7 +66,7 @@ def fixtures():
     return sorted(glob.glob(os.path.join(HERE, "*.txt")))
 
 
-def cases(modes=(0, 1, 2)):
+def cases(modes=(0, 1, 2, 3)):
     """(path, mode) for every fixture and every stated mode among ``modes``."""
     return [(p, m) for p in fixtures() for m in load(p)["modes"] if m in modes]
 

@@ -12,6 +12,8 @@ definitions and by mathematics, not by the oracle itself.
 * Cross-mode identities: identical cells and counts in both modes.
 * Hand-worked examples under tests/golden/ (whole results in every mode
   each file states, each derivation written out in its file).
+* First come (Section 4.2.1, oracle mode 3): the brute-force checker takes
+  every cell's first point in input order.
 * Neighbourhood-weighted average (Section 4.2.4, oracle mode 2): the mean
   of the corner samples on cubes of edge <= 128 (equal weights), cells and
   counts equal to the average mode's, constant colours exact, channels
@@ -232,14 +234,14 @@ def test_bruteforce_random_tiny(seed):
     T = int(rng.integers(1, 17))
     max_depth = int(rng.choice([21, 3, 1, 6]))
     pts = _random_cloud(rng, n, int(rng.integers(1, 24)))
-    for mode in (0, 1):
+    for mode in (0, 1, 3):
         r = oracle.build(pts, T, mode, max_depth)
         check(pts, r, T, mode, max_depth)
 
 
 def test_bruteforce_sphere_small():
     pts = synth.sphere(1500, seed=5)
-    for mode in (0, 1):
+    for mode in (0, 1, 3):
         r = oracle.build(pts, 16, mode)
         check(pts, r, 16, mode, 21)
 
@@ -308,7 +310,7 @@ def test_rejects_bad_arguments():
     with pytest.raises(ValueError):
         oracle.build(pts, 0, 0)
     with pytest.raises(ValueError):
-        oracle.build(pts, 10, 3)  # modes: 0 average, 1 pick, 2 weighted
+        oracle.build(pts, 10, 4)  # modes: 0 average, 1 pick, 2 weighted, 3 first come
     with pytest.raises(ValueError):
         oracle.build(pts, 10, 0, 33)
 
@@ -338,10 +340,11 @@ def test_bruteforce_checker_catches_planted_mistakes():
             check(pts, mutated(fn), 12, 0, 21)
 
 
-def test_bruteforce_pick_catches_wrong_argmin():
+@pytest.mark.parametrize("mode", [1, 3])
+def test_bruteforce_pick_catches_wrong_argmin(mode):
     pts = synth.sphere(600, seed=12)
-    good = oracle.build(pts, 10, 1)
-    check(pts, good, 10, 1, 21)
+    good = oracle.build(pts, 10, mode)
+    check(pts, good, 10, mode, 21)
     bad = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in good.items()}
     # find a voxel with >= 2 members and replace the pick by another member
     v = bad["voxels"]
@@ -358,7 +361,7 @@ def test_bruteforce_pick_catches_wrong_argmin():
     v[i, 3] = other
     v[i, 1] = int(pts[other, 3]) & 0xFFFFFFFF
     with pytest.raises(AssertionError):
-        check(pts, bad, 10, 1, 21)
+        check(pts, bad, 10, mode, 21)
     assert splitmix64_py(0) == 0xE220A8397B1DCDAF
 
 
