@@ -172,7 +172,10 @@ int lod_build_from_host(const lod_point_t* h_points, uint64_t n, const lod_param
                         void* stream, lod_result_t** out);
 
 /* Build n_tiles independent octrees in one batched pass: every stage runs
- * as one launch over the work of all tiles (one device work list).
+ * as one launch over the work of all tiles (one device work list).  No
+ * passage of the paper defines this call (the paper builds one cloud at a
+ * time); it serves workloads of many independent scan tiles, and each
+ * tile's octree is the one Sections 4.1 and 4.2 define for that tile.
  *   d_tiles   host array of n_tiles device pointers (each 16-byte aligned).
  *   n         host array of n_tiles point counts (each < 2^32).
  *   out       host array of n_tiles result pointers, filled on LOD_OK.
@@ -237,11 +240,13 @@ int lod_trim(void* stream);
  *            extent) — the root node lod_build produces; an empty tile
  *            gives 0, 0, 0, 0.
  *   stream   cudaStream_t as void*; the call is asynchronous on it.
- * Scratch: a 160 KB array in static device memory, one per device that
+ * Scratch: a 192 KB array in static device memory, one per device that
  * loads the library, held until the process exits.  The first call on a
- * device looks up that array's device address; make that first call before
- * any stream capture.  All calls share the array, so calls whose work
- * overlaps on the GPU race with one another: issue them on one stream. */
+ * device looks up that array's device address and keeps it; make that
+ * first call before any stream capture, and do not use the call after
+ * cudaDeviceReset in the same process.  All calls share the array, so
+ * calls whose work overlaps on the GPU race with one another: issue them
+ * on one stream. */
 int lod_root_cubes_noalloc(const lod_point_t* const* d_tiles, const uint64_t* n, uint32_t n_tiles,
                            int32_t* d_cubes, void* stream);
 
@@ -321,14 +326,19 @@ typedef struct lod_server lod_server_t;
 
 int lod_server_create(const lod_server_config_t* cfg, lod_server_t** out);
 
-/* Enqueue a build of n device points (kept valid by the caller until the
+/* No passage of the paper defines the serving calls below (lod_submit,
+ * lod_poll, lod_wait); they add request admission around lod_build, whose
+ * result each request receives unchanged.
+ *
+ * Enqueue a build of n device points (kept valid by the caller until the
  * result is returned).  *ticket identifies the request.  Returns
  * LOD_ERR_BUDGET if the request alone exceeds the budget. */
 int lod_submit(lod_server_t* s, const lod_point_t* d_points, uint64_t n, const lod_params_t* params,
                uint64_t* ticket);
 
-/* Non-blocking: LOD_OK and *out set when the request has finished (the
- * ticket is then consumed), LOD_NOT_READY otherwise, or the build's error. */
+/* Non-blocking (no paper counterpart, see lod_submit): LOD_OK and *out set
+ * when the request has finished (the ticket is then consumed),
+ * LOD_NOT_READY otherwise, or the build's error. */
 int lod_poll(lod_server_t* s, uint64_t ticket, lod_result_t** out);
 
 /* Blocking variant of lod_poll with a timeout in milliseconds. */

@@ -3,10 +3,13 @@
 // The device work of all tiles of a batch runs in the same launches: one
 // bounding-box pass, then counting rounds (first grid per tile, then the
 // refinement grids of overflowing cells), the node tables (one CTA per
-// tile), and the bottom-up voxel levels.  The host only reads back small
-// counters between phases to size the next allocations: once after the
-// bounding box, once per counting round, once after the node tables and
-// once per voxel level.
+// tile), and the bottom-up voxel levels.  The host reads back small
+// counters between phases to size the next allocations: once per counting
+// round (the root cubes are set on the device, so the bounding box needs no
+// read-back unless a cube is too small for the first grid's depth), once
+// more when refinement rounds make the node table follow them, and once
+// after all voxel levels, which are enqueued together with no read-back
+// between them.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -117,6 +120,17 @@ struct WsLease {
   }
 };
 
+// Allocation-failure injection for tests of the error paths, on the host
+// side (the failing allocation is never requested from CUDA, so no device
+// state is involved): with LOD_INJECT_OOM_AT=k in the environment, the k-th
+// device allocation of every build on this thread fails as out of memory.
+thread_local int64_t tl_oom_countdown = -1;
+
+void arm_oom_injection() {
+  const char* e = std::getenv("LOD_INJECT_OOM_AT");
+  tl_oom_countdown = (e && *e) ? std::atoll(e) : -1;
+}
+
 // Stream-ordered device buffer released on destruction; from the build's
 // workspace when it has one (scratch), else from the stream-ordered pool
 // (results, which outlive the build).
@@ -131,6 +145,7 @@ struct DevBuf {
   ~DevBuf() { release(); }
   cudaError_t alloc(size_t b) {
     release();
+    if (tl_oom_countdown > 0 && --tl_oom_countdown == 0) return cudaErrorMemoryAllocation;
     if (b == 0) b = 16;
     if (ws) {
       const int k = ws->take(b);
@@ -604,6 +619,7 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
                           BuildStats* stats, bool use_workspace, bool sync_roots) {
   BuildStats S;
   PhaseClock clk;
+  arm_oom_injection();
   WsLease lease(st, use_workspace);  // declared first: outlives every scratch buffer
   Workspace* const ws = lease.ws;
   if (nt == 0 || !tin) return LOD_ERR_INVALID_ARG;

@@ -15,7 +15,7 @@ KEYS = ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_
 def run(env_extra, *args):
     env = dict(os.environ, **env_extra)
     cmd = [sys.executable, "bench.py", "--impl", "reference", "--workload", "sphere1m", "--steps", "2",
-           "--warmup", "3", "--ref-fraction", "0.25", *args]
+           "--warmup", "3", *args]
     return subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
 
 
@@ -39,6 +39,27 @@ def test_reference_arm_other_ranks_exit_quietly():
     p = run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert p.returncode == 0, p.stderr[-2000:]
     assert not [l for l in p.stdout.splitlines() if l.strip().startswith("{")]
+
+
+def test_oracle_sample_is_one_definition():
+    # the cpu_baseline leg and the reference arm time the oracle on the
+    # same sample: the smallest lower-corner x-y window (1/4096, 1/1024, ...
+    # of the area) that holds at least the requested number of points
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    rng = np.random.default_rng(3)
+    pts = np.zeros((200_000, 4), np.int32)
+    pts[:, :3] = rng.integers(0, 1 << 20, size=(200_000, 3))
+    s, frac = bench.oracle_sample(pts, min_points=5_000)
+    assert frac == 1.0 / 16 and len(s) >= 5_000
+    side = int(np.floor(np.sqrt(frac) * ((1 << 20) - 1 - 0 + 1)))
+    lo = pts[:, :2].min(axis=0)
+    assert np.all((s[:, :2] >= lo) & (s[:, :2] < lo + side))
+    inside = np.all((pts[:, :2] >= lo) & (pts[:, :2] < lo + side), axis=1)
+    assert len(s) == int(inside.sum())
+    s2, frac2 = bench.oracle_sample(pts, min_points=10**9)
+    assert frac2 == 1.0 and len(s2) == len(pts)
 
 
 def test_roofline_object_of_the_dominant_kernel():

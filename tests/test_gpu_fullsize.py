@@ -3,6 +3,8 @@ exactly as bench.py times it (lod.build on the current stream, T = 50k,
 max_depth 21, default tuning), both modes, compared with the oracle over
 the whole result (node table, every leaf's point multiset, indices, every
 voxel), plus the size-independent invariants of the tree."""
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import pytest
 
@@ -67,6 +69,72 @@ def test_aerial_50m_full_parity(lod, aerial, mode):
 
 
 # --------------------------------------------------------------------------
+# Filtered colour sums of items whose cube holds more than 0xFFFFFFFF / 255
+# = 16,843,009 points take 64-bit lanes in the voxel pass (32-bit lanes
+# could overflow there).  17.5M points uniform in a 2^15 cube in one corner
+# of a 2^22 root (a far point sets the extent) put all of them into one
+# cell of the root's grid, whose channel sums exceed 2^32: with max_depth 1
+# the item is an overfull leaf (points read directly), with max_depth 21 a
+# chain of single-child inner nodes (child voxels merged with wide sums).
+
+def wide_cloud():
+    rng = np.random.default_rng(4242)
+    n = 17_500_000
+    pts = np.empty((n + 1, 4), np.int32)
+    pts[:n, :3] = rng.integers(0, 1 << 15, size=(n, 3), dtype=np.int32)
+    r = np.full(n, 255)
+    g = 255 - rng.integers(0, 3, size=n)
+    b = 200 + rng.integers(0, 56, size=n)
+    pts[:n, 3] = synth.pack_rgba(r, g, b)
+    pts[n] = (1 << 21, 1 << 21, 1 << 21, int(synth.pack_rgba(np.array([1]), np.array([2]), np.array([3]))[0]))
+    return pts
+
+
+@pytest.mark.parametrize("max_depth", [1, 21])
+def test_filtered_wide_sums_against_oracle(lod, max_depth):
+    import torch
+    pts = wide_cloud()
+    with ThreadPoolExecutor(1) as ex:
+        fut = ex.submit(oracle.build, pts, T, 0, max_depth)
+        d = torch.from_numpy(pts).cuda()
+        r = lod.build(d, T, 0, max_depth, stream=torch.cuda.current_stream())
+        got = r.to_host()
+        r.free()
+        want = fut.result()
+    root = want["voxels"][: int(want["voxel_count"][0])]
+    assert int(root[:, 2].max()) == len(pts) - 1  # one root cell holds all corner points
+    compare(got, want, inp=pts)
+
+
+# --------------------------------------------------------------------------
+# A whole-cloud comparison beyond the 50M aerial cloud: 100M points of the
+# indoor recipe (numpy generator), both modes, at the bench's settings.  Its
+# log-normal clusters need refinement rounds and its deep volumetric levels
+# overflow the voxel tables into partitions, the paths the 1B build takes.
+
+@pytest.fixture(scope="module")
+def indoor100m():
+    return synth.indoor(100_000_000, seed=3)
+
+
+def test_indoor_100m_full_parity_both_modes(lod, indoor100m):
+    import torch
+    pts = indoor100m
+    with ThreadPoolExecutor(2) as ex:
+        futs = {mode: ex.submit(oracle.build, pts, T, mode, 21) for mode in (0, 1)}
+        d = torch.from_numpy(pts).cuda()
+        got = {}
+        for mode in (0, 1):
+            r = lod.build(d, T, mode, 21, stream=torch.cuda.current_stream())
+            got[mode] = r.to_host()
+            r.free()
+        del d
+        for mode in (0, 1):
+            invariants(got[mode], len(pts))
+            compare(got[mode], futs[mode].result(), inp=pts)
+
+
+# --------------------------------------------------------------------------
 # The billion-point indoor scan (drawn on the device with the same recipe as
 # synth.indoor), built exactly as the bench times it.  The whole-cloud oracle
 # would take tens of minutes, so every node is checked against the tree's
@@ -96,6 +164,23 @@ def cube_points(dev_pts, mn, lg):
 def sorted_rows(a):
     a = np.asarray(a)
     return a[np.lexsort(a.T[::-1])]
+
+
+def check_cube_nodes(got, dev_pts, mode, nodes):
+    """Inner nodes of a large build against the single-cube oracle, several
+    at a time (the oracle releases the GIL)."""
+    vox = got["voxels"].reshape(-1, 4)
+    jobs = []
+    with ThreadPoolExecutor(4) as ex:
+        for i in nodes:
+            pts, idx = cube_points(dev_pts, got["min"][i], got["log2_size"][i])
+            assert len(pts) == int(got["point_count"][i])
+            jobs.append((i, ex.submit(oracle.cube_voxels, pts, idx, got["min"][i], got["log2_size"][i], mode)))
+        for i, f in jobs:
+            a, c = int(got["voxel_offset"][i]), int(got["voxel_count"][i])
+            have = vox[a:a + c]
+            have = have[np.argsort(have[:, 0], kind="stable")]
+            assert np.array_equal(have, f.result()), f"node {i}"
 
 
 def check_sampled_nodes(got, dev_pts, mode, rng, n_inner=6, n_leaf=6, max_pts=3_000_000):
@@ -130,14 +215,21 @@ def test_indoor_1b_invariants_and_sampled_nodes(lod, indoor1b, mode):
     r.free()
     invariants(got, N1B)
     check_sampled_nodes(got, indoor1b, mode, np.random.default_rng(77 + mode))
+    # two level-1 nodes (each over 16.8M points: the filtered pass sums them
+    # in 64-bit lanes): the smallest inner one and the largest
+    lvl1 = np.nonzero((got["level"] == 1) & ((got["flags"] & 1) == 0))[0]
+    cnt = got["point_count"][lvl1].astype(np.int64)
+    pick = sorted({int(lvl1[np.argmin(cnt)]), int(lvl1[np.argmax(cnt)])})
+    assert got["point_count"][pick].max() > 16_843_009
+    check_cube_nodes(got, indoor1b, mode, pick)
 
 
 # --------------------------------------------------------------------------
 # Batched tiles as the bench builds them: the first wave (<= 1e9 points) of
 # 2048 tiles with sizes log-uniform in [1e4, 2e7], each a sphere with its own
-# seed and bbox, one lod_build_batched call, filtered mode.  Tiles up to a
-# few million points are compared with the whole-cloud oracle, every tile
-# with the invariants.
+# seed and bbox, one lod_build_batched call, filtered mode.  Every tile of at
+# most 3M points is compared with the whole-cloud oracle, every tile with
+# the invariants.
 
 def test_batched_first_wave_of_2048_tiles(lod):
     import torch
@@ -154,15 +246,20 @@ def test_batched_first_wave_of_2048_tiles(lod):
         off = np.random.default_rng((1000 + t) ^ 0x5EED).integers(0, (1 << 30) - (1 << 21), size=3)
         tiles.append(synth_gpu.sphere(int(sizes[t]), seed=1000 + t, offset=tuple(int(o) for o in off)))
     rs = lod.build_batched(tiles, T, 0, stream=torch.cuda.current_stream())
-    small = [k for k in range(len(wave)) if sizes[wave[k]] <= 3_000_000]
-    check = set(small[:: max(1, len(small) // 4)][:4])
-    for k, r in enumerate(rs):
-        got = r.to_host()
-        r.free()
-        invariants(got, int(sizes[wave[k]]))
-        if k in check:
+    check = [k for k in range(len(wave)) if sizes[wave[k]] <= 3_000_000]
+    assert len(check) > 100
+    with ThreadPoolExecutor(8) as ex:
+        futs = {}
+        for k in check:
             pts = tiles[k].cpu().numpy()
-            compare(got, oracle.build(pts, T, 0, 21), inp=pts)
+            futs[k] = (pts, ex.submit(oracle.build, pts, T, 0, 21))
+        for k, r in enumerate(rs):
+            got = r.to_host()
+            r.free()
+            invariants(got, int(sizes[wave[k]]))
+            if k in futs:
+                pts, f = futs.pop(k)
+                compare(got, f.result(), inp=pts)
 
 
 # --------------------------------------------------------------------------

@@ -297,3 +297,79 @@ def test_hand_worked_examples(lod, mode):
         fx = golden.load(path)
         got = gpu_build(lod, fx["input"], fx["T"], m, fx["max_depth"])
         golden.check(got, fx, m)
+
+
+# ------------------------------------------------------------ failure paths
+
+def _pool_used_bytes():
+    """Bytes in use in the current device's default stream-ordered pool (the
+    pool the library's results and pool buffers come from), read through the
+    CUDA runtime the library is linked against."""
+    import ctypes
+
+    import torch
+    try:
+        rt = ctypes.CDLL("libcudart.so.13")
+    except OSError:
+        pytest.skip("CUDA runtime library not found by name")
+    pool = ctypes.c_void_p()
+    assert rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), torch.cuda.current_device()) == 0
+    val = ctypes.c_uint64()
+    used_mem_current = 7  # cudaMemPoolAttrUsedMemCurrent
+    assert rt.cudaMemPoolGetAttribute(pool, used_mem_current, ctypes.byref(val)) == 0
+    return val.value
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_injected_allocation_failure_fails_cleanly(lod, mode, monkeypatch):
+    # the k-th device allocation of a build fails (on the host side, never
+    # asked of CUDA): the build returns LOD_ERR_OOM, holds no pool memory
+    # afterwards, and the next build is correct
+    import torch
+    pts = synth.indoor(400_000, seed=41, n_prims=64)
+    d = torch.from_numpy(pts).cuda()
+    st = torch.cuda.current_stream()
+    r = lod.build(d, 3000, mode, stream=st)  # warm: workspace and pool set up
+    r.free()
+    torch.cuda.synchronize()
+    base = _pool_used_bytes()
+    failed = 0
+    for k in range(1, 400):
+        monkeypatch.setenv("LOD_INJECT_OOM_AT", str(k))
+        try:
+            r = lod.build(d, 3000, mode, stream=st)
+        except lod.LodError as e:
+            assert e.status == lod.LOD_ERR_OOM, e
+            failed += 1
+            torch.cuda.synchronize()
+            assert _pool_used_bytes() == base, f"pool memory held after failing allocation {k}"
+            continue
+        r.free()
+        break
+    else:
+        raise AssertionError("every injected failure point failed the build")
+    assert failed >= 10
+    monkeypatch.delenv("LOD_INJECT_OOM_AT")
+    torch.cuda.synchronize()
+    assert _pool_used_bytes() == base
+    compare(gpu_build(lod, pts, 3000, mode), oracle.build(pts, 3000, mode, 21), inp=pts)
+
+
+def test_wait_times_out_and_the_request_still_completes(lod):
+    import torch
+    big = torch.from_numpy(synth.aerial(20_000_000, seed=42, n_buildings=200)).cuda()
+    small_np = synth.sphere(500_000, seed=43)
+    small = torch.from_numpy(small_np).cuda()
+    torch.cuda.synchronize()
+    srv = lod.Server(hbm_budget_bytes=64 << 30, max_inflight=1)
+    try:
+        t_big = srv.submit(big, 50000, 0)
+        t_small = srv.submit(small, 20000, 1)  # queued behind the big build (one slot)
+        with pytest.raises(lod.LodError) as e:
+            srv.wait(t_small, timeout_ms=0)
+        assert e.value.status == lod.LOD_ERR_TIMEOUT
+        got = srv.wait(t_small).to_host()  # the ticket is still valid and completes
+        srv.wait(t_big).free()
+    finally:
+        srv.close()
+    compare(got, oracle.build(small_np, 20000, 1, 21), inp=small_np)
