@@ -7,7 +7,7 @@
  *     leaves hold at most T original points (hierarchical counting sort);
  *   - Section 4.2: every inner node is then filled bottom-up with the
  *     occupied cells ("voxels") of a 128^3 grid laid over its cube.
- * Two sampling modes are provided:
+ * Sampling modes:
  *   - LOD_FILTER: the cell-wise average of Section 4.2.3, made exact — each
  *     voxel carries the integer mean (rounded half up) of the RGB of all
  *     original points inside its cell, accumulated as unsigned 64-bit sums;
@@ -15,6 +15,25 @@
  *   - LOD_PICK: replaces the random pick of Section 4.2.2 (Listing 1) by an
  *     order-independent rule — each voxel keeps the original point of
  *     minimal splitmix64(input index); pick_index is that index.
+ *   - LOD_WEIGHTED: the neighbourhood-weighted average of Section 4.2.4 —
+ *     an inner node samples its children's samples (points of leaf
+ *     children; voxels of inner children at their cell centres with their
+ *     8-bit colours); each sample adds weight max(0, 1 - distance to the
+ *     cell centre in cells) times its colour to the cells of the 2x2x2
+ *     block around it and occupies the cell it lies in; an occupied cell's
+ *     colour is its weighted sum over its weight sum, rounded half up,
+ *     alpha 255.  Weights are fp32, rounded to 24 fractional bits and
+ *     summed exactly, so results are deterministic; they agree with an
+ *     exact-arithmetic evaluation except where a mean lies within about
+ *     1e-5 of a rounding boundary.
+ *   - LOD_FIRST: first come (Section 4.2.1), with input order defining
+ *     "first" — each voxel keeps its cell's point of smallest input index.
+ *   - LOD_RANDOM: the random pick of Section 4.2.2 with Listing 1's 32-bit
+ *     key (12 random bits above the low 20 bits of the sample index, the
+ *     largest key kept), drawn afresh at every level from the children's
+ *     samples; the random bits are the top 12 of the high half of
+ *     splitmix64(level << 32 | input index), equal keys go to the larger
+ *     index.
  *
  * Every entry point is extern "C", takes plain pointers and sizes, and
  * returns an int status (LOD_OK on success).  Pointers documented as
@@ -64,16 +83,18 @@ typedef struct lod_point {
   uint32_t rgba;
 } lod_point_t;
 
-enum { LOD_FILTER = 0, LOD_PICK = 1 };
+enum { LOD_FILTER = 0, LOD_PICK = 1, LOD_WEIGHTED = 2, LOD_FIRST = 3, LOD_RANDOM = 4 };
 
-/* Keep the original input index of every leaf point (always kept in
- * LOD_PICK mode, where the sampling rule needs it). */
+/* Keep the original input index of every leaf point (always kept in the
+ * single-sample modes LOD_PICK, LOD_FIRST and LOD_RANDOM, whose sampling
+ * rules need it). */
 enum { LOD_FLAG_LEAF_INDEX = 1u };
 
 /* Build parameters.
  *   leaf_threshold  T >= 1: a node with more than T points is split into its
  *                   non-empty octants (Section 3; the paper uses T = 50k).
- *   mode            LOD_FILTER or LOD_PICK.
+ *   mode            LOD_FILTER, LOD_PICK, LOD_WEIGHTED, LOD_FIRST or
+ *                   LOD_RANDOM.
  *   max_depth       <= 32: nodes at this level are leaves even above T.
  *                   Unit cubes (edge 1) are leaves too; such leaves may hold
  *                   more than T points and are flagged LOD_NODE_OVERFULL.
@@ -118,10 +139,11 @@ typedef struct lod_node {
  *   cell        x | y << 7 | z << 14, the 128^3 grid cell relative to the
  *               node's cube (cell edge 2^log2_size / 128).
  *   rgba        LOD_FILTER: rounded-half-up mean RGB, A = 255;
- *               LOD_PICK: colour of the picked input point.
+ *               LOD_WEIGHTED: rounded-half-up weighted mean RGB, A = 255;
+ *               single-sample modes: colour of the picked input point.
  *   count       number of original points inside the cell.
- *   pick_index  LOD_PICK: input index of the picked point (splitmix64-min);
- *               LOD_FILTER: 0xFFFFFFFF.
+ *   pick_index  single-sample modes: input index of the picked point;
+ *               LOD_FILTER, LOD_WEIGHTED: 0xFFFFFFFF.
  * Voxel order within a node is unspecified. */
 typedef struct lod_voxel {
   uint32_t cell, rgba, count, pick_index;

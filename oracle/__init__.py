@@ -23,8 +23,9 @@ _lib = None
 
 FILTER = 0
 PICK = 1
-WEIGHTED = 2  # neighbourhood-weighted average (Section 4.2.4); oracle only so far
-FIRST = 3     # first come in input order (Section 4.2.1); oracle only so far
+WEIGHTED = 2  # neighbourhood-weighted average (Section 4.2.4)
+FIRST = 3     # first come in input order (Section 4.2.1)
+RANDOM = 4    # random pick with the key of Listing 1 (Section 4.2.2), bottom up
 
 
 def compile_oracle(force: bool = False) -> str:
@@ -64,6 +65,11 @@ def _load():
         lib.oracle_free.restype = None
         lib.oracle_splitmix64.argtypes = [ctypes.c_uint64]
         lib.oracle_splitmix64.restype = ctypes.c_uint64
+        lib.oracle_weighted_node.argtypes = [ctypes.c_void_p, ctypes.c_uint64, u32p, u8p, ctypes.c_uint64, i32p,
+                                             ctypes.c_uint32, u32p]
+        lib.oracle_weighted_node.restype = ctypes.c_int64
+        lib.oracle_random_key.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
+        lib.oracle_random_key.restype = ctypes.c_uint64
         lib.oracle_cube_voxels.argtypes = [ctypes.c_void_p, u32p, ctypes.c_uint64, i32p, ctypes.c_uint32,
                                            ctypes.c_uint32, u32p]
         lib.oracle_cube_voxels.restype = ctypes.c_int64
@@ -79,13 +85,20 @@ def splitmix64(x: int) -> int:
     return int(_load().oracle_splitmix64(ctypes.c_uint64(x)))
 
 
+def random_key(i: int, level: int) -> int:
+    """The oracle's 64-bit random-strategy key: Listing 1's 32-bit key above
+    the index (the larger wins)."""
+    return int(_load().oracle_random_key(ctypes.c_uint32(i), ctypes.c_uint32(level)))
+
+
 def build(points: np.ndarray, leaf_threshold: int = 50000, mode: int = FILTER,
           max_depth: int = 21) -> dict:
     """Run the oracle on an (N, 4) int32 point array; return numpy arrays.
 
     ``mode``: FILTER (cell average), PICK (minimal-hash sample), WEIGHTED
-    (neighbourhood-weighted average, computed bottom-up as the paper does)
-    or FIRST (the cell's first point in input order).
+    (neighbourhood-weighted average, computed bottom-up as the paper does),
+    FIRST (the cell's first point in input order) or RANDOM (largest key of
+    Listing 1 among the children's samples, bottom up).
 
     Keys: ``min`` (n,3) int32, ``level``, ``log2_size``, ``child_mask``,
     ``flags`` (uint8), ``parent``, ``first_child`` (uint32),
@@ -152,4 +165,26 @@ def cube_voxels(points: np.ndarray, index: np.ndarray, cube_min, log2_size: int,
                                 _ptr(mn, ctypes.c_int32), int(log2_size), int(mode), _ptr(out, ctypes.c_uint32))
     if nv < 0:
         raise ValueError("oracle_cube_voxels: invalid arguments (a point outside the cube?)")
+    return out[:nv].copy()
+
+
+def weighted_node(points: np.ndarray, voxels: np.ndarray, octants: np.ndarray, cube_min, log2_size: int) -> np.ndarray:
+    """Neighbourhood-weighted voxels (Section 4.2.4) of one inner node from
+    its children's samples: ``points`` (the leaf children's points, (n, 4)
+    int32) and ``voxels`` (the inner children's voxels, (m, 4) rows of cell,
+    rgba, count, pick_index) with ``octants`` (m,) giving each voxel's child
+    octant.  Rows of (cell, rgba, count, pick_index) sorted by cell."""
+    lib = _load()
+    pts = np.ascontiguousarray(points, dtype=np.int32).reshape(-1, 4)
+    vox = np.ascontiguousarray(voxels, dtype=np.uint32).reshape(-1, 4)
+    octs = np.ascontiguousarray(octants, dtype=np.uint8).reshape(-1)
+    assert len(octs) == len(vox)
+    mn = np.ascontiguousarray(np.asarray(cube_min, dtype=np.int32).reshape(3))
+    out = np.empty((max(len(pts) + len(vox), 1), 4), np.uint32)
+    nv = lib.oracle_weighted_node(pts.ctypes.data if len(pts) else None, len(pts),
+                                  _ptr(vox, ctypes.c_uint32) if len(vox) else None,
+                                  _ptr(octs, ctypes.c_uint8) if len(vox) else None, len(vox),
+                                  _ptr(mn, ctypes.c_int32), int(log2_size), _ptr(out, ctypes.c_uint32))
+    if nv < 0:
+        raise ValueError("oracle_weighted_node: invalid arguments")
     return out[:nv].copy()

@@ -33,6 +33,14 @@
 //    Section 4.2.2, Listing 1) keeps the point of minimal splitmix64(index);
 //    first come (Section 4.2.1; mode 3) keeps the first point of the cell in
 //    input order.
+//  * Random (Section 4.2.2 with the key of Listing 1; mode 4) also follows
+//    the paper's bottom-up order: an inner node samples its children's
+//    samples (points of leaf children, voxels of inner children), each with
+//    a 32-bit key of 12 random bits above the low 20 bits of its index,
+//    and every cell keeps the sample of largest key.  The random number of
+//    a sample is drawn afresh for each node from a counter-based generator
+//    (the high half of splitmix64(level << 32 | index)), and equal keys go
+//    to the larger index.
 //  * Neighbourhood-weighted average (Section 4.2.4; mode 2) follows the
 //    paper's own order instead, since its result depends on it: inner nodes
 //    deepest level first, each sampling its children's samples (the points
@@ -82,6 +90,7 @@ struct OVoxel {
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint32_t kModeWeighted = 2u;
 constexpr uint32_t kModeFirst = 3u;
+constexpr uint32_t kModeRandom = 4u;
 constexpr uint32_t kLeaf = 1u;
 constexpr uint32_t kOverfull = 2u;
 
@@ -94,6 +103,17 @@ uint64_t splitmix64(uint64_t x) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return z ^ (z >> 31);
+}
+
+// Section 4.2.2, Listing 1: the 32-bit key of a sample with index i drawn
+// while filling a node at `level`: the top 12 bits of a 32-bit random number
+// above the low 20 bits of i.  The random number is the high half of
+// splitmix64(level << 32 | i).  Returned with i appended below it, so that
+// comparing the 64-bit values compares the keys and breaks ties by index.
+uint64_t random_key(uint32_t i, uint32_t level) {
+  const uint32_t r = (uint32_t)(splitmix64(((uint64_t)level << 32) | i) >> 32);
+  const uint32_t key = (r & 0xFFF00000u) | (i & 0x000FFFFFu);
+  return ((uint64_t)key << 32) | i;
 }
 
 // Offset of point p from the cube min c along one axis, as a non-negative
@@ -182,6 +202,66 @@ struct Builder {
     nd.voxel_count = (uint32_t)(voxels.size() - nd.voxel_offset);
   }
 
+  // Section 4.2.2: one inner node's voxels under the random strategy, from
+  // its children's samples (their voxels must exist already).  Each sample
+  // falls into one cell of this node's grid; the cell keeps the sample of
+  // largest random_key at this node's level and counts the original points.
+  void voxelize_random(uint32_t id) {
+    ONode& nd = nodes[id];
+    struct RCell {
+      uint64_t key = 0;
+      uint32_t index = 0, rgba = 0;
+      uint64_t count = 0;
+    };
+    std::map<uint32_t, RCell> cells;
+    auto sample = [&](uint32_t cell, uint32_t index, uint32_t rgba, uint64_t count) {
+      RCell& c = cells[cell];
+      const uint64_t k = random_key(index, nd.level);
+      if (c.count == 0 || k > c.key) {
+        c.key = k;
+        c.index = index;
+        c.rgba = rgba;
+      }
+      c.count += count;
+    };
+    uint32_t c = nd.first_child;
+    for (uint32_t k = 0; k < 8; ++k) {
+      if (!(nd.child_mask & (1u << k))) continue;
+      const ONode& ch = nodes[c];
+      if (ch.flags & kLeaf) {
+        for (uint32_t i : leaf_lists[c]) {
+          const OPoint& p = pts[i];
+          const uint32_t qx = grid_coord(rel(p.x, nd.min[0]), nd.log2_size);
+          const uint32_t qy = grid_coord(rel(p.y, nd.min[1]), nd.log2_size);
+          const uint32_t qz = grid_coord(rel(p.z, nd.min[2]), nd.log2_size);
+          sample(qx | (qy << 7) | (qz << 14), in_index(i), p.rgba, 1);
+        }
+      } else {
+        // a child cell q lies in the cell 64 b + q / 2 of this node (the
+        // child is octant b, half the edge)
+        const uint32_t b[3] = {(k >> 2) & 1u, (k >> 1) & 1u, k & 1u};
+        for (uint32_t v = 0; v < ch.voxel_count; ++v) {
+          const OVoxel& vx = voxels[ch.voxel_offset + v];
+          const uint32_t q[3] = {vx.cell & 127u, (vx.cell >> 7) & 127u, (vx.cell >> 14) & 127u};
+          uint32_t own[3];
+          for (int a = 0; a < 3; ++a) own[a] = 64u * b[a] + (q[a] >> 1);
+          sample(own[0] | (own[1] << 7) | (own[2] << 14), vx.pick_index, vx.rgba, vx.count);
+        }
+      }
+      ++c;
+    }
+    nd.voxel_offset = voxels.size();
+    for (const auto& kv : cells) {
+      OVoxel v;
+      v.cell = kv.first;
+      v.rgba = kv.second.rgba;
+      v.count = (uint32_t)kv.second.count;
+      v.pick_index = kv.second.index;
+      voxels.push_back(v);
+    }
+    nd.voxel_count = (uint32_t)(voxels.size() - nd.voxel_offset);
+  }
+
   // Section 4.2.4: one inner node's voxels under the neighbourhood-weighted
   // average, from its children's samples (their voxels must exist already).
   // Positions are in units of the node's grid cells, so the node's cube is
@@ -222,48 +302,36 @@ struct Builder {
         }
   }
 
-  void voxelize_weighted(uint32_t id) {
-    ONode& nd = nodes[id];
-    std::map<uint32_t, WCell> cells;
+  // A point sample of node nd: its position in grid cells and its cell.
+  static void weighted_point(std::map<uint32_t, WCell>& cells, const ONode& nd, const OPoint& p) {
     const double scale = std::ldexp(1.0, 7 - (int)nd.log2_size);  // grid cells per unit of length
-    uint32_t c = nd.first_child;
-    for (uint32_t k = 0; k < 8; ++k) {
-      if (!(nd.child_mask & (1u << k))) continue;
-      const ONode& ch = nodes[c];
-      if (ch.flags & kLeaf) {
-        // a leaf child's samples are its points
-        for (uint32_t i : leaf_lists[c]) {
-          const OPoint& p = pts[i];
-          const int64_t d[3] = {rel(p.x, nd.min[0]), rel(p.y, nd.min[1]), rel(p.z, nd.min[2])};
-          double pos[3];
-          uint32_t own[3];
-          for (int a = 0; a < 3; ++a) {
-            pos[a] = (double)d[a] * scale;
-            own[a] = grid_coord(d[a], nd.log2_size);
-          }
-          add_weighted(cells, pos, own, p.rgba, 1);
-        }
-      } else {
-        // an inner child's samples are its voxels, each at the centre of its
-        // cell; the child is one octant (half the edge) of this node
-        const uint32_t b[3] = {(k >> 2) & 1u, (k >> 1) & 1u, k & 1u};
-        for (uint32_t v = 0; v < ch.voxel_count; ++v) {
-          const OVoxel& vx = voxels[ch.voxel_offset + v];
-          const uint32_t q[3] = {vx.cell & 127u, (vx.cell >> 7) & 127u, (vx.cell >> 14) & 127u};
-          double pos[3];
-          uint32_t own[3];
-          for (int a = 0; a < 3; ++a) {
-            pos[a] = 64.0 * b[a] + ((double)q[a] + 0.5) / 2.0;
-            own[a] = 64u * b[a] + (q[a] >> 1);
-          }
-          add_weighted(cells, pos, own, vx.rgba, vx.count);
-        }
-      }
-      ++c;
+    const int64_t d[3] = {rel(p.x, nd.min[0]), rel(p.y, nd.min[1]), rel(p.z, nd.min[2])};
+    double pos[3];
+    uint32_t own[3];
+    for (int a = 0; a < 3; ++a) {
+      pos[a] = (double)d[a] * scale;
+      own[a] = grid_coord(d[a], nd.log2_size);
     }
-    // occupied cells only, in cell order; colour = weighted mean rounded to
-    // the nearest integer (halves up), alpha 255
-    nd.voxel_offset = voxels.size();
+    add_weighted(cells, pos, own, p.rgba, 1);
+  }
+
+  // A voxel of the inner child in octant k, taken as one sample at the
+  // centre of its cell; the child is one octant (half the edge) of the node.
+  static void weighted_voxel(std::map<uint32_t, WCell>& cells, uint32_t k, const OVoxel& vx) {
+    const uint32_t b[3] = {(k >> 2) & 1u, (k >> 1) & 1u, k & 1u};
+    const uint32_t q[3] = {vx.cell & 127u, (vx.cell >> 7) & 127u, (vx.cell >> 14) & 127u};
+    double pos[3];
+    uint32_t own[3];
+    for (int a = 0; a < 3; ++a) {
+      pos[a] = 64.0 * b[a] + ((double)q[a] + 0.5) / 2.0;
+      own[a] = 64u * b[a] + (q[a] >> 1);
+    }
+    add_weighted(cells, pos, own, vx.rgba, vx.count);
+  }
+
+  // Occupied cells only, in cell order; colour = weighted mean rounded to
+  // the nearest integer (halves up), alpha 255.
+  static void weighted_emit(const std::map<uint32_t, WCell>& cells, std::vector<OVoxel>& out) {
     for (const auto& kv : cells) {
       const WCell& wc = kv.second;
       if (!wc.occupied) continue;
@@ -276,8 +344,28 @@ struct Builder {
       v.rgba = channel(wc.r) | (channel(wc.g) << 8) | (channel(wc.b) << 16) | (255u << 24);
       v.count = (uint32_t)wc.count;
       v.pick_index = kNone;
-      voxels.push_back(v);
+      out.push_back(v);
     }
+  }
+
+  void voxelize_weighted(uint32_t id) {
+    ONode& nd = nodes[id];
+    std::map<uint32_t, WCell> cells;
+    uint32_t c = nd.first_child;
+    for (uint32_t k = 0; k < 8; ++k) {
+      if (!(nd.child_mask & (1u << k))) continue;
+      const ONode& ch = nodes[c];
+      if (ch.flags & kLeaf) {
+        // a leaf child's samples are its points
+        for (uint32_t i : leaf_lists[c]) weighted_point(cells, nd, pts[i]);
+      } else {
+        // an inner child's samples are its voxels
+        for (uint32_t v = 0; v < ch.voxel_count; ++v) weighted_voxel(cells, k, voxels[ch.voxel_offset + v]);
+      }
+      ++c;
+    }
+    nd.voxel_offset = voxels.size();
+    weighted_emit(cells, voxels);
     nd.voxel_count = (uint32_t)(voxels.size() - nd.voxel_offset);
   }
 
@@ -369,14 +457,17 @@ struct Builder {
           leaf_lists.emplace_back();
           next.emplace_back((uint32_t)(nodes.size() - 1), std::move(part[k]));
         }
-        if (mode != kModeWeighted) voxelize(nodes[id], idx);
+        if (mode != kModeWeighted && mode != kModeRandom) voxelize(nodes[id], idx);
       }
       std::swap(cur, next);
     }
-    if (mode == kModeWeighted) {
+    if (mode == kModeWeighted || mode == kModeRandom) {
       // bottom up: breadth-first ids put every child after its parent
-      for (size_t id = nodes.size(); id-- > 0;)
-        if (!(nodes[id].flags & kLeaf)) voxelize_weighted((uint32_t)id);
+      for (size_t id = nodes.size(); id-- > 0;) {
+        if (nodes[id].flags & kLeaf) continue;
+        if (mode == kModeWeighted) voxelize_weighted((uint32_t)id);
+        else voxelize_random((uint32_t)id);
+      }
     }
     leaf_points.resize(n);
     leaf_index.resize(n);
@@ -393,11 +484,11 @@ struct oracle_result {
 extern "C" {
 
 // mode 0: cell-wise average, 1: sample pick, 2: neighbourhood-weighted
-// average, 3: first come.  Returns 0 on success, 1 on invalid arguments, 2
-// on allocation failure.
+// average, 3: first come, 4: random (Listing 1 key).  Returns 0 on success,
+// 1 on invalid arguments, 2 on allocation failure.
 int oracle_build(const void* points, uint64_t n, uint32_t leaf_threshold, uint32_t mode,
                  uint32_t max_depth, oracle_result** out) {
-  if (!out || (n > 0 && !points) || leaf_threshold == 0 || mode > kModeFirst || max_depth > 32 ||
+  if (!out || (n > 0 && !points) || leaf_threshold == 0 || mode > kModeRandom || max_depth > 32 ||
       n > 0xFFFFFFFFull)
     return 1;
   oracle_result* r = new (std::nothrow) oracle_result();
@@ -474,9 +565,10 @@ void oracle_free(oracle_result* r) { delete r; }
 // (a point outside the cube, log2_size > 32).
 int64_t oracle_cube_voxels(const void* points, const uint32_t* index, uint64_t n, const int32_t* min3,
                            uint32_t log2_size, uint32_t mode, uint32_t* out4) {
-  // the weighted average depends on the children's voxels: not defined per cube
+  // the weighted average and the random strategy depend on the children's
+  // voxels: not defined per cube
   if ((n > 0 && (!points || !index || !out4)) || !min3 || log2_size > 32 || mode == kModeWeighted ||
-      mode > kModeFirst)
+      mode == kModeRandom || mode > kModeRandom)
     return -1;
   const OPoint* p = static_cast<const OPoint*>(points);
   for (uint64_t i = 0; i < n; ++i) {
@@ -504,6 +596,47 @@ int64_t oracle_cube_voxels(const void* points, const uint32_t* index, uint64_t n
   return (int64_t)b.voxels.size();
 }
 
+// The neighbourhood-weighted voxels (Section 4.2.4) of one inner node (min
+// corner min3, edge 2^log2_size) from the samples its children give: the
+// n_points points of its leaf children (any order) and the n_voxels voxels
+// (rows of cell, rgba, count, pick_index) of its inner children, octant[j]
+// being the child octant of voxel j.  Rows of (cell, rgba, count,
+// 0xFFFFFFFF) sorted by cell go to out4 (at least n_points + n_voxels rows);
+// returns their number, or -1 on invalid arguments.
+int64_t oracle_weighted_node(const void* points, uint64_t n_points, const uint32_t* voxels4, const uint8_t* octant,
+                             uint64_t n_voxels, const int32_t* min3, uint32_t log2_size, uint32_t* out4) {
+  if ((n_points && !points) || (n_voxels && (!voxels4 || !octant)) || !min3 || !out4 || log2_size > 32 ||
+      log2_size == 0)
+    return -1;
+  ONode nd{};
+  for (int a = 0; a < 3; ++a) nd.min[a] = min3[a];
+  nd.log2_size = log2_size;
+  std::map<uint32_t, Builder::WCell> cells;
+  const OPoint* p = static_cast<const OPoint*>(points);
+  for (uint64_t i = 0; i < n_points; ++i) {
+    const int64_t d[3] = {rel(p[i].x, min3[0]), rel(p[i].y, min3[1]), rel(p[i].z, min3[2])};
+    for (int a = 0; a < 3; ++a)
+      if (d[a] < 0 || d[a] >= (int64_t(1) << log2_size)) return -1;
+    Builder::weighted_point(cells, nd, p[i]);
+  }
+  for (uint64_t j = 0; j < n_voxels; ++j) {
+    if (octant[j] > 7) return -1;
+    const OVoxel vx{voxels4[4 * j], voxels4[4 * j + 1], voxels4[4 * j + 2], voxels4[4 * j + 3]};
+    Builder::weighted_voxel(cells, octant[j], vx);
+  }
+  std::vector<OVoxel> out;
+  Builder::weighted_emit(cells, out);
+  for (size_t i = 0; i < out.size(); ++i) {
+    out4[4 * i + 0] = out[i].cell;
+    out4[4 * i + 1] = out[i].rgba;
+    out4[4 * i + 2] = out[i].count;
+    out4[4 * i + 3] = out[i].pick_index;
+  }
+  return (int64_t)out.size();
+}
+
 uint64_t oracle_splitmix64(uint64_t x) { return splitmix64(x); }
+
+uint64_t oracle_random_key(uint32_t i, uint32_t level) { return random_key(i, level); }
 
 }  // extern "C"

@@ -462,8 +462,7 @@ int lod_submit(lod_server_t* s, const lod_point_t* d_points, uint64_t n, const l
   rq->d_points = d_points;
   rq->n = n;
   rq->params = params ? *params : defaults();
-  if (rq->params.leaf_threshold == 0 || rq->params.mode > 1 || rq->params.max_depth > 32)
-    return LOD_ERR_INVALID_ARG;
+  if (!lodk::valid_params(rq->params)) return LOD_ERR_INVALID_ARG;
   rq->est = lodk::estimate_build_bytes(n, rq->params);
   if (rq->est > s->budget->limit) return LOD_ERR_BUDGET;
   {

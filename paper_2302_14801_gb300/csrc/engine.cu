@@ -57,6 +57,10 @@ struct Workspace {
   };
   std::vector<Block> blocks;
   bool busy = false;
+  // dense grids of the weighted mode (Section 4.2.4): zeroed when
+  // allocated, and every launch leaves the cells it touched empty again
+  void* wgrid = nullptr;
+  size_t wgrid_bytes = 0;
   int take(size_t b) {
     int best = -1;
     for (size_t i = 0; i < blocks.size(); ++i)
@@ -434,7 +438,7 @@ uint64_t workspace_bytes(cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_ws_mu);
   auto it = g_ws.find({dev, st});
   if (it == g_ws.end() || !it->second) return 0;
-  uint64_t b = 0;
+  uint64_t b = it->second->wgrid_bytes;
   for (auto& k : it->second->blocks) b += k.p ? k.bytes : 0;
   return b;
 }
@@ -453,6 +457,7 @@ void release_workspace(cudaStream_t st) {
   }
   for (auto& k : w->blocks)
     if (k.p) cudaFree(k.p);
+  if (w->wgrid) cudaFree(w->wgrid);
   delete w;
 }
 
@@ -533,8 +538,21 @@ SharedBuffers::~SharedBuffers() {
   cudaSetDevice(prev);
 }
 
+bool valid_mode(uint32_t mode) {
+  return mode == LOD_FILTER || mode == LOD_PICK || mode == LOD_WEIGHTED || mode == LOD_FIRST || mode == LOD_RANDOM;
+}
+
+bool valid_params(const lod_params_t& p) {
+  return p.leaf_threshold != 0 && valid_mode(p.mode) && p.max_depth <= 32;
+}
+
+// The single-sample modes need every leaf point's input index.
+bool keeps_index(const lod_params_t& p) {
+  return p.mode == LOD_PICK || p.mode == LOD_FIRST || p.mode == LOD_RANDOM || (p.flags & LOD_FLAG_LEAF_INDEX);
+}
+
 uint64_t estimate_result_bytes(uint64_t n, const lod_params_t& p) {
-  const bool idx = p.mode == LOD_PICK || (p.flags & LOD_FLAG_LEAF_INDEX);
+  const bool idx = keeps_index(p);
   const uint64_t T = std::max<uint32_t>(p.leaf_threshold, 1);
   const uint64_t nodes = 64 + 16 * ((n + T - 1) / T);
   return n * 16 + (idx ? n * 4 : 0) + (n / 2 + 1024) * 16 + nodes * sizeof(lod_node_t);
@@ -549,7 +567,7 @@ uint64_t estimate_build_bytes(uint64_t n, const lod_params_t& p) {
   // point (plus exact sums when filtering) + the voxel array's first
   // estimate + node aux + pool, plus the 32-byte leaf staging of modes that
   // keep input indices
-  const bool keep_idx = p.mode == LOD_PICK || (p.flags & LOD_FLAG_LEAF_INDEX);
+  const bool keep_idx = keeps_index(p);
   const uint64_t staging = n * (p.mode == LOD_FILTER ? 64 : 32);
   return estimate_result_bytes(n, p) + n * 20 + staging + n * 8 + (keep_idx ? n * 32 : 0) +
          nodes * sizeof(NodeAux) + pool + (16u << 20);
@@ -624,8 +642,8 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
   Workspace* const ws = lease.ws;
   if (nt == 0 || !tin) return LOD_ERR_INVALID_ARG;
   retain_pool_memory();
-  if (prm.leaf_threshold == 0 || prm.mode > 1 || prm.max_depth > 32) return LOD_ERR_INVALID_ARG;
-  const bool want_idx = prm.mode == LOD_PICK || (prm.flags & LOD_FLAG_LEAF_INDEX);
+  if (!valid_params(prm)) return LOD_ERR_INVALID_ARG;
+  const bool want_idx = keeps_index(prm);
   const uint32_t T = prm.leaf_threshold;
 
   // ---- tile table and round-0 chunk space
@@ -1062,6 +1080,34 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
       LOD_CK(d_sum1.alloc(stage_cap * 16));
     }
   }
+  // weighted mode: one dense grid per persistent CTA
+  const bool weighted = prm.mode == LOD_WEIGHTED;
+  const int wctas = sm_count();
+  const size_t cells = size_t(1) << 21;
+  DevBuf d_wtmp(st);
+  unsigned char* wbase = nullptr;
+  if (weighted && n_vlev > 0) {
+    const size_t wbytes = (size_t)wctas * wgrid_bytes_per_cta();
+    const size_t wzero = (size_t)wctas * cells * 36;  // sums and counts start at zero; the lists need not
+    if (ws) {
+      if (ws->wgrid_bytes < wbytes) {
+        if (ws->wgrid) {
+          LOD_CK(cudaStreamSynchronize(st));
+          cudaFree(ws->wgrid);
+          ws->wgrid = nullptr;
+          ws->wgrid_bytes = 0;
+        }
+        LOD_CK(cudaMalloc(&ws->wgrid, wbytes));
+        ws->wgrid_bytes = wbytes;
+        LOD_CK(cudaMemsetAsync(ws->wgrid, 0, wzero, st));
+      }
+      wbase = static_cast<unsigned char*>(ws->wgrid);
+    } else {
+      LOD_CK(d_wtmp.alloc(wbytes));
+      LOD_CK(cudaMemsetAsync(d_wtmp.p, 0, wzero, st));
+      wbase = d_wtmp.as<unsigned char>();
+    }
+  }
   const uint32_t units_cap = (uint32_t)std::min<uint64_t>((uint64_t)max_items * 64, 1u << 20);
   LOD_CK(d_units.alloc((size_t)units_cap * sizeof(uint4)));
   const size_t lctr_bytes = (size_t)std::max(n_vlev, 1) * sizeof(DevCounters);
@@ -1110,7 +1156,17 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
       vl.unit_cap = units_cap;
       vl.dense_cap = dense_cap;
       vl.vstate = d_vstate.as<unsigned long long>();
-      LOD_LAUNCH(debug_stats() ? kVoxLevelNames[l] : "voxelize", 0, launch_vox(A, vl, lc, st));
+      vl.parent_prefix = d_pref.as<uint32_t>() + (size_t)l * pstride + (nt + 1);
+      vl.n_parents = n_par;
+      if (weighted) {
+        vl.wgrid = reinterpret_cast<unsigned long long*>(wbase);
+        vl.wcnt = reinterpret_cast<uint32_t*>(wbase + (size_t)wctas * cells * 32);
+        vl.wtouch = reinterpret_cast<uint32_t*>(wbase + (size_t)wctas * cells * 36);
+        LOD_LAUNCH(debug_stats() ? kVoxLevelNames[l] : "voxelize", 0,
+                   launch_wvox(A, vl, lc, (int)std::min<uint32_t>((uint32_t)wctas, n_par), st));
+      } else {
+        LOD_LAUNCH(debug_stats() ? kVoxLevelNames[l] : "voxelize", 0, launch_vox(A, vl, lc, st));
+      }
       vox_rec[l] = prof.recs.size();
       LOD_LAUNCH("level_scan", 0,
                  launch_level_scan(A, vl, d_pref.as<uint32_t>() + (size_t)l * pstride + (nt + 1), n_par,

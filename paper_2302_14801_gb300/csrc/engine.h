@@ -56,6 +56,11 @@ int run_build(const TileInput* tiles, uint32_t n_tiles, const lod_params_t& para
 uint64_t workspace_bytes(cudaStream_t st);
 void release_workspace(cudaStream_t st);
 
+// Parameter checks shared by every entry point, and whether a build keeps
+// the input index of every leaf point.
+bool valid_params(const lod_params_t& p);
+bool keeps_index(const lod_params_t& p);
+
 // Rough device footprint (bytes) of building n points (result + temporaries).
 uint64_t estimate_build_bytes(uint64_t n, const lod_params_t& params);
 // Rough device footprint of a finished result of n points.

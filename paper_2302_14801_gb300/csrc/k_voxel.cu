@@ -9,10 +9,11 @@
 // shared-memory open-addressing hash table instead of a dense grid.  An
 // octant whose occupied cells exceed the table is processed in several
 // hash-partitioned passes.  Colour sums are exact integers (32-bit lanes
-// while they provably cannot overflow, 64-bit otherwise); the pick keeps,
-// per cell, the entry {splitmix64(index), rgba | index << 32} of minimal
-// hash, updated by a 128-bit compare-and-swap, so the picked colour travels
-// with the winning hash and is never gathered from the input.
+// while they provably cannot overflow, 64-bit otherwise); the single-sample
+// modes (minimal-hash pick, first come of Section 4.2.1, random with the
+// key of Listing 1) keep, per cell, the entry {key, rgba | index << 32} of
+// minimal key, updated by a 128-bit compare-and-swap, so the picked colour
+// travels with the winning key and is never gathered from the input.
 //
 // Every octant's voxels go to a staging area; a level scan then assigns
 // each parent one contiguous voxel range (children are consecutive in node
@@ -150,6 +151,32 @@ __device__ __forceinline__ uint32_t mean_rgba(uint64_t r, uint64_t g, uint64_t b
   return round_mean(r, n) | (round_mean(g, n) << 8) | (round_mean(b, n) << 16) | 0xFF000000u;
 }
 
+// Key of a sample in the single-sample modes; every cell keeps the sample
+// of smallest key, and every key is below the empty entry's ~0 (the
+// splitmix64 preimage of ~0 is not a 32-bit index).  `level` is the level
+// of the node being filled.
+//  - LOD_PICK: splitmix64(input index) (replaces Listing 1 with an exact,
+//    order-independent rule).
+//  - LOD_FIRST: the input index itself: the first sample in input order
+//    (Section 4.2.1); a child's voxel carries its own first point, so the
+//    bottom-up merge keeps the cell's first point.
+//  - LOD_RANDOM: Listing 1 of Section 4.2.2: a 32-bit key holding the top
+//    12 bits of a random number drawn for the sample at this level above
+//    the low 20 bits of the sample's index, the largest key winning; equal
+//    keys go to the larger index.  The random number is the high half of
+//    splitmix64(level << 32 | index).  Minimising 2^64 - 2 - (key << 32 |
+//    index) maximises (key, index).
+template <int MODE>
+__device__ __forceinline__ uint64_t pick_key(uint32_t ix, uint32_t level) {
+  if (MODE == LOD_FIRST) return ix;
+  if (MODE == LOD_RANDOM) {
+    const uint32_t r = (uint32_t)(splitmix64(((uint64_t)level << 32) | ix) >> 32);
+    const uint64_t key = (r & 0xFFF00000u) | (ix & 0x000FFFFFu);
+    return 0xFFFFFFFFFFFFFFFEull - ((key << 32) | ix);
+  }
+  return splitmix64(ix);
+}
+
 }  // namespace
 
 int vox_smem_bytes() { return kSmemBytes; }
@@ -220,9 +247,10 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
   const ItemInfo& I = S.I;
   const TileDesc& td = a.tiles[I.tile];
   const lod_node_t& c = v.nodes[I.g];
+  constexpr bool PICKLIKE = MODE != LOD_FILTER;  // one sample kept per cell
   // 32-bit channel sums cannot overflow when the cube holds few enough points
   const bool narrow = MODE == LOD_FILTER && I.npts <= kNarrowMaxSamples;
-  const uint32_t H = MODE == LOD_PICK ? kHp : (narrow ? kHn : kHw);
+  const uint32_t H = PICKLIKE ? kHp : (narrow ? kHn : kHw);
   // shared-memory carve-up (u64 arrays first)
   unsigned long long* A0 = reinterpret_cast<unsigned long long*>(smem);
   unsigned long long* A1 = A0 + H;
@@ -230,7 +258,7 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
   ulonglong2* E = reinterpret_cast<ulonglong2*>(smem);  // pick entries
   uint32_t* keys;
   uint32_t* cnt32;
-  if (MODE == LOD_PICK) {
+  if (PICKLIKE) {
     keys = reinterpret_cast<uint32_t*>(E + H);
     cnt32 = keys + H;
   } else if (narrow) {
@@ -244,7 +272,7 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
   const uint64_t bound = umin64(I.n, kOctCells);  // cells the item can occupy
   const uint64_t pbase = td.pt_base + c.point_offset;
   const int4* pts = a.out + pbase;
-  const uint32_t* pidx = (MODE == LOD_PICK) ? a.out_idx + pbase : nullptr;
+  const uint32_t* pidx = PICKLIKE ? a.out_idx + pbase : nullptr;
   // with kept indices the leaf is read from the 32-byte staging records and
   // published to the point / index arrays here, contiguously
   const int4* wsrc = a.wide ? a.wide + 2 * pbase : nullptr;
@@ -262,7 +290,7 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
     if (!S.clean) {
       // an empty entry is all zero bytes in filtered mode whatever the
       // table's layout, so a clean table serves every item
-      if (MODE == LOD_PICK) {
+      if (PICKLIKE) {
         for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) {
           keys[i] = 0u;
           E[i] = make_ulonglong2(~0ull, 0ull);
@@ -305,8 +333,8 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
         n_same = 1;
         if (key1 == 0u) return false;
         // most pick updates lose the comparison against the entry they
-        // read, so pick mode skips the merge
-        if (MODE == LOD_PICK) return true;
+        // read, so the single-sample modes skip the merge
+        if (PICKLIKE) return true;
         const unsigned peers = __match_any_sync(act, key1);
         n_same = __popc(peers);
         if (n_same > 1) {
@@ -322,8 +350,8 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
           S.fail = 1;
           return;
         }
-        if (MODE == LOD_PICK) {
-          if (!pick_update(&E[slot], splitmix64(ix), (uint64_t)(uint32_t)q.w | ((uint64_t)ix << 32)))
+        if (PICKLIKE) {
+          if (!pick_update(&E[slot], pick_key<MODE>(ix, v.level), (uint64_t)(uint32_t)q.w | ((uint64_t)ix << 32)))
             atomicOr(&ctr->error, kErrInternal);
           atomicAdd(&cnt32[slot], n_same);
         } else if (narrow) {
@@ -362,7 +390,7 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
           ld_wide(wsrc + 2 * i, q, x);
         } else {
           q = __ldcs(pts + i);
-          if (MODE == LOD_PICK) x = __ldcs(pidx + i);
+          if (PICKLIKE) x = __ldcs(pidx + i);
         }
       };
       const bool publish = wsrc != nullptr && part == 0;
@@ -431,9 +459,9 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
             S.fail = 1;
             continue;
           }
-          if (MODE == LOD_PICK) {
+          if (PICKLIKE) {
             const uint32_t idx = (uint32_t)vr.w;
-            if (!pick_update(&E[slot], splitmix64(idx), (uint64_t)(uint32_t)vr.y | ((uint64_t)idx << 32)))
+            if (!pick_update(&E[slot], pick_key<MODE>(idx, v.level), (uint64_t)(uint32_t)vr.y | ((uint64_t)idx << 32)))
               atomicOr(&ctr->error, kErrInternal);
             atomicAdd(&cnt32[slot], (uint32_t)vr.z);
           } else {
@@ -537,7 +565,7 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
       ulonglong2 e = make_ulonglong2(0ull, 0ull);
       uint32_t c32 = 0;
       uint64_t sr = 0, sg = 0, sb = 0, n = 0;
-      if (MODE == LOD_PICK) {
+      if (PICKLIKE) {
         e = E[i];
         c32 = cnt32[i];
         E[i] = make_ulonglong2(~0ull, 0ull);
@@ -564,9 +592,9 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
       const uint32_t cell = key_to_cell(key1, I);
       int4 rec;
       rec.x = (int)cell;
-      if (MODE == LOD_PICK) {
+      if (PICKLIKE) {
         const uint32_t best = (uint32_t)(e.y >> 32);
-        if (best >= td.n || splitmix64(best) != e.x) {  // cannot happen for a cell that received a sample
+        if (best >= td.n || pick_key<MODE>(best, v.level) != e.x) {  // cannot happen for a cell that received a sample
           atomicOr(&ctr->error, kErrInternal);
           continue;
         }
@@ -686,7 +714,12 @@ static cudaError_t launch_vox_mode(const BuildArgs& a, const VoxLevel& v, DevCou
 
 cudaError_t launch_vox(const BuildArgs& a, const VoxLevel& v, DevCounters* ctr, cudaStream_t st) {
   if (!v.n_items) return cudaSuccess;
-  return a.mode == LOD_PICK ? launch_vox_mode<LOD_PICK>(a, v, ctr, st) : launch_vox_mode<LOD_FILTER>(a, v, ctr, st);
+  switch (a.mode) {
+    case LOD_PICK: return launch_vox_mode<LOD_PICK>(a, v, ctr, st);
+    case LOD_FIRST: return launch_vox_mode<LOD_FIRST>(a, v, ctr, st);
+    case LOD_RANDOM: return launch_vox_mode<LOD_RANDOM>(a, v, ctr, st);
+    default: return launch_vox_mode<LOD_FILTER>(a, v, ctr, st);
+  }
 }
 
 // Assign every item its place in the level's contiguous voxel block

@@ -49,8 +49,18 @@ struct VoxLevel {
   uint32_t unit_cap;
   uint64_t dense_cap;          // records the public voxel array holds
   unsigned long long* vstate;  // [0] voxels of the levels done so far, [1] nonzero: dense_cap too small
+  // weighted mode (Section 4.2.4): parents of this level and the per-CTA
+  // dense grids (2^21 cells each: four u64 sums, a u32 count, a touched list)
+  const uint32_t* parent_prefix;  // n_tiles + 1 prefix of parents (nodes at level l) per tile
+  uint32_t n_parents;
+  unsigned long long* wgrid;
+  uint32_t* wcnt;
+  uint32_t* wtouch;
 };
 cudaError_t launch_vox(const BuildArgs& a, const VoxLevel& v, DevCounters* ctr, cudaStream_t st);
+// Section 4.2.4: one persistent CTA per grid over the parents of a level.
+cudaError_t launch_wvox(const BuildArgs& a, const VoxLevel& v, DevCounters* ctr, int ctas, cudaStream_t st);
+size_t wgrid_bytes_per_cta();
 cudaError_t launch_level_scan(const BuildArgs& a, const VoxLevel& v, const uint32_t* parent_prefix,
                               uint32_t n_parents, unsigned long long* tile_voxels, DevCounters* ctr,
                               cudaStream_t st);

@@ -25,6 +25,10 @@ LOD_ERR_INTERNAL = 7
 
 FILTER = 0
 PICK = 1
+WEIGHTED = 2
+FIRST = 3
+RANDOM = 4
+MODES = {"filter": FILTER, "filtered": FILTER, "pick": PICK, "weighted": WEIGHTED, "first": FIRST, "random": RANDOM}
 FLAG_LEAF_INDEX = 1
 NODE_LEAF = 1
 NODE_OVERFULL = 2
@@ -143,7 +147,7 @@ def error_string(status: int) -> str:
 
 def make_params(leaf_threshold=50000, mode=FILTER, max_depth=21, keep_index=False) -> Params:
     if isinstance(mode, str):
-        mode = {"filter": FILTER, "filtered": FILTER, "pick": PICK}[mode]
+        mode = MODES[mode]
     return Params(int(leaf_threshold), int(mode), int(max_depth), FLAG_LEAF_INDEX if keep_index else 0)
 
 

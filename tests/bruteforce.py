@@ -15,7 +15,13 @@ oracle's dictionary layout) against the definitions:
 * every inner node's voxels are exactly the occupied 128^3 cells, with the
   exact count, the rounded-half-up mean colour (filtered), the member of
   minimal splitmix64(index) (pick) or the first member in input order
-  (first come).
+  (first come);
+* random (Section 4.2.2, Listing 1): computed recursively here from its
+  definition — an inner node's candidates in a cell are the points of its
+  leaf children and the winners of its inner children's cells that lie in
+  that cell; the winner is the candidate of largest 32-bit key (top 12
+  bits of the high half of splitmix64(level << 32 | index) above the low
+  20 index bits), the larger index on equal keys.
 """
 from __future__ import annotations
 
@@ -29,6 +35,13 @@ def splitmix64_py(x: int) -> int:
     z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
     z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
     return z ^ (z >> 31)
+
+
+def random_key_py(i: int, level: int) -> tuple:
+    """Listing 1's key of sample i drawn while filling a node at ``level``,
+    with the index as the tie-break: compare as a tuple."""
+    r = splitmix64_py((level << 32) | i) >> 32
+    return ((r >> 20) << 20) | (i & 0xFFFFF), i
 
 
 def _morton(dx: int, dy: int, dz: int, bits: int) -> int:
@@ -135,6 +148,30 @@ def check(points: np.ndarray, res: dict, T: int, mode: int, max_depth: int) -> N
     vox = np.asarray(res["voxels"], dtype=np.int64).reshape(-1, 4)
     voff = res["voxel_offset"].astype(np.int64)
     vcnt = res["voxel_count"].astype(np.int64)
+
+    def cell_of(p, node):
+        c, s = mins[node], 2 ** int(lg[node])
+        q = [((int(xyz[p, a]) - int(c[a])) * 128) // s for a in range(3)]
+        return q[0] + 128 * q[1] + 16384 * q[2]
+
+    winners = {}  # random mode: node -> {cell: winning input index}
+
+    def random_winners(i):
+        if i in winners:
+            return winners[i]
+        cand = {}
+        for r in range(bin(int(mask[i])).count("1")):
+            j = int(fc[i] + r)
+            if flags[j] & 1:
+                c, s = mins[j], 2 ** int(lg[j])
+                pts_j = np.nonzero(np.all((xyz >= c) & (xyz < c + s), axis=1))[0].tolist()
+            else:
+                pts_j = list(random_winners(j).values())
+            for p in pts_j:
+                cand.setdefault(cell_of(p, i), []).append(p)
+        winners[i] = {cell: max(ps, key=lambda p: random_key_py(p, int(lvl[i]))) for cell, ps in cand.items()}
+        return winners[i]
+
     for i in range(nn):
         if flags[i] & 1:
             assert vcnt[i] == 0
@@ -163,6 +200,9 @@ def check(points: np.ndarray, res: dict, T: int, mode: int, max_depth: int) -> N
                 assert r[1] == want_rgba and r[3] == NONE
             elif mode == 3:
                 best = min(members)  # first come: the first member in input order
+                assert r[3] == best and r[1] == int(rgba[best])
+            elif mode == 4:
+                best = random_winners(i)[cell]
                 assert r[3] == best and r[1] == int(rgba[best])
             else:
                 best = min(members, key=splitmix64_py)

@@ -55,17 +55,21 @@ def invariants(res, n):
         assert int(vox[a:a + c, 2].astype(np.int64).sum()) == cnt[i]
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_aerial_50m_full_parity(lod, aerial, mode):
+def test_aerial_50m_full_parity_all_modes(lod, aerial):
+    # filtered, pick, first come and random, each against the whole-cloud
+    # oracle (the oracle builds run side by side on the host cores)
     import torch
-    d = torch.from_numpy(aerial).cuda()
-    r = lod.build(d, T, mode, 21, stream=torch.cuda.current_stream())
-    got = r.to_host()
-    r.free()
-    del d
-    invariants(got, N)
-    want = oracle.build(aerial, T, mode, 21)
-    compare(got, want, inp=aerial)
+    modes = (0, 1, 3, 4)
+    with ThreadPoolExecutor(len(modes)) as ex:
+        futs = {m: ex.submit(oracle.build, aerial, T, m, 21) for m in modes}
+        d = torch.from_numpy(aerial).cuda()
+        for m in modes:
+            r = lod.build(d, T, m, 21, stream=torch.cuda.current_stream())
+            got = r.to_host()
+            r.free()
+            invariants(got, N)
+            compare(got, futs[m].result(), inp=aerial)
+        del d
 
 
 # --------------------------------------------------------------------------

@@ -1,7 +1,8 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle,
 bit-exact, on seeded synthetic inputs spanning many chunks and ragged
 tails, the edge cases of the method, and the batched / host-input /
-serving entry points."""
+serving entry points.  Modes: 0 cell-wise average (filtered), 1 minimal
+splitmix64 pick, 3 first come, 4 random with Listing 1's key."""
 import numpy as np
 import pytest
 
@@ -49,20 +50,20 @@ def P(rows):
 
 # ------------------------------------------------------------- edge cases
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 3, 4])
 def test_empty(lod, mode):
     got = gpu_build(lod, np.zeros((0, 4), np.int32), 10, mode)
     assert len(got["level"]) == 1 and got["flags"][0] == 1 and got["point_count"][0] == 0
     assert list(got["min"][0]) == [0, 0, 0] and got["log2_size"][0] == 0
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 3, 4])
 def test_single_point_and_leaf_root(lod, mode):
     parity(lod, P([(5, -7, 9, 1, 2, 3)]), 1, mode)
     parity(lod, synth.sphere(3000, seed=3), 3000, mode)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 3, 4])
 def test_identical_points_and_chains(lod, mode):
     parity(lod, P([(5, 5, 5, 1, 2, 3)] * 1000), 3, mode)
     pts = P([(0, 0, 0, 1, 1, 1)] * 9 + [(1023, 0, 0, 2, 2, 2)])
@@ -70,7 +71,7 @@ def test_identical_points_and_chains(lod, mode):
         parity(lod, pts, 3, mode, md)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 3, 4])
 def test_full_int32_extent(lod, mode):
     rng = np.random.default_rng(5)
     xyz = rng.integers(-(2**31), 2**31, size=(5000, 3))
@@ -83,7 +84,7 @@ def test_full_int32_extent(lod, mode):
     assert got["log2_size"][0] == 32
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 3, 4])
 def test_lattices(lod, mode):
     g = np.stack(np.meshgrid(np.arange(8), np.arange(8), np.arange(8), indexing="ij"), -1).reshape(-1, 3)
     rows = np.concatenate([g, np.full((512, 3), 9)], axis=1)
@@ -95,8 +96,8 @@ def test_lattices(lod, mode):
 @pytest.mark.parametrize("n", [4095, 4096, 4097, 3 * 4096 + 1])
 def test_chunk_boundaries(lod, n):
     pts = synth.sphere(n, seed=n)
-    parity(lod, pts, 200, 0)
-    parity(lod, pts, 200, 1)
+    for mode in (0, 1, 3, 4):
+        parity(lod, pts, 200, mode)
 
 
 def _random_cloud(rng, n, spread_log2):
@@ -122,7 +123,7 @@ def test_random_tiny_deep_trees(lod, seed):
     T = int(rng.integers(1, 17))
     max_depth = int(rng.choice([21, 3, 1, 6, 32]))
     pts = _random_cloud(rng, n, int(rng.integers(1, 31)))
-    for mode in (0, 1):
+    for mode in (0, 1, 3, 4):
         got = parity(lod, pts, T, mode, max_depth)
         if n <= 600:
             check(pts, got, T, mode, max_depth)
@@ -168,7 +169,7 @@ def test_autotune_picks_a_candidate_and_keeps_results(lod):
 
 # --------------------------------------------------- workload-shaped inputs
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 3, 4])
 def test_sphere_1m_default_T(lod, mode):
     parity(lod, synth.sphere(1_000_000, seed=1), 50000, mode)
 
@@ -179,7 +180,7 @@ def test_aerial_2m(lod, mode, T):
     parity(lod, synth.aerial(2_000_000, seed=2, n_buildings=80), T, mode)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 3, 4])
 @pytest.mark.parametrize("T", [50000, 2000])
 def test_indoor_dense_clusters_refinement(lod, mode, T):
     # log-normal densities put millions of points into single first-grid
@@ -187,7 +188,7 @@ def test_indoor_dense_clusters_refinement(lod, mode, T):
     parity(lod, synth.indoor(3_000_000, seed=3, n_prims=256), T, mode)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 3, 4])
 def test_volumetric_octants_overflow_tables(lod, mode):
     # 400k points uniform in a cube with T = 150k: every child octant of the
     # root holds ~50k distinct cells, more than one shared-memory table pass
@@ -240,7 +241,7 @@ def test_trim_frees_scratch_and_keeps_results(lod):
     assert lod.scratch_bytes(st) == 0
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 3, 4])
 def test_batched_equals_single(lod, mode):
     import torch
     sizes = [0, 1, 17, 4096, 4097, 30_000, 250_000, 1_000_000, 60_000, 5]
@@ -290,7 +291,7 @@ def test_server_budget_rejects_oversized(lod):
 
 # ---------------------------------------------------------------- golden
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 3, 4])
 def test_hand_worked_examples(lod, mode):
     import golden
     for path, m in golden.cases(modes=(mode,)):

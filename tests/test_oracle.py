@@ -14,6 +14,11 @@ definitions and by mathematics, not by the oracle itself.
   each file states, each derivation written out in its file).
 * First come (Section 4.2.1, oracle mode 3): the brute-force checker takes
   every cell's first point in input order.
+* Random (Section 4.2.2 with Listing 1's key, oracle mode 4): the
+  brute-force checker's recursive definition (children's winners compete
+  again at every level with fresh random bits); the key's bit layout from
+  the published splitmix64 outputs; cells and counts equal to the average
+  mode's; the result differs from a single top-down draw.
 * Neighbourhood-weighted average (Section 4.2.4, oracle mode 2): the mean
   of the corner samples on cubes of edge <= 128 (equal weights), cells and
   counts equal to the average mode's, constant colours exact, channels
@@ -24,7 +29,7 @@ import pytest
 
 import golden
 import oracle
-from bruteforce import check, splitmix64_py
+from bruteforce import check, random_key_py, splitmix64_py
 from paper_2302_14801_gb300 import synth
 
 NONE = 0xFFFFFFFF
@@ -234,14 +239,14 @@ def test_bruteforce_random_tiny(seed):
     T = int(rng.integers(1, 17))
     max_depth = int(rng.choice([21, 3, 1, 6]))
     pts = _random_cloud(rng, n, int(rng.integers(1, 24)))
-    for mode in (0, 1, 3):
+    for mode in (0, 1, 3, 4):
         r = oracle.build(pts, T, mode, max_depth)
         check(pts, r, T, mode, max_depth)
 
 
 def test_bruteforce_sphere_small():
     pts = synth.sphere(1500, seed=5)
-    for mode in (0, 1, 3):
+    for mode in (0, 1, 3, 4):
         r = oracle.build(pts, 16, mode)
         check(pts, r, 16, mode, 21)
 
@@ -310,7 +315,7 @@ def test_rejects_bad_arguments():
     with pytest.raises(ValueError):
         oracle.build(pts, 0, 0)
     with pytest.raises(ValueError):
-        oracle.build(pts, 10, 4)  # modes: 0 average, 1 pick, 2 weighted, 3 first come
+        oracle.build(pts, 10, 5)  # modes: 0 average, 1 pick, 2 weighted, 3 first come, 4 random
     with pytest.raises(ValueError):
         oracle.build(pts, 10, 0, 33)
 
@@ -340,7 +345,7 @@ def test_bruteforce_checker_catches_planted_mistakes():
             check(pts, mutated(fn), 12, 0, 21)
 
 
-@pytest.mark.parametrize("mode", [1, 3])
+@pytest.mark.parametrize("mode", [1, 3, 4])
 def test_bruteforce_pick_catches_wrong_argmin(mode):
     pts = synth.sphere(600, seed=12)
     good = oracle.build(pts, 10, mode)
@@ -549,3 +554,97 @@ def test_weighted_check_catches_planted_mistakes():
         mutate(bad["voxels"])
         with pytest.raises(AssertionError):
             check_corner_means(pts, bad, 7)
+
+
+# ------------------------------------------------- random (Listing 1 key)
+
+def test_random_key_layout_from_published_splitmix64():
+    # Listing 1: key = (random & 0xfff00000) | (index & 0x000fffff).  The
+    # random number of index i at level l is the high half of
+    # splitmix64(l << 32 | i); for level 0 and i = 0 that is the published
+    # seed-0 output 0xe220a8397b1dcdaf, whose high half 0xe220a839 keeps
+    # 0xe22 as its top 12 bits.
+    assert oracle.random_key(0, 0) == (0xE2200000 << 32) | 0
+    # the high 12 bits come from the random number, the low 20 from the index
+    # (which also breaks ties below the 32-bit key)
+    i = (5 << 20) | 0x12345
+    k = oracle.random_key(i, 7)
+    assert (k >> 32) & 0xFFFFF == 0x12345 and k & 0xFFFFFFFF == i
+    assert (k >> 52) == splitmix64_py((7 << 32) | i) >> 52
+
+
+def test_random_cells_and_counts_equal_the_average_modes():
+    pts = synth.indoor(60_000, seed=8, n_prims=16)
+    a = oracle.build(pts, 700, 0)
+    b = oracle.build(pts, 700, 4)
+    for k in ("min", "level", "log2_size", "child_mask", "flags", "parent", "first_child",
+              "point_offset", "point_count", "voxel_count"):
+        assert np.array_equal(a[k], b[k]), k
+    # per node (the bottom-up mode lays its node blocks out in another order)
+    for i in np.nonzero(a["voxel_count"])[0]:
+        va = a["voxels"][int(a["voxel_offset"][i]):][: int(a["voxel_count"][i])]
+        vb = b["voxels"][int(b["voxel_offset"][i]):][: int(b["voxel_count"][i])]
+        assert np.array_equal(va[:, [0, 2]], vb[:, [0, 2]]), i
+    # every pick is a member point of its cell with that point's colour
+    assert np.array_equal(b["voxels"][:, 1], pts[b["voxels"][:, 3].astype(np.int64), 3].view(np.uint32))
+
+
+def test_random_is_drawn_bottom_up_not_top_down():
+    # children's winners compete again with fresh random bits: on a tree a
+    # few levels deep some cell of the root keeps another point than a
+    # single draw over all of the cell's points would
+    pts = synth.sphere(20_000, seed=9)
+    r = oracle.build(pts, 200, 4)
+    root = r["voxels"][int(r["voxel_offset"][0]):][: int(r["voxel_count"][0])]
+    d = pts[:, :3].astype(np.int64) - r["min"][0].astype(np.int64)
+    q = (d * 128) >> int(r["log2_size"][0])
+    cell = q[:, 0] + 128 * q[:, 1] + 16384 * q[:, 2]
+    differ = 0
+    for row in root:
+        members = np.nonzero(cell == row[0])[0]
+        top_down = max(members.tolist(), key=lambda p: random_key_py(p, 0))
+        differ += int(top_down != row[3])
+    assert differ > 0
+
+
+def test_random_checker_catches_a_top_down_draw():
+    pts = synth.sphere(3000, seed=10)
+    good = oracle.build(pts, 40, 4)
+    check(pts, good, 40, 4, 21)
+    bad = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in good.items()}
+    d = pts[:, :3].astype(np.int64) - good["min"][0].astype(np.int64)
+    q = (d * 128) >> int(good["log2_size"][0])
+    cell = q[:, 0] + 128 * q[:, 1] + 16384 * q[:, 2]
+    changed = 0
+    o = int(good["voxel_offset"][0])  # the root's block (laid out last when filled bottom up)
+    for j in range(o, o + int(good["voxel_count"][0])):
+        members = np.nonzero(cell == bad["voxels"][j, 0])[0]
+        top_down = max(members.tolist(), key=lambda p: random_key_py(p, 0))
+        if top_down != bad["voxels"][j, 3]:
+            bad["voxels"][j, 3] = top_down
+            bad["voxels"][j, 1] = int(pts[top_down, 3]) & 0xFFFFFFFF
+            changed += 1
+    assert changed > 0
+    with pytest.raises(AssertionError):
+        check(pts, bad, 40, 4, 21)
+
+
+# -------------------------------------- weighted average, one node at a time
+
+@pytest.mark.parametrize("seed", [4, 5])
+def test_weighted_node_entry_point_equals_every_inner_node(seed):
+    # the per-node entry point (used to check CUDA results node by node on
+    # their own children's samples) gives exactly the voxels the weighted
+    # build computed for every inner node, on trees several levels deep
+    import weighted
+    pts = synth.sphere(15_000, seed=seed, radius_log2=12)
+    res = oracle.build(pts, 200, 2, 21)
+    assert res["level"].max() >= 3
+    total, exact = weighted.per_node_check(res, tol=0)
+    assert total > 0 and exact == total
+
+
+def test_weighted_node_rejects_points_outside_the_cube():
+    with pytest.raises(ValueError):
+        oracle.weighted_node(P([(300, 0, 0, 1, 2, 3)]), np.zeros((0, 4), np.uint32), np.zeros(0, np.uint8),
+                             [0, 0, 0], 8)
