@@ -68,7 +68,7 @@ def test_invalid_arguments_rejected_on_host(lodmod):
     odd = ctypes.c_void_p((1 << 20) + 8)
     assert L.lod_build(odd, 1, ctypes.byref(p), None, ctypes.byref(h)) == lodmod.LOD_ERR_INVALID_ARG
     assert L.lod_build(dev, 1 << 32, ctypes.byref(p), None, ctypes.byref(h)) == lodmod.LOD_ERR_INVALID_ARG
-    for bad in (lodmod.make_params(mode=2), lodmod.make_params(max_depth=33), lodmod.make_params(leaf_threshold=0)):
+    for bad in (lodmod.make_params(mode=5), lodmod.make_params(max_depth=33), lodmod.make_params(leaf_threshold=0)):
         assert L.lod_build(dev, 1, ctypes.byref(bad), None, ctypes.byref(h)) == lodmod.LOD_ERR_INVALID_ARG
     tiles = (ctypes.c_void_p * 2)(dev, odd)
     ns = (ctypes.c_uint64 * 2)(5, 5)
