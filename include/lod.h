@@ -85,10 +85,13 @@ typedef struct lod_point {
 
 enum { LOD_FILTER = 0, LOD_PICK = 1, LOD_WEIGHTED = 2, LOD_FIRST = 3, LOD_RANDOM = 4 };
 
-/* Keep the original input index of every leaf point (always kept in the
- * single-sample modes LOD_PICK, LOD_FIRST and LOD_RANDOM, whose sampling
- * rules need it). */
-enum { LOD_FLAG_LEAF_INDEX = 1u };
+/* LOD_FLAG_LEAF_INDEX: keep the original input index of every leaf point
+ * (always kept in the single-sample modes LOD_PICK, LOD_FIRST and
+ * LOD_RANDOM, whose sampling rules need it).
+ * LOD_FLAG_FULL_PRECISION: the full-precision variant of Section 7 for the
+ * single-sample modes — every voxel also carries the input point it picked,
+ * unquantised (see lod_result_voxel_points); other modes reject the flag. */
+enum { LOD_FLAG_LEAF_INDEX = 1u, LOD_FLAG_FULL_PRECISION = 2u };
 
 /* Build parameters.
  *   leaf_threshold  T >= 1: a node with more than T points is split into its
@@ -98,7 +101,7 @@ enum { LOD_FLAG_LEAF_INDEX = 1u };
  *   max_depth       <= 32: nodes at this level are leaves even above T.
  *                   Unit cubes (edge 1) are leaves too; such leaves may hold
  *                   more than T points and are flagged LOD_NODE_OVERFULL.
- *   flags           LOD_FLAG_* bits. */
+ *   flags           LOD_FLAG_* bits (unknown bits are rejected). */
 typedef struct lod_params {
   uint32_t leaf_threshold;
   uint32_t mode;
@@ -218,6 +221,19 @@ int lod_result_view(const lod_result_t* r, lod_view_t* view);
  *   voxels  n_voxels records, grouped per node in node order. */
 int lod_result_copy_to_host(const lod_result_t* r, lod_node_t* nodes, lod_point_t* points,
                             uint32_t* index, lod_voxel_t* voxels, void* stream);
+
+/* Full-precision variant (Section 7; built with LOD_FLAG_FULL_PRECISION):
+ * *d_points (device, owned by the result) receives an array parallel to
+ * the view's voxel array — element voxel_offset + j of a node is the input
+ * point (x, y, z, rgba) that voxel j of that node picked, i.e. the input
+ * record at its pick_index.  Returns LOD_ERR_INVALID_ARG when the result
+ * was built without the flag. */
+int lod_result_voxel_points(const lod_result_t* r, const lod_point_t** d_points);
+
+/* Copy those points to host memory in the order lod_result_copy_to_host
+ * gives the voxels (grouped per node in node order); `points` holds the
+ * result's n_voxels records.  Synchronises `stream` before returning. */
+int lod_result_copy_voxel_points_to_host(const lod_result_t* r, lod_point_t* points, void* stream);
 
 /* Device bytes held by a result (its share of shared buffers included). */
 uint64_t lod_result_device_bytes(const lod_result_t* r);

@@ -203,6 +203,42 @@ int lod_result_copy_to_host(const lod_result_t* r, lod_node_t* nodes, lod_point_
   return LOD_OK;
 }
 
+int lod_result_voxel_points(const lod_result_t* r, const lod_point_t** d_points) {
+  if (!r || !d_points || !r->sh->voxel_points) return LOD_ERR_INVALID_ARG;
+  *d_points = static_cast<const lod_point_t*>(r->sh->voxel_points);
+  return LOD_OK;
+}
+
+int lod_result_copy_voxel_points_to_host(const lod_result_t* r, lod_point_t* points, void* stream) {
+  if (!r || !r->sh->voxel_points || (!points && r->tr.n_voxels)) return LOD_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  lod_view_t v;
+  lod_result_view(r, &v);
+  std::vector<lod_node_t> hn(v.n_nodes);
+  cudaError_t e = cudaMemcpyAsync(hn.data(), v.nodes, v.n_nodes * sizeof(lod_node_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return to_status(e);
+  std::vector<uint64_t> off(v.n_nodes);
+  uint64_t acc = 0;
+  for (uint32_t i = 0; i < v.n_nodes; ++i) {
+    off[i] = acc;
+    acc += hn[i].voxel_count;
+  }
+  if (!acc) return LOD_OK;
+  void *d_off = nullptr, *d_tmp = nullptr;
+  e = cudaMallocAsync(&d_off, v.n_nodes * 8, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&d_tmp, acc * 16, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, off.data(), v.n_nodes * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = lodk::launch_gather_voxels(v.nodes, v.n_nodes, static_cast<const uint64_t*>(d_off),
+                                   static_cast<const int4*>(r->sh->voxel_points), static_cast<int4*>(d_tmp), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(points, d_tmp, acc * 16, cudaMemcpyDeviceToHost, st);
+  if (d_off) cudaFreeAsync(d_off, st);
+  if (d_tmp) cudaFreeAsync(d_tmp, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return to_status(e);
+}
+
 uint64_t lod_result_device_bytes(const lod_result_t* r) { return r ? r->bytes : 0; }
 
 void lod_free(lod_result_t* r) {

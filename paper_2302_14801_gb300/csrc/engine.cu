@@ -533,7 +533,7 @@ SharedBuffers::~SharedBuffers() {
   if (cudaGetDevice(&prev) != cudaSuccess) return;
   cudaSetDevice(device);
   cudaStream_t fs = free_stream();
-  for (void* q : {points, index, nodes, voxels, input})
+  for (void* q : {points, index, nodes, voxels, voxel_points, input})
     if (q) cudaFreeAsync(q, fs);
   cudaSetDevice(prev);
 }
@@ -543,6 +543,9 @@ bool valid_mode(uint32_t mode) {
 }
 
 bool valid_params(const lod_params_t& p) {
+  const bool single = p.mode == LOD_PICK || p.mode == LOD_FIRST || p.mode == LOD_RANDOM;
+  if (p.flags & ~(uint32_t)(LOD_FLAG_LEAF_INDEX | LOD_FLAG_FULL_PRECISION)) return false;
+  if ((p.flags & LOD_FLAG_FULL_PRECISION) && !single) return false;
   return p.leaf_threshold != 0 && valid_mode(p.mode) && p.max_depth <= 32;
 }
 
@@ -1240,6 +1243,16 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
     std::swap(exact.bytes, d_dense.bytes);
     dense_cap = std::max<uint64_t>(V, 1);
   }
+  // full-precision variant: the picked input points, parallel to the voxels
+  DevBuf d_vpts(st);  // result
+  if ((prm.flags & LOD_FLAG_FULL_PRECISION) && V) {
+    uint32_t max_nodes = 0;
+    for (uint32_t t = 0; t < nt; ++t) max_nodes = std::max(max_nodes, n_nodes[t]);
+    LOD_CK(d_vpts.alloc(dense_cap * 16));
+    LOD_LAUNCH("voxel_points", 32.0 * V,
+               launch_voxel_points(d_tiles.as<TileDesc>(), nt, d_nodes.as<lod_node_t>(), d_nn.as<uint32_t>(), max_nodes,
+                                   d_dense.as<int4>(), d_vpts.as<int4>(), st));
+  }
   up_.recycle();
   prof.resolve();
 
@@ -1254,7 +1267,9 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
     r.n_levels = n_levels[t];
     r.n_voxels = tvox[t];
   }
-  sh->bytes = M * 16 + (want_idx ? M * 4 : 0) + total_cap * sizeof(lod_node_t) + dense_cap * 16;
+  sh->bytes = M * 16 + (want_idx ? M * 4 : 0) + total_cap * sizeof(lod_node_t) + dense_cap * 16 +
+              (d_vpts.p ? dense_cap * 16 : 0);
+  sh->voxel_points = d_vpts.take();
   sh->points = d_points.take();
   sh->index = want_idx ? d_index.take() : nullptr;
   sh->nodes = d_nodes.take();

@@ -18,6 +18,7 @@ struct SharedBuffers {
   void* index = nullptr;    // original indices (or null)
   void* nodes = nullptr;    // node tables of all tiles
   void* voxels = nullptr;   // voxels of all tiles
+  void* voxel_points = nullptr;  // full-precision picked points, parallel to voxels (or null)
   void* input = nullptr;    // owned copy of host input (lod_build_from_host), or null
   uint64_t bytes = 0;
   ~SharedBuffers();

@@ -847,6 +847,37 @@ cudaError_t launch_unwide(const BuildArgs& a, const uint32_t* tiles, uint32_t n_
   return cudaGetLastError();
 }
 
+// Full-precision variant (Section 7): the input point each voxel of a
+// single-sample mode picked, gathered from the caller's input into an
+// array parallel to the voxel array.  blockIdx.y selects the tile.
+__global__ void __launch_bounds__(256) k_voxel_points(const TileDesc* __restrict__ tiles,
+                                                      const lod_node_t* __restrict__ nodes,
+                                                      const uint32_t* __restrict__ n_nodes,
+                                                      const int4* __restrict__ dense, int4* __restrict__ out) {
+  const TileDesc& td = tiles[blockIdx.y];
+  const uint32_t nn = n_nodes[blockIdx.y];
+  for (uint32_t i = blockIdx.x; i < nn; i += gridDim.x) {
+    const lod_node_t& nd = nodes[td.node_base + i];
+    for (uint32_t j = threadIdx.x; j < nd.voxel_count; j += blockDim.x) {
+      const uint32_t pick = (uint32_t)dense[nd.voxel_offset + j].w;
+      out[nd.voxel_offset + j] = pick < td.n ? td.in[pick] : make_int4(0, 0, 0, 0);
+    }
+  }
+}
+
+cudaError_t launch_voxel_points(const TileDesc* tiles, uint32_t n_tiles, const lod_node_t* nodes,
+                                const uint32_t* n_nodes, uint32_t max_nodes, const int4* dense, int4* out,
+                                cudaStream_t st) {
+  if (!n_tiles || !max_nodes) return cudaSuccess;
+  const uint32_t gx = max_nodes < 4096 ? max_nodes : 4096;
+  for (uint32_t t0 = 0; t0 < n_tiles; t0 += 65535) {
+    const uint32_t m = n_tiles - t0 < 65535 ? n_tiles - t0 : 65535;
+    k_voxel_points<<<dim3(gx, m), 256, 0, st>>>(tiles + t0, nodes, n_nodes + t0, dense, out);
+    note_launch();
+  }
+  return cudaGetLastError();
+}
+
 // Gather each node's voxels to a new offset (compact per-result copies).
 __global__ void __launch_bounds__(256) k_gather_voxels(const lod_node_t* __restrict__ nodes,
                                                        const uint64_t* __restrict__ new_off,

@@ -67,6 +67,9 @@ cudaError_t launch_level_scan(const BuildArgs& a, const VoxLevel& v, const uint3
 cudaError_t launch_copy_items(const BuildArgs& a, const VoxLevel& v, cudaStream_t st);
 cudaError_t launch_unwide(const BuildArgs& a, const uint32_t* tiles, uint32_t n_tiles, uint32_t max_points,
                           cudaStream_t st);
+cudaError_t launch_voxel_points(const TileDesc* tiles, uint32_t n_tiles, const lod_node_t* nodes,
+                                const uint32_t* n_nodes, uint32_t max_nodes, const int4* dense, int4* out,
+                                cudaStream_t st);
 cudaError_t launch_gather_voxels(const lod_node_t* nodes, uint32_t n_nodes, const uint64_t* new_off,
                                  const int4* src, int4* dst, cudaStream_t st);
 

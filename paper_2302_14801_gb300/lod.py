@@ -30,6 +30,7 @@ FIRST = 3
 RANDOM = 4
 MODES = {"filter": FILTER, "filtered": FILTER, "pick": PICK, "weighted": WEIGHTED, "first": FIRST, "random": RANDOM}
 FLAG_LEAF_INDEX = 1
+FLAG_FULL_PRECISION = 2
 NODE_LEAF = 1
 NODE_OVERFULL = 2
 
@@ -39,7 +40,7 @@ EXPORTED = [
     "lod_server_create", "lod_submit", "lod_poll", "lod_wait", "lod_server_bytes_in_use",
     "lod_server_destroy", "lod_profile_enable", "lod_profile_reset", "lod_profile_read", "lod_launch_count",
     "lod_root_cubes_noalloc", "lod_set_tuning", "lod_get_tuning", "lod_autotune", "lod_scratch_bytes",
-    "lod_trim",
+    "lod_trim", "lod_result_voxel_points", "lod_result_copy_voxel_points_to_host",
 ]
 
 
@@ -123,6 +124,8 @@ def _load():
         "lod_autotune": (i, [vp, u64, P(Params), vp, P(Tuning), P(ctypes.c_float)]),
         "lod_scratch_bytes": (u64, [vp]),
         "lod_trim": (i, [vp]),
+        "lod_result_voxel_points": (i, [vp, P(vp)]),
+        "lod_result_copy_voxel_points_to_host": (i, [vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -145,10 +148,11 @@ def error_string(status: int) -> str:
     return lib().lod_error_string(status).decode()
 
 
-def make_params(leaf_threshold=50000, mode=FILTER, max_depth=21, keep_index=False) -> Params:
+def make_params(leaf_threshold=50000, mode=FILTER, max_depth=21, keep_index=False, full_precision=False) -> Params:
     if isinstance(mode, str):
         mode = MODES[mode]
-    return Params(int(leaf_threshold), int(mode), int(max_depth), FLAG_LEAF_INDEX if keep_index else 0)
+    flags = (FLAG_LEAF_INDEX if keep_index else 0) | (FLAG_FULL_PRECISION if full_precision else 0)
+    return Params(int(leaf_threshold), int(mode), int(max_depth), flags)
 
 
 def _check(rc, what):
@@ -294,6 +298,16 @@ class Result:
             "voxel_count": nodes["voxel_count"].copy(), "points": pts, "index": idx, "voxels": vox,
         }
 
+    def voxel_points_host(self, stream=None) -> np.ndarray:
+        """lod_result_copy_voxel_points_to_host: the full-precision picked
+        points ((V, 4) int32), in the voxel order of ``to_host()``."""
+        v = self.view()
+        out = np.empty((v.n_voxels, 4), np.int32)
+        _check(lib().lod_result_copy_voxel_points_to_host(self._h, out.ctypes.data if v.n_voxels else None,
+                                                          _stream_handle(stream)),
+               "lod_result_copy_voxel_points_to_host")
+        return out
+
     def free(self):
         if self._h:
             lib().lod_free(self._h)
@@ -316,10 +330,11 @@ def _dev_ptr(points):
     return points.data_ptr(), points.shape[0]
 
 
-def build(points, leaf_threshold=50000, mode=FILTER, max_depth=21, keep_index=False, stream=None) -> Result:
+def build(points, leaf_threshold=50000, mode=FILTER, max_depth=21, keep_index=False, stream=None,
+          full_precision=False) -> Result:
     """lod_build on a CUDA int32 (N, 4) tensor of (x, y, z, rgba) rows."""
     ptr, n = _dev_ptr(points)
-    p = make_params(leaf_threshold, mode, max_depth, keep_index)
+    p = make_params(leaf_threshold, mode, max_depth, keep_index, full_precision)
     h = ctypes.c_void_p()
     _check(lib().lod_build(ptr if n else None, n, ctypes.byref(p), _stream_handle(stream), ctypes.byref(h)),
            "lod_build")

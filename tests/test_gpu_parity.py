@@ -374,3 +374,31 @@ def test_wait_times_out_and_the_request_still_completes(lod):
     finally:
         srv.close()
     compare(got, oracle.build(small_np, 20000, 1, 21), inp=small_np)
+
+
+# ------------------------------------------- full-precision variant (Section 7)
+
+@pytest.mark.parametrize("mode", [1, 3, 4])
+def test_full_precision_voxel_points(lod, mode):
+    # each voxel also carries the input point it picked, unquantised: the
+    # input record at its pick_index, lying inside the voxel's cell
+    import torch
+    pts = synth.aerial(500_000, seed=44, n_buildings=20)
+    d = torch.from_numpy(pts).cuda()
+    r = lod.build(d, 5000, mode, full_precision=True)
+    got = r.to_host()
+    vp = r.voxel_points_host()
+    r.free()
+    compare(got, oracle.build(pts, 5000, mode, 21), inp=pts)
+    vox = got["voxels"]
+    assert np.array_equal(vp, pts[vox[:, 3].astype(np.int64)])
+    for i in np.nonzero(got["voxel_count"])[0]:
+        a, c = int(got["voxel_offset"][i]), int(got["voxel_count"][i])
+        dd = vp[a:a + c, :3].astype(np.int64) - got["min"][i].astype(np.int64)
+        L = int(got["log2_size"][i])
+        q = (dd >> (L - 7)) if L >= 7 else (dd << (7 - L))
+        assert np.array_equal(q[:, 0] | (q[:, 1] << 7) | (q[:, 2] << 14), vox[a:a + c, 0].astype(np.int64))
+    for m in (0, 2):  # the averaging modes have no single picked point
+        with pytest.raises(lod.LodError) as e:
+            lod.build(d, 5000, m, full_precision=True)
+        assert e.value.status == lod.LOD_ERR_INVALID_ARG
