@@ -319,6 +319,46 @@ int lod_get_tuning(lod_tuning_t* t);
 int lod_autotune(const lod_point_t* d_points, uint64_t n, const lod_params_t* params, void* stream,
                  lod_tuning_t* best, float* best_ms);
 
+/* ------------------------------------------------------------ rendering */
+
+/* Camera of lod_render.  A sample at integer position p is projected as
+ * clip = view_proj * (p - origin, 1) with view_proj row-major (clip.x is
+ * row 0 . (p - origin, 1)); it is drawn when clip.w > 0 and x/w, y/w, z/w
+ * all lie in [-1, 1], at pixel floor((x/w * 0.5 + 0.5) * width),
+ * floor((y/w * 0.5 + 0.5) * height) (clamped to the last row / column).
+ * lod_pixels is the refinement threshold of Section 5 (a node's children
+ * are considered when its projected bounding box spans more than this many
+ * pixels; 0 selects 100, the paper's value for a 128^3 grid). */
+typedef struct lod_camera {
+  float view_proj[16];
+  int32_t origin[3];
+  uint32_t width, height;
+  float lod_pixels;
+  uint32_t reserved[2];
+} lod_camera_t;
+
+typedef struct lod_render_stats {
+  uint32_t visible_nodes;  /* nodes drawn */
+  uint32_t reserved;
+  uint64_t samples_drawn;  /* voxels and points that reached a pixel */
+} lod_render_stats_t;
+
+/* Render result r into a headless framebuffer (Section 5, restated as CUDA
+ * kernels instead of draw calls).  A node is drawn when it is at least
+ * partly inside the view frustum and every ancestor is drawn and projects
+ * larger than lod_pixels; a drawn inner node draws its voxels (at their
+ * cell centres) except those in an octant whose child is drawn, a drawn
+ * leaf draws its points.  Each pixel of d_framebuffer (device,
+ * width * height uint64, row-major, 8-byte aligned, caller-owned) receives
+ * the smallest key (float bits of depth) << 32 | rgba over the samples
+ * landing there, depth = z/w * 0.5 + 0.5 in [0, 1], or 0xFFFFFFFFFFFFFFFF
+ * where none does; the call overwrites every pixel.  Single-precision arithmetic with every operation rounded on
+ * its own, so images are reproducible bit for bit.  Asynchronous on
+ * `stream` unless stats is not NULL (it then waits for the counts).
+ * Errors: LOD_ERR_INVALID_ARG, LOD_ERR_OOM, LOD_ERR_CUDA. */
+int lod_render(const lod_result_t* r, const lod_camera_t* cam, uint64_t* d_framebuffer, void* stream,
+               lod_render_stats_t* stats);
+
 /* ------------------------------------------------------------ profiling */
 
 /* Per-kernel statistics accumulated by the library while profiling is on:

@@ -18,6 +18,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lod_oracle.cpp")
+_SRCS = [_SRC, os.path.join(_HERE, "render_oracle.cpp")]
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 _lib = None
 
@@ -29,11 +30,15 @@ RANDOM = 4    # random pick with the key of Listing 1 (Section 4.2.2), bottom up
 
 
 def compile_oracle(force: bool = False) -> str:
-    """Compile the oracle with g++ (plain -O2, no target-specific flags)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile the oracle with g++ (plain -O2, no target-specific flags, no
+    floating-point contraction: the rasteriser's pixel decisions depend on
+    every single-precision operation being rounded on its own)."""
+    newest = max(os.path.getmtime(f) for f in _SRCS + [os.path.abspath(__file__)])
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         os.makedirs(os.path.dirname(_LIB), exist_ok=True)
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC", "-o", tmp,
+                               *_SRCS])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -68,6 +73,11 @@ def _load():
         lib.oracle_weighted_node.argtypes = [ctypes.c_void_p, ctypes.c_uint64, u32p, u8p, ctypes.c_uint64, i32p,
                                              ctypes.c_uint32, u32p]
         lib.oracle_weighted_node.restype = ctypes.c_int64
+        f32p = ctypes.POINTER(ctypes.c_float)
+        lib.oracle_render.argtypes = [ctypes.c_uint32, i32p, u8p, u8p, u8p, u32p, u32p, u64p, u64p, u64p, u32p,
+                                      u32p, i32p, f32p, i32p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_float,
+                                      u64p, u8p]
+        lib.oracle_render.restype = ctypes.c_int64
         lib.oracle_random_key.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
         lib.oracle_random_key.restype = ctypes.c_uint64
         lib.oracle_cube_voxels.argtypes = [ctypes.c_void_p, u32p, ctypes.c_uint64, i32p, ctypes.c_uint32,
@@ -188,3 +198,37 @@ def weighted_node(points: np.ndarray, voxels: np.ndarray, octants: np.ndarray, c
     if nv < 0:
         raise ValueError("oracle_weighted_node: invalid arguments")
     return out[:nv].copy()
+
+
+def render(res: dict, view_proj, origin, width: int, height: int, threshold: float = 100.0):
+    """Rasterise an LOD octree (a result dictionary as ``build`` returns it)
+    into a headless framebuffer (rendering of Section 5, see
+    render_oracle.cpp).  Returns (framebuffer (height, width) uint64 keys of
+    the bits of depth (z/w / 2 + 1/2) << 32 | rgba, ~0 where nothing was
+    drawn; drawn node flags; samples drawn)."""
+    lib = _load()
+    n = len(res["level"])
+    m = np.ascontiguousarray(np.asarray(view_proj, dtype=np.float32).reshape(16))
+    org = np.ascontiguousarray(np.asarray(origin, dtype=np.int32).reshape(3))
+    fb = np.empty((height, width), np.uint64)
+    vis = np.zeros(n, np.uint8)
+    arr = {k: np.ascontiguousarray(res[k]) for k in ("min", "log2_size", "child_mask", "flags", "parent",
+                                                     "first_child", "point_offset", "point_count",
+                                                     "voxel_offset", "voxel_count")}
+    vox = np.ascontiguousarray(np.asarray(res["voxels"], dtype=np.uint32).reshape(-1, 4))
+    pts = np.ascontiguousarray(np.asarray(res["points"], dtype=np.int32).reshape(-1, 4))
+    if len(vox) == 0:
+        vox = np.zeros((1, 4), np.uint32)
+    if len(pts) == 0:
+        pts = np.zeros((1, 4), np.int32)
+    drawn = lib.oracle_render(n, _ptr(arr["min"], ctypes.c_int32), _ptr(arr["log2_size"], ctypes.c_uint8),
+                              _ptr(arr["child_mask"], ctypes.c_uint8), _ptr(arr["flags"], ctypes.c_uint8),
+                              _ptr(arr["parent"], ctypes.c_uint32), _ptr(arr["first_child"], ctypes.c_uint32),
+                              _ptr(arr["point_offset"], ctypes.c_uint64), _ptr(arr["point_count"], ctypes.c_uint64),
+                              _ptr(arr["voxel_offset"], ctypes.c_uint64), _ptr(arr["voxel_count"], ctypes.c_uint32),
+                              _ptr(vox, ctypes.c_uint32), _ptr(pts, ctypes.c_int32), _ptr(m, ctypes.c_float),
+                              _ptr(org, ctypes.c_int32), int(width), int(height), float(threshold),
+                              _ptr(fb, ctypes.c_uint64), _ptr(vis, ctypes.c_uint8))
+    if drawn < 0:
+        raise ValueError("oracle_render: invalid arguments")
+    return fb, vis, int(drawn)

@@ -2,6 +2,7 @@
 // result objects, host copies and the serving loop.
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -20,6 +21,8 @@ static_assert(sizeof(lod_node_t) == 56, "node record is 56 bytes");
 static_assert(sizeof(lod_voxel_t) == 16, "voxel record is 16 bytes");
 static_assert(sizeof(lod_view_t) == 64, "view is 64 bytes");
 static_assert(sizeof(lod_params_t) == 16, "params are 16 bytes");
+static_assert(sizeof(lod_camera_t) == 96, "camera is 96 bytes");
+static_assert(sizeof(lod_render_stats_t) == 16, "render stats are 16 bytes");
 
 namespace {
 
@@ -237,6 +240,52 @@ int lod_result_copy_voxel_points_to_host(const lod_result_t* r, lod_point_t* poi
   if (d_tmp) cudaFreeAsync(d_tmp, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return to_status(e);
+}
+
+int lod_render(const lod_result_t* r, const lod_camera_t* cam, uint64_t* d_framebuffer, void* stream,
+               lod_render_stats_t* stats) {
+  if (!r || !cam || !d_framebuffer || (reinterpret_cast<uintptr_t>(d_framebuffer) & 7u)) return LOD_ERR_INVALID_ARG;
+  if (cam->width == 0 || cam->height == 0 || (uint64_t)cam->width * cam->height > (1ull << 31) ||
+      !(cam->lod_pixels >= 0.0f))
+    return LOD_ERR_INVALID_ARG;
+  for (float f : cam->view_proj)
+    if (!std::isfinite(f)) return LOD_ERR_INVALID_ARG;
+  lod_camera_t c = *cam;
+  if (c.lod_pixels == 0.0f) c.lod_pixels = 100.0f;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  lod_view_t v;
+  lod_result_view(r, &v);
+  const uint64_t pixels = (uint64_t)c.width * c.height;
+  cudaError_t e = cudaMemsetAsync(d_framebuffer, 0xFF, pixels * 8, st);
+  if (e != cudaSuccess) return to_status(e);
+  // scratch: drawn-node flags and two counters
+  void* scratch = nullptr;
+  const size_t cnt_off = ((size_t)v.n_nodes + 15) & ~size_t(15);
+  e = cudaMallocAsync(&scratch, cnt_off + 16, st);
+  if (e != cudaSuccess) return to_status(e);
+  unsigned long long* drawn = reinterpret_cast<unsigned long long*>(static_cast<char*>(scratch) + cnt_off);
+  unsigned int* n_vis = reinterpret_cast<unsigned int*>(drawn + 1);
+  e = cudaMemsetAsync(drawn, 0, 16, st);
+  int dev = 0, sms = 1;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = lodk::launch_render(v.nodes, v.n_nodes, reinterpret_cast<const int4*>(v.points),
+                            reinterpret_cast<const int4*>(v.voxels), c, static_cast<uint8_t*>(scratch), n_vis,
+                            reinterpret_cast<unsigned long long*>(d_framebuffer), drawn, sms, st);
+  unsigned long long host[2] = {0, 0};
+  if (e == cudaSuccess && stats) {
+    e = cudaMemcpyAsync(host, drawn, 16, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  cudaFreeAsync(scratch, st);
+  if (e != cudaSuccess) return to_status(e);
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->samples_drawn = host[0];
+    stats->visible_nodes = (uint32_t)host[1];
+  }
+  return LOD_OK;
 }
 
 uint64_t lod_result_device_bytes(const lod_result_t* r) { return r ? r->bytes : 0; }

@@ -75,4 +75,9 @@ cudaError_t launch_gather_voxels(const lod_node_t* nodes, uint32_t n_nodes, cons
 
 int vox_smem_bytes();
 
+// ----- rendering (Section 5) -----
+cudaError_t launch_render(const lod_node_t* nodes, uint32_t n_nodes, const int4* points, const int4* voxels,
+                          const lod_camera_t& cam, uint8_t* visible, unsigned int* n_visible,
+                          unsigned long long* fb, unsigned long long* drawn, int sms, cudaStream_t st);
+
 }  // namespace lodk

@@ -40,7 +40,7 @@ EXPORTED = [
     "lod_server_create", "lod_submit", "lod_poll", "lod_wait", "lod_server_bytes_in_use",
     "lod_server_destroy", "lod_profile_enable", "lod_profile_reset", "lod_profile_read", "lod_launch_count",
     "lod_root_cubes_noalloc", "lod_set_tuning", "lod_get_tuning", "lod_autotune", "lod_scratch_bytes",
-    "lod_trim", "lod_result_voxel_points", "lod_result_copy_voxel_points_to_host",
+    "lod_trim", "lod_result_voxel_points", "lod_result_copy_voxel_points_to_host", "lod_render",
 ]
 
 
@@ -72,6 +72,16 @@ class ServerConfig(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("root_depth", ctypes.c_uint32), ("stream_ctas_per_sm", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32 * 6)]
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("view_proj", ctypes.c_float * 16), ("origin", ctypes.c_int32 * 3), ("width", ctypes.c_uint32),
+                ("height", ctypes.c_uint32), ("lod_pixels", ctypes.c_float), ("reserved", ctypes.c_uint32 * 2)]
+
+
+class RenderStats(ctypes.Structure):
+    _fields_ = [("visible_nodes", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("samples_drawn", ctypes.c_uint64)]
 
 
 class KernelStat(ctypes.Structure):
@@ -125,6 +135,7 @@ def _load():
         "lod_scratch_bytes": (u64, [vp]),
         "lod_trim": (i, [vp]),
         "lod_result_voxel_points": (i, [vp, P(vp)]),
+        "lod_render": (i, [vp, P(Camera), vp, vp, P(RenderStats)]),
         "lod_result_copy_voxel_points_to_host": (i, [vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -339,6 +350,36 @@ def build(points, leaf_threshold=50000, mode=FILTER, max_depth=21, keep_index=Fa
     _check(lib().lod_build(ptr if n else None, n, ctypes.byref(p), _stream_handle(stream), ctypes.byref(h)),
            "lod_build")
     return Result(h.value)
+
+
+def make_camera(view_proj, origin, width: int, height: int, lod_pixels: float = 100.0) -> Camera:
+    m = np.ascontiguousarray(np.asarray(view_proj, dtype=np.float32).reshape(16))
+    c = Camera()
+    c.view_proj[:] = [float(x) for x in m]
+    c.origin[:] = [int(x) for x in np.asarray(origin).reshape(3)]
+    c.width, c.height, c.lod_pixels = int(width), int(height), float(lod_pixels)
+    return c
+
+
+def render(result: "Result", view_proj, origin, width: int, height: int, lod_pixels: float = 100.0, out=None,
+           stream=None, stats: bool = False):
+    """lod_render: rasterise ``result`` into a CUDA int64 tensor (height,
+    width) of keys (bits of depth in [0, 1] << 32 | rgba; -1 where nothing
+    was drawn).
+    With ``stats`` returns (framebuffer, {"visible_nodes", "samples_drawn"})."""
+    import torch
+    if out is None:
+        out = torch.empty((height, width), dtype=torch.int64, device="cuda")
+    if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.int64 and out.is_contiguous()
+            and tuple(out.shape) == (height, width)):
+        raise TypeError("out must be a contiguous CUDA int64 tensor of shape (height, width)")
+    cam = make_camera(view_proj, origin, width, height, lod_pixels)
+    st = RenderStats()
+    _check(lib().lod_render(result.handle, ctypes.byref(cam), out.data_ptr(), _stream_handle(stream),
+                            ctypes.byref(st) if stats else None), "lod_render")
+    if stats:
+        return out, {"visible_nodes": int(st.visible_nodes), "samples_drawn": int(st.samples_drawn)}
+    return out
 
 
 def build_from_host(points, leaf_threshold=50000, mode=FILTER, max_depth=21, keep_index=False,

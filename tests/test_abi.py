@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -78,6 +79,10 @@ def test_invalid_arguments_rejected_on_host(lodmod):
     assert L.lod_root_cubes_noalloc(tiles, ns, 0, dev, None) == lodmod.LOD_ERR_INVALID_ARG
     assert L.lod_root_cubes_noalloc(tiles, ns, 1, ctypes.c_void_p((1 << 20) + 2), None) == lodmod.LOD_ERR_INVALID_ARG
     assert L.lod_autotune(None, 10, None, None, None, None) == lodmod.LOD_ERR_INVALID_ARG
+    cam = lodmod.make_camera(np.eye(4, dtype=np.float32), [0, 0, 0], 8, 8)
+    assert L.lod_render(None, ctypes.byref(cam), dev, None, None) == lodmod.LOD_ERR_INVALID_ARG
+    assert L.lod_result_voxel_points(None, None) == lodmod.LOD_ERR_INVALID_ARG
+    assert L.lod_result_copy_voxel_points_to_host(None, None, None) == lodmod.LOD_ERR_INVALID_ARG
     assert L.lod_profile_read(None, 0, None) == lodmod.LOD_ERR_INVALID_ARG
 
 
