@@ -497,6 +497,8 @@ def main():
     ap.add_argument("--workload", default="indoor1b", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra-modes", action="store_true", help="skip timing the weighted / first / random modes")
+    ap.add_argument("--no-render", action="store_true", help="skip timing the rasteriser")
     ap.add_argument("--suite", default="single", choices=["single", "batched", "serve"],
                     help="single: the headline line; batched: many independent tiles per launch "
                          "(lod_build_batched); serve: Poisson request stream through lod_submit/lod_poll")
@@ -624,6 +626,62 @@ def main():
         kern[k]["share"] = prof[k]["total_ms"] / tot
     roof = roofline_of(prof, name, pk)
 
+    # the other sampling modes, timed one build at a time outside the step
+    # (weighted average, first come, random with Listing 1's key)
+    extra = {}
+    if not args.no_extra_modes:
+        for mode, key in ((2, "weighted"), (3, "first"), (4, "random")):
+            lat = []
+            vox = root_vox = None
+            for it in range(4):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                r = lod.build(d, T, mode, 21, stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                if it == 0:
+                    vv = r.view()
+                    vox = int(vv.n_voxels)
+                    root_vox = int(r.tensors()["nodes"][0, 12].item())  # voxel_count of the root
+                else:
+                    lat.append(a.elapsed_time(b))
+                r.free()
+            med = statistics.median(lat)
+            ba = b_alg(n, vox, root_vox)
+            extra[key] = {"ms_p50": med, "mpts_per_s": n / (med * 1e-3) / 1e6, "voxels": vox, "alg_bytes": ba,
+                          "hbm_frac": (ba / (med * 1e-3) / 1e9) / pk["hbm_gbs"], "builds_timed": len(lat),
+                          "in_step": False}
+    # rendering (Section 5): full-HD frames of the pick-mode octree
+    render = None
+    if not args.no_render:
+        from paper_2302_14801_gb300 import camera
+        r = lod.build(d, T, lod.PICK, 21, stream=stream)
+        hn = r.to_host()
+        L = int(hn["log2_size"][0])
+        lo = hn["min"][0].astype(np.int64)
+        c = lo + (1 << (L - 1))
+        cams = {"overview": camera.perspective(c + [2 << L, -(1 << L), 1 << L], c, fovy_deg=50, aspect=16 / 9,
+                                               near=1, far=1e9),
+                "close": camera.perspective(c + [1 << (L - 4), 1 << (L - 5), 1 << (L - 4)], c, fovy_deg=70,
+                                            aspect=16 / 9, near=1, far=1e9)}
+        fb = torch.empty((1080, 1920), dtype=torch.int64, device="cuda")
+        render = {"width": 1920, "height": 1080, "lod_pixels": 100.0}
+        for cname, (m, org) in cams.items():
+            _, stt = lod.render(r, m, org, 1920, 1080, 100.0, out=fb, stream=stream, stats=True)
+            times = []
+            for _ in range(10):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                lod.render(r, m, org, 1920, 1080, 100.0, out=fb, stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                times.append(a.elapsed_time(b))
+            render[cname] = {"ms_p50": statistics.median(times), "visible_nodes": stt["visible_nodes"],
+                             "samples_drawn": stt["samples_drawn"]}
+        r.free()
+
     # end to end through the host-buffer call: H2D of the input + build + D2H of the octree
     e2e = None
     if not args.no_e2e:
@@ -672,7 +730,8 @@ def main():
                                    f"{', drawn on the device' if on_device(name) else ''}), T={T}, 128^3 grid; "
                                    "step = 1 filtered + 1 pick build, input resident in HBM",
                        "l2": f"inputs ({n * 16 / 1e6:.0f} MB) larger than L2; no flush", "replicas": world},
-            "modes": per_mode, "roofline": roof, "kernels": kern, "gpu_launches": launches,
+            "modes": per_mode, "modes_extra": extra, "render": render, "roofline": roof, "kernels": kern,
+            "gpu_launches": launches,
             "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
