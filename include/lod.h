@@ -261,6 +261,35 @@ const char* lod_error_string(int status);
 uint64_t lod_scratch_bytes(void* stream);
 int lod_trim(void* stream);
 
+/* --------------------------------------------------------- out of core */
+
+/* Out-of-core build (Section 7: a cloud too large to build in device memory
+ * at once is split into chunks that are built one batch at a time, and the
+ * coarsest nodes above the chunks are filled afterwards).
+ *   chunk_points   the largest chunk (subtree) built at once; >= T; 0: 10M.
+ *                  A chunk root is a node of at most chunk_points points, a
+ *                  leaf of the octree, or a node 8 levels below the root
+ *                  (such chunks may be larger).
+ *   stream_points  points moved host -> device per transfer (0: 16M).
+ *   batch_points   points of the chunks built together (0: 256M). */
+typedef struct lod_ooc_config {
+  uint64_t chunk_points;
+  uint64_t stream_points;
+  uint64_t batch_points;
+} lod_ooc_config_t;
+
+/* Build the LOD octree of n points in host memory (h_points, read three
+ * times: bounding box, top-level counts, partition into chunks) holding
+ * only the output and one batch of chunks under construction in device
+ * memory.  The result is identical to lod_build of the same points
+ * (pick_index and leaf indices are input indices of the whole cloud) and
+ * is used like any other result.  Uses page-locked host memory of 20 bytes
+ * per point for the partitioned chunks.  LOD_FLAG_FULL_PRECISION is not
+ * supported here (LOD_ERR_INVALID_ARG).  Blocks until done.
+ * Errors: LOD_ERR_INVALID_ARG, LOD_ERR_OOM, LOD_ERR_CUDA, LOD_ERR_INTERNAL. */
+int lod_build_out_of_core(const lod_point_t* h_points, uint64_t n, const lod_params_t* params,
+                          const lod_ooc_config_t* cfg, void* stream, lod_result_t** out);
+
 /* ------------------------------------------------------- no allocation */
 
 /* Root cube of each of n_tiles point clouds, computed without allocating

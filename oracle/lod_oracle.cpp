@@ -48,7 +48,10 @@
 //    A sample adds weight max(0, 1 - distance to the cell centre, in cells)
 //    times its colour to the cells of the 2x2x2 block around it and marks
 //    the cell it lies in as occupied; an occupied cell's colour is its
-//    weighted sum over its weight sum.  Arithmetic in double precision.
+//    weighted sum over its weight sum, rounded half up.  The paper fixes no
+//    precision; the weights are taken in the kernel's (single precision,
+//    rounded to multiples of 2^-24), since the rounding of the mean is an
+//    integer decision both sides must take alike.
 //
 // Function-level citations are beside each function.
 
@@ -265,10 +268,15 @@ struct Builder {
   // Section 4.2.4: one inner node's voxels under the neighbourhood-weighted
   // average, from its children's samples (their voxels must exist already).
   // Positions are in units of the node's grid cells, so the node's cube is
-  // [0, 128)^3 and cell j has its centre at j + 1/2.
+  // [0, 128)^3 and cell j has its centre at j + 1/2.  The paper fixes no
+  // precision, and the rounding of the mean is an integer decision, so the
+  // weights are taken in the precision the kernel uses: single precision
+  // with every operation rounded on its own, then rounded to a multiple of
+  // 2^-24 (ties to even); the weighted sums are exact integers and the mean
+  // is rounded half up exactly.
   struct WCell {
-    double r = 0, g = 0, b = 0, w = 0;  // weighted colour sums, weight sum
-    uint64_t count = 0;                 // original points in the cell
+    uint64_t r = 0, g = 0, b = 0, w = 0;  // weighted colour sums, weight sum (units of 2^-24)
+    uint64_t count = 0;                   // original points in the cell
     bool occupied = false;
   };
   static void add_weighted(std::map<uint32_t, WCell>& cells, const double pos[3], const uint32_t own[3],
@@ -277,28 +285,37 @@ struct Builder {
     home.occupied = true;
     home.count += count;
     // the cells whose centres lie within one cell width along every axis:
-    // floor(pos - 1/2) and the next one, inside the grid
+    // floor(pos - 1/2) and the next one, inside the grid; the offset to the
+    // first is exact in double and rounded once to single precision, the
+    // offset to the second is that minus one in single precision
     int64_t lo[3];
-    for (int a = 0; a < 3; ++a) lo[a] = (int64_t)std::floor(pos[a] - 0.5);
+    float e0[3];
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = (int64_t)std::floor(pos[a] - 0.5);
+      e0[a] = (float)(pos[a] - ((double)lo[a] + 0.5));
+    }
     for (int dz = 0; dz < 2; ++dz)
       for (int dy = 0; dy < 2; ++dy)
         for (int dx = 0; dx < 2; ++dx) {
           const int64_t j[3] = {lo[0] + dx, lo[1] + dy, lo[2] + dz};
+          const int dd[3] = {dx, dy, dz};
           bool inside = true;
-          double d2 = 0;
+          float e[3];
           for (int a = 0; a < 3; ++a) {
             if (j[a] < 0 || j[a] > 127) inside = false;
-            const double e = pos[a] - ((double)j[a] + 0.5);
-            d2 += e * e;
+            e[a] = dd[a] ? e0[a] - 1.0f : e0[a];
           }
           if (!inside) continue;
-          const double w = 1.0 - std::sqrt(d2);  // linear weight, zero beyond one cell
-          if (w <= 0) continue;
+          const float d2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+          if (!(d2 < 1.0f)) continue;  // linear weight, zero from one cell on
+          const float w = 1.0f - std::sqrt(d2);
+          const uint64_t wq = (uint64_t)std::nearbyint(w * 16777216.0f);
+          if (wq == 0) continue;
           WCell& c = cells[(uint32_t)j[0] | ((uint32_t)j[1] << 7) | ((uint32_t)j[2] << 14)];
-          c.r += w * (double)(rgba & 0xFFu);
-          c.g += w * (double)((rgba >> 8) & 0xFFu);
-          c.b += w * (double)((rgba >> 16) & 0xFFu);
-          c.w += w;
+          c.r += wq * (rgba & 0xFFu);
+          c.g += wq * ((rgba >> 8) & 0xFFu);
+          c.b += wq * ((rgba >> 16) & 0xFFu);
+          c.w += wq;
         }
   }
 
@@ -329,15 +346,16 @@ struct Builder {
     add_weighted(cells, pos, own, vx.rgba, vx.count);
   }
 
-  // Occupied cells only, in cell order; colour = weighted mean rounded to
-  // the nearest integer (halves up), alpha 255.
+  // Occupied cells only, in cell order; colour = weighted mean rounded half
+  // up (exact integer division), alpha 255.
   static void weighted_emit(const std::map<uint32_t, WCell>& cells, std::vector<OVoxel>& out) {
     for (const auto& kv : cells) {
       const WCell& wc = kv.second;
       if (!wc.occupied) continue;
-      auto channel = [&](double sum) {
-        const double m = std::floor(sum / wc.w + 0.5);
-        return (uint32_t)std::min(255.0, std::max(0.0, m));
+      auto channel = [&](uint64_t sum) {
+        const uint64_t q = sum / wc.w, rem = sum - q * wc.w;
+        const uint64_t m = q + (2 * rem >= wc.w ? 1u : 0u);
+        return (uint32_t)std::min<uint64_t>(m, 255);
       };
       OVoxel v;
       v.cell = kv.first;

@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblod.so")
-SOURCES = ["k_split.cu", "k_voxel.cu", "k_weighted.cu", "k_render.cu", "engine.cu", "api.cu", "no_alloc.cu"]
+SOURCES = ["k_split.cu", "k_voxel.cu", "k_weighted.cu", "k_render.cu", "k_ooc.cu", "ooc.cu", "engine.cu", "api.cu",
+           "no_alloc.cu"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 

@@ -15,6 +15,7 @@
 
 #include "engine.h"
 #include "kernels.h"
+#include "result.h"
 
 static_assert(sizeof(lod_point_t) == 16, "point record is 16 bytes");
 static_assert(sizeof(lod_node_t) == 56, "node record is 56 bytes");
@@ -25,22 +26,6 @@ static_assert(sizeof(lod_camera_t) == 96, "camera is 96 bytes");
 static_assert(sizeof(lod_render_stats_t) == 16, "render stats are 16 bytes");
 
 namespace {
-
-// Budget accounting shared between a server and the results it returned
-// (results may outlive the server).
-struct Budget {
-  std::mutex mu;
-  std::condition_variable cv;
-  uint64_t limit = 0;
-  uint64_t in_use = 0;
-  void release(uint64_t b) {
-    {
-      std::lock_guard<std::mutex> lk(mu);
-      in_use = b > in_use ? 0 : in_use - b;
-    }
-    cv.notify_all();
-  }
-};
 
 int to_status(cudaError_t e) {
   if (e == cudaSuccess) return LOD_OK;
@@ -57,25 +42,6 @@ lod_params_t defaults() {
 }
 
 }  // namespace
-
-struct lod_result {
-  std::shared_ptr<lodk::SharedBuffers> sh;
-  lodk::TileResult tr;
-  uint32_t mode = 0;
-  uint64_t bytes = 0;
-  std::shared_ptr<Budget> budget;  // set when a server accounts for this result
-};
-
-static lod_result_t* make_result(const std::shared_ptr<lodk::SharedBuffers>& sh, const lodk::TileResult& tr,
-                                 uint32_t mode, uint64_t share) {
-  lod_result_t* r = new (std::nothrow) lod_result_t();
-  if (!r) return nullptr;
-  r->sh = sh;
-  r->tr = tr;
-  r->mode = mode;
-  r->bytes = share;
-  return r;
-}
 
 extern "C" {
 

@@ -38,6 +38,9 @@ struct TileDesc {
   uint32_t node_cap;   // capacity of this tile's node region
   uint64_t pt_base;    // absolute base of the tile in the shared point buffers
   uint64_t node_base;  // absolute first node of the tile in the node buffer
+  const uint32_t* in_idx;  // input index of each input point, or null (the position)
+  uint32_t idx_bound;      // input indices are below this
+  uint32_t level0;         // octree level of the tile's root
 };
 
 // A counting grid ("source"): 8^d cells under one cube, the whole root for
@@ -161,6 +164,52 @@ __device__ __forceinline__ void ld_wide(const int4* p, int4& q, uint32_t& idx) {
   (void)u0;
   (void)u1;
   (void)u2;
+}
+
+// ---------------------------------------------------------- sampling rules
+
+// floor((s + n/2) / n) for a channel sum s of n 8-bit samples, i.e. the
+// mean rounded half up, which lies in [0, 255].  A single-precision
+// quotient is within 1 of it (relative error ~1e-7 on a value <= 255.5),
+// and one exact integer comparison each way settles it, avoiding a 64-bit
+// integer division.
+__device__ __forceinline__ uint32_t round_mean(uint64_t s, uint64_t n) {
+  const uint64_t num = s + (n >> 1);
+  uint32_t q = (uint32_t)__fdividef((float)num, (float)n);
+  q = q > 255u ? 255u : q;
+  if ((uint64_t)q * n > num) --q;
+  else if ((uint64_t)(q + 1) * n <= num) ++q;
+  return q;
+}
+
+__device__ __forceinline__ uint32_t mean_rgba(uint64_t r, uint64_t g, uint64_t b, uint64_t n) {
+  return round_mean(r, n) | (round_mean(g, n) << 8) | (round_mean(b, n) << 16) | 0xFF000000u;
+}
+
+// Key of a sample in the single-sample modes; every cell keeps the sample
+// of smallest key, and every key is below the empty entry's ~0 (the
+// splitmix64 preimage of ~0 is not a 32-bit index).  `level` is the level
+// of the node being filled.
+//  - LOD_PICK: splitmix64(input index) (replaces Listing 1 with an exact,
+//    order-independent rule).
+//  - LOD_FIRST: the input index itself: the first sample in input order
+//    (Section 4.2.1); a child's voxel carries its own first point, so the
+//    bottom-up merge keeps the cell's first point.
+//  - LOD_RANDOM: Listing 1 of Section 4.2.2: a 32-bit key holding the top
+//    12 bits of a random number drawn for the sample at this level above
+//    the low 20 bits of the sample's index, the largest key winning; equal
+//    keys go to the larger index.  The random number is the high half of
+//    splitmix64(level << 32 | index).  Minimising 2^64 - 2 - (key << 32 |
+//    index) maximises (key, index).
+template <int MODE>
+__device__ __forceinline__ uint64_t pick_key(uint32_t ix, uint32_t level) {
+  if (MODE == LOD_FIRST) return ix;
+  if (MODE == LOD_RANDOM) {
+    const uint32_t r = (uint32_t)(splitmix64(((uint64_t)level << 32) | ix) >> 32);
+    const uint64_t key = (r & 0xFFF00000u) | (ix & 0x000FFFFFu);
+    return 0xFFFFFFFFFFFFFFFEull - ((key << 32) | ix);
+  }
+  return splitmix64(ix);
 }
 
 }  // namespace lodk

@@ -533,7 +533,7 @@ SharedBuffers::~SharedBuffers() {
   if (cudaGetDevice(&prev) != cudaSuccess) return;
   cudaSetDevice(device);
   cudaStream_t fs = free_stream();
-  for (void* q : {points, index, nodes, voxels, voxel_points, input})
+  for (void* q : {points, index, nodes, voxels, voxel_points, root_sums, input})
     if (q) cudaFreeAsync(q, fs);
   cudaSetDevice(prev);
 }
@@ -620,7 +620,7 @@ constexpr int kRetryWithRoots = -100;  // internal: redo the build with root cub
 
 static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaStream_t st,
                           std::shared_ptr<SharedBuffers>* shared_out, std::vector<TileResult>* tiles_out,
-                          BuildStats* stats, bool use_workspace, bool sync_roots);
+                          BuildStats* stats, bool use_workspace, bool sync_roots, const BuildOptions& opt);
 
 // Builds normally go without a host round trip after the bounding box: the
 // root cubes are set on the device and the first grids' depths chosen from
@@ -629,15 +629,18 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
 // cubes read back first.
 int run_build(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaStream_t st,
               std::shared_ptr<SharedBuffers>* shared_out, std::vector<TileResult>* tiles_out, BuildStats* stats,
-              bool use_workspace) {
-  const int rc = run_build_impl(tin, nt, prm, st, shared_out, tiles_out, stats, use_workspace, false);
+              bool use_workspace, const BuildOptions& opt) {
+  // tiles with a prescribed cube take the path that sets the cubes on the host
+  bool given = false;
+  for (uint32_t t = 0; tin && t < nt; ++t) given = given || tin[t].cube != nullptr;
+  const int rc = run_build_impl(tin, nt, prm, st, shared_out, tiles_out, stats, use_workspace, given, opt);
   if (rc != kRetryWithRoots) return rc;
-  return run_build_impl(tin, nt, prm, st, shared_out, tiles_out, stats, use_workspace, true);
+  return run_build_impl(tin, nt, prm, st, shared_out, tiles_out, stats, use_workspace, true, opt);
 }
 
 static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t& prm, cudaStream_t st,
                           std::shared_ptr<SharedBuffers>* shared_out, std::vector<TileResult>* tiles_out,
-                          BuildStats* stats, bool use_workspace, bool sync_roots) {
+                          BuildStats* stats, bool use_workspace, bool sync_roots, const BuildOptions& opt) {
   BuildStats S;
   PhaseClock clk;
   arm_oom_injection();
@@ -661,6 +664,10 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
     std::memset(&td[t], 0, sizeof(TileDesc));
     td[t].in = reinterpret_cast<const int4*>(tin[t].d_points);
     td[t].n = (uint32_t)n;
+    td[t].in_idx = tin[t].d_index;
+    td[t].idx_bound = tin[t].index_bound ? tin[t].index_bound : (uint32_t)n;
+    td[t].level0 = tin[t].level0;
+    if (tin[t].d_index && (prm.flags & LOD_FLAG_FULL_PRECISION)) return LOD_ERR_INVALID_ARG;
     td[t].pt_base = M;
     M += n;
     chunk0[t + 1] = chunk0[t] + (n + kChunk - 1) / kChunk;
@@ -742,7 +749,11 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
       src_bound0 += td[t].n / (T + 1ull);
       continue;
     }
-    if (td[t].n == 0) {
+    if (tin[t].cube) {
+      for (int a = 0; a < 3; ++a) td[t].min[a] = tin[t].cube[a];
+      td[t].log2S = (uint32_t)tin[t].cube[3];
+      if (tin[t].cube[3] < 0 || tin[t].cube[3] > 32) return LOD_ERR_INVALID_ARG;
+    } else if (td[t].n == 0) {
       td[t].min[0] = td[t].min[1] = td[t].min[2] = 0;
       td[t].log2S = 0;
     } else {
@@ -1130,8 +1141,10 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
       "voxelize_L24", "voxelize_L25", "voxelize_L26", "voxelize_L27", "voxelize_L28", "voxelize_L29",
       "voxelize_L30", "voxelize_L31", "voxelize_L32", "voxelize_L33"};
   A.tiles = d_tiles.as<TileDesc>();
+  DevBuf d_rsums(st);  // result (out-of-core merges): exact sums of the roots' voxels
   for (int attempt = 0;; ++attempt) {
     LOD_CK(d_dense.alloc(dense_cap * 16));
+    if (opt.keep_root_sums && filt) LOD_CK(d_rsums.alloc(dense_cap * 16));
     LOD_CK(cudaMemsetAsync(d_tvox.p, 0, nt * 8, st));
     LOD_CK(cudaMemsetAsync(d_lctr.p, 0, lctr_bytes, st));
     LOD_CK(cudaMemsetAsync(d_vstate.p, 0, 2 * sizeof(unsigned long long), st));
@@ -1178,7 +1191,9 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
     if (n_vlev > 0) {
       // the roots' voxels: the items of the top level have no parent pass
       // that would copy their staged records
+      vl.root_sums = d_rsums.as<ulonglong2>();
       LOD_LAUNCH("publish_top", 0, launch_copy_items(A, vl, st));
+      vl.root_sums = nullptr;
     }
     LOD_CK(cudaMemcpyAsync(lctr.data(), d_lctr.p, lctr_bytes, cudaMemcpyDeviceToHost, st));
     LOD_CK(cudaMemcpyAsync(vstate, d_vstate.p, sizeof(vstate), cudaMemcpyDeviceToHost, st));
@@ -1235,7 +1250,7 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
   }
   // trim the voxel array when the estimate was more than three times too
   // generous (a copy of the voxels; smaller slack is cheaper to keep)
-  if (dense_cap > 3 * V + 65536) {
+  if (dense_cap > 3 * V + 65536 && !d_rsums.p) {
     DevBuf exact(st);
     LOD_CK(exact.alloc(std::max<uint64_t>(V, 1) * 16));
     if (V) LOD_CK(cudaMemcpyAsync(exact.p, d_dense.p, V * 16, cudaMemcpyDeviceToDevice, st));
@@ -1270,6 +1285,8 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
   sh->bytes = M * 16 + (want_idx ? M * 4 : 0) + total_cap * sizeof(lod_node_t) + dense_cap * 16 +
               (d_vpts.p ? dense_cap * 16 : 0);
   sh->voxel_points = d_vpts.take();
+  if (d_rsums.p) sh->bytes += dense_cap * 16;
+  sh->root_sums = d_rsums.take();
   sh->points = d_points.take();
   sh->index = want_idx ? d_index.take() : nullptr;
   sh->nodes = d_nodes.take();

@@ -19,6 +19,7 @@ struct SharedBuffers {
   void* nodes = nullptr;    // node tables of all tiles
   void* voxels = nullptr;   // voxels of all tiles
   void* voxel_points = nullptr;  // full-precision picked points, parallel to voxels (or null)
+  void* root_sums = nullptr;     // BuildOptions::keep_root_sums: packed exact sums parallel to voxels
   void* input = nullptr;    // owned copy of host input (lod_build_from_host), or null
   uint64_t bytes = 0;
   ~SharedBuffers();
@@ -42,6 +43,16 @@ struct BuildStats {
 struct TileInput {
   const lod_point_t* d_points;
   uint64_t n;
+  // Optional, for builds of one part of a larger cloud (out-of-core chunks):
+  const uint32_t* d_index = nullptr;  // input index of every point (device), used by the pick rules and
+                                      // reported as pick_index / leaf index; null: the position in d_points
+  uint32_t index_bound = 0;           // indices are < index_bound (0: n)
+  const int32_t* cube = nullptr;      // host: min x, y, z and log2 edge of the root cube (null: bounding box)
+  uint32_t level0 = 0;                // octree level of the root (the random pick draws per level)
+};
+
+struct BuildOptions {
+  bool keep_root_sums = false;  // filtered mode: keep the exact sums of every root's voxels
 };
 
 // Runs the complete build of n_tiles independent tiles on stream st.
@@ -50,7 +61,7 @@ struct TileInput {
 // stream between builds (see workspace_bytes).
 int run_build(const TileInput* tiles, uint32_t n_tiles, const lod_params_t& params, cudaStream_t st,
               std::shared_ptr<SharedBuffers>* shared, std::vector<TileResult>* tiles_out, BuildStats* stats,
-              bool use_workspace = true);
+              bool use_workspace = true, const BuildOptions& opt = BuildOptions());
 
 // Device bytes kept for stream st's builds between builds, and their release
 // (the stream must be idle).
@@ -80,6 +91,10 @@ int profile_enable(bool on);
 int profile_reset();
 int profile_read(lod_kernel_stat_t* out, uint32_t cap, uint32_t* n);
 uint64_t launch_count();
+
+// The out-of-core build of lod_build_out_of_core (ooc.cu).
+int build_out_of_core(const lod_point_t* h, uint64_t n, const lod_params_t& prm, const lod_ooc_config_t& cfg,
+                      cudaStream_t st, std::shared_ptr<SharedBuffers>* sh_out, TileResult* tr_out);
 
 // A library-owned non-blocking stream of the current device used to
 // release buffers asynchronously.

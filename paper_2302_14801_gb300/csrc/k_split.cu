@@ -685,7 +685,7 @@ __global__ void __launch_bounds__(kBlock) k_scatter(BuildArgs a, const uint32_t*
     }
     const TileDesc& td = a.tiles[s.tile];
     const uint32_t* src_idx =
-        s.buf == 0 ? nullptr : (s.buf == 1 ? a.tmp_idx[0] : a.tmp_idx[1]) + td.pt_base + s.pt_off;
+        s.buf == 0 ? td.in_idx : (s.buf == 1 ? a.tmp_idx[0] : a.tmp_idx[1]) + td.pt_base + s.pt_off;
     const uint64_t first = (c - s.chunk0) << kChunkLog2;
     const uint64_t end = min(first + kChunk, (uint64_t)s.n);
     uint32_t* cursor = s.start + pyr_off(s.d);

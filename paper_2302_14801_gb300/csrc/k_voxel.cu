@@ -133,50 +133,6 @@ __device__ __forceinline__ uint32_t key_to_cell(uint32_t key1, const ItemInfo& I
          (((I.kz << 6) | (l >> 12)) << 14);
 }
 
-// floor((s + n/2) / n) for a channel sum s of n 8-bit samples, i.e. the
-// mean rounded half up, which lies in [0, 255].  A single-precision
-// quotient is within 1 of it (relative error ~1e-7 on a value <= 255.5),
-// and one exact integer comparison each way settles it, avoiding a 64-bit
-// integer division.
-__device__ __forceinline__ uint32_t round_mean(uint64_t s, uint64_t n) {
-  const uint64_t num = s + (n >> 1);
-  uint32_t q = (uint32_t)__fdividef((float)num, (float)n);
-  q = q > 255u ? 255u : q;
-  if ((uint64_t)q * n > num) --q;
-  else if ((uint64_t)(q + 1) * n <= num) ++q;
-  return q;
-}
-
-__device__ __forceinline__ uint32_t mean_rgba(uint64_t r, uint64_t g, uint64_t b, uint64_t n) {
-  return round_mean(r, n) | (round_mean(g, n) << 8) | (round_mean(b, n) << 16) | 0xFF000000u;
-}
-
-// Key of a sample in the single-sample modes; every cell keeps the sample
-// of smallest key, and every key is below the empty entry's ~0 (the
-// splitmix64 preimage of ~0 is not a 32-bit index).  `level` is the level
-// of the node being filled.
-//  - LOD_PICK: splitmix64(input index) (replaces Listing 1 with an exact,
-//    order-independent rule).
-//  - LOD_FIRST: the input index itself: the first sample in input order
-//    (Section 4.2.1); a child's voxel carries its own first point, so the
-//    bottom-up merge keeps the cell's first point.
-//  - LOD_RANDOM: Listing 1 of Section 4.2.2: a 32-bit key holding the top
-//    12 bits of a random number drawn for the sample at this level above
-//    the low 20 bits of the sample's index, the largest key winning; equal
-//    keys go to the larger index.  The random number is the high half of
-//    splitmix64(level << 32 | index).  Minimising 2^64 - 2 - (key << 32 |
-//    index) maximises (key, index).
-template <int MODE>
-__device__ __forceinline__ uint64_t pick_key(uint32_t ix, uint32_t level) {
-  if (MODE == LOD_FIRST) return ix;
-  if (MODE == LOD_RANDOM) {
-    const uint32_t r = (uint32_t)(splitmix64(((uint64_t)level << 32) | ix) >> 32);
-    const uint64_t key = (r & 0xFFF00000u) | (ix & 0x000FFFFFu);
-    return 0xFFFFFFFFFFFFFFFEull - ((key << 32) | ix);
-  }
-  return splitmix64(ix);
-}
-
 }  // namespace
 
 int vox_smem_bytes() { return kSmemBytes; }
@@ -351,7 +307,8 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
           return;
         }
         if (PICKLIKE) {
-          if (!pick_update(&E[slot], pick_key<MODE>(ix, v.level), (uint64_t)(uint32_t)q.w | ((uint64_t)ix << 32)))
+          if (!pick_update(&E[slot], pick_key<MODE>(ix, td.level0 + v.level),
+                           (uint64_t)(uint32_t)q.w | ((uint64_t)ix << 32)))
             atomicOr(&ctr->error, kErrInternal);
           atomicAdd(&cnt32[slot], n_same);
         } else if (narrow) {
@@ -461,7 +418,8 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
           }
           if (PICKLIKE) {
             const uint32_t idx = (uint32_t)vr.w;
-            if (!pick_update(&E[slot], pick_key<MODE>(idx, v.level), (uint64_t)(uint32_t)vr.y | ((uint64_t)idx << 32)))
+            if (!pick_update(&E[slot], pick_key<MODE>(idx, td.level0 + v.level),
+                             (uint64_t)(uint32_t)vr.y | ((uint64_t)idx << 32)))
               atomicOr(&ctr->error, kErrInternal);
             atomicAdd(&cnt32[slot], (uint32_t)vr.z);
           } else {
@@ -594,7 +552,7 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
       rec.x = (int)cell;
       if (PICKLIKE) {
         const uint32_t best = (uint32_t)(e.y >> 32);
-        if (best >= td.n || pick_key<MODE>(best, v.level) != e.x) {  // cannot happen for a cell that received a sample
+        if (best >= td.idx_bound || pick_key<MODE>(best, td.level0 + v.level) != e.x) {  // cannot happen for a cell that received a sample
           atomicOr(&ctr->error, kErrInternal);
           continue;
         }
@@ -811,7 +769,10 @@ __global__ void __launch_bounds__(256) k_copy_items(BuildArgs a, VoxLevel v) {
                      (it - v.item_prefix[t]);
   const NodeAux ca = v.aux[g];
   if (ca.dense + ca.occ > v.dense_cap) return;  // the build is redone with a larger array
-  for (uint32_t i = threadIdx.x; i < ca.occ; i += blockDim.x) v.dense[ca.dense + i] = v.stage_out[ca.stage + i];
+  for (uint32_t i = threadIdx.x; i < ca.occ; i += blockDim.x) {
+    v.dense[ca.dense + i] = v.stage_out[ca.stage + i];
+    if (v.root_sums) v.root_sums[ca.dense + i] = v.stage_out_sum[ca.stage + i];
+  }
 }
 
 cudaError_t launch_copy_items(const BuildArgs& a, const VoxLevel& v, cudaStream_t st) {

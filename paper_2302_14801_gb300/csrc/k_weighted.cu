@@ -24,12 +24,11 @@
 // copy into the voxel array are shared).
 #include "common.cuh"
 #include "kernels.h"
+#include "wgrid.cuh"
 
 namespace lodk {
 
 namespace {
-
-constexpr float kWScale = 16777216.0f;  // 2^24: fixed-point weight unit
 
 // Shared state of one weighted CTA.
 struct WShared {
@@ -49,68 +48,15 @@ __device__ __forceinline__ uint32_t find_in_prefix(const uint32_t* prefix, uint3
   return lo;
 }
 
-// One weighted contribution to grid cell `cell`: the first toucher (the
-// weight sum was zero before) lists the cell for extraction.
-__device__ __forceinline__ void w_add(unsigned long long* grid, uint32_t* touched, WShared& S, uint32_t cell,
-                                      uint32_t wq, uint32_t rgba) {
-  unsigned long long* e = grid + 4ull * cell;
-  const unsigned long long old = atomicAdd(e + 3, (unsigned long long)wq);
-  if (old == 0ull) touched[atomicAdd(&S.touched, 1u)] = cell;
-  atomicAdd(e + 0, (unsigned long long)wq * (rgba & 255u));
-  atomicAdd(e + 1, (unsigned long long)wq * ((rgba >> 8) & 255u));
-  atomicAdd(e + 2, (unsigned long long)wq * ((rgba >> 16) & 255u));
-}
-
-// One sample whose position along axis a is P_a / 2^(s+1) cells (P_a an
-// integer), colour rgba, `count` original points, lying in cell own:
-// weights to the cells floor(pos - 1/2) and the next one per axis, inside
-// the grid.  The offset of the sample from the centre of cell j is
-// (P - (2j + 1) 2^s) / 2^(s+1).
-__device__ __forceinline__ void w_sample(unsigned long long* grid, uint32_t* cnt, uint32_t* touched, WShared& S,
-                                         const int64_t P[3], uint32_t s, uint32_t own, uint32_t rgba,
-                                         uint32_t count) {
-  const float inv = __int_as_float((int)(127u - (s + 1u)) << 23);  // 2^-(s+1), s + 1 <= 33
-  int32_t j0[3];
-  float e0[3], e1[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const int64_t h = int64_t(1) << s;
-    j0[a] = (int32_t)((P[a] - h) >> (s + 1));  // floor(pos - 1/2)
-    e0[a] = (float)(P[a] - (2 * (int64_t)j0[a] + 1) * h) * inv;
-    e1[a] = e0[a] - 1.0f;  // offset to the centre of j0 + 1
-  }
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int32_t jx = j0[0] + ((k >> 2) & 1), jy = j0[1] + ((k >> 1) & 1), jz = j0[2] + (k & 1);
-    if ((uint32_t)jx > 127u || (uint32_t)jy > 127u || (uint32_t)jz > 127u) continue;
-    const float ex = (k & 4) ? e1[0] : e0[0];
-    const float ey = (k & 2) ? e1[1] : e0[1];
-    const float ez = (k & 1) ? e1[2] : e0[2];
-    const float d2 = ex * ex + ey * ey + ez * ez;
-    if (d2 >= 1.0f) continue;
-    const uint32_t wq = __float2uint_rn((1.0f - sqrtf(d2)) * kWScale);
-    if (!wq) continue;
-    w_add(grid, touched, S, (uint32_t)jx | ((uint32_t)jy << 7) | ((uint32_t)jz << 14), wq, rgba);
-  }
-  atomicAdd(&cnt[own], count);
-}
-
-// Weighted mean of one channel, rounded half up: floor(s / w + 1/2).
-__device__ __forceinline__ uint32_t w_round(unsigned long long s, unsigned long long w) {
-  const unsigned long long q = s / w, r = s - q * w;
-  const unsigned long long m = q + (2 * r >= w ? 1ull : 0ull);
-  return m > 255ull ? 255u : (uint32_t)m;
-}
-
 }  // namespace
 
 // Parents at level v.level, taken in order by persistent CTAs.
 __global__ void __launch_bounds__(kBlock, 1) k_wvox(BuildArgs a, VoxLevel v, DevCounters* __restrict__ ctr) {
   __shared__ WShared S;
   __shared__ uint32_t s_par;
-  unsigned long long* grid = v.wgrid + (uint64_t)blockIdx.x * 4ull * (1u << 21);
-  uint32_t* cnt = v.wcnt + (uint64_t)blockIdx.x * (1u << 21);
-  uint32_t* touched = v.wtouch + (uint64_t)blockIdx.x * (1u << 21);
+  unsigned long long* grid = v.wgrid + (uint64_t)blockIdx.x * 4ull * kGridCells;
+  uint32_t* cnt = v.wcnt + (uint64_t)blockIdx.x * kGridCells;
+  uint32_t* touched = v.wtouch + (uint64_t)blockIdx.x * kGridCells;
   for (;;) {
     if (threadIdx.x == 0) s_par = atomicAdd(&ctr->item_head, 1u);
     __syncthreads();
@@ -133,11 +79,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_wvox(BuildArgs a, VoxLevel v, Dev
       const uint64_t cg = fc + r++;
       const lod_node_t& c = v.nodes[cg];
       if (c.flags & LOD_NODE_LEAF) {
-        // leaf child: its points; position (p - c) / 2^(L-7) cells, i.e.
-        // P = 2 (p - c) over 2^(s+1) with s = L - 7 (cubes of edge >= 128),
-        // or 2 (p - c) 2^(7-L) over 2 (smaller cubes: s = 0)
-        const uint32_t s = L >= 7 ? L - 7 : 0u;
-        const uint32_t up = L >= 7 ? 0u : 7u - L;
+        // leaf child: its points
         const uint64_t pbase = td.pt_base + c.point_offset;
         for (uint64_t i = threadIdx.x; i < c.point_count; i += blockDim.x) {
           int4 q;
@@ -149,22 +91,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_wvox(BuildArgs a, VoxLevel v, Dev
           } else {
             q = __ldcs(a.out + pbase + i);
           }
-          const uint32_t d[3] = {(uint32_t)q.x - (uint32_t)P.min[0], (uint32_t)q.y - (uint32_t)P.min[1],
-                                 (uint32_t)q.z - (uint32_t)P.min[2]};
           int64_t Pp[3];
-          uint32_t own = 0;
-#pragma unroll
-          for (int ax = 0; ax < 3; ++ax) {
-            Pp[ax] = (int64_t)((uint64_t)d[ax] << (1 + up));
-            own |= grid_coord(d[ax], L) << (7 * ax);
-          }
-          w_sample(grid, cnt, touched, S, Pp, s, own, (uint32_t)q.w, 1u);
+          uint32_t s, own;
+          w_point_pos(q, P.min, L, Pp, &s, &own);
+          w_sample(grid, cnt, touched, &S.touched, Pp, s, own, (uint32_t)q.w, 1u);
         }
       } else {
-        // inner child (octant b): its voxels, each at the centre of its
-        // cell q of the child's grid: position 64 b + (q + 1/2) / 2 cells =
-        // (256 b + 2 q + 1) / 4, lying in cell 64 b + q / 2
-        const uint32_t b[3] = {(k >> 2) & 1u, (k >> 1) & 1u, k & 1u};
+        // inner child (octant k): its voxels, each one sample at its cell centre
         const uint32_t nch = __popc(c.child_mask);
         const uint64_t gfc = td.node_base + c.first_child;
         for (uint32_t rr = 0; rr < nch; ++rr) {
@@ -175,16 +108,10 @@ __global__ void __launch_bounds__(kBlock, 1) k_wvox(BuildArgs a, VoxLevel v, Dev
           for (uint32_t i = threadIdx.x; i < ca.occ; i += blockDim.x) {
             const int4 vr = rec[i];
             if (fits) dst[i] = vr;  // publish the child's voxel
-            const uint32_t cell = (uint32_t)vr.x;
-            const uint32_t q[3] = {cell & 127u, (cell >> 7) & 127u, cell >> 14};
             int64_t Pp[3];
-            uint32_t own = 0;
-#pragma unroll
-            for (int ax = 0; ax < 3; ++ax) {
-              Pp[ax] = (int64_t)(256u * b[ax] + 2u * q[ax] + 1u);
-              own |= (64u * b[ax] + (q[ax] >> 1)) << (7 * ax);
-            }
-            w_sample(grid, cnt, touched, S, Pp, 1u, own, (uint32_t)vr.y, (uint32_t)vr.z);
+            uint32_t own;
+            w_voxel_pos((uint32_t)vr.x, k, Pp, &own);
+            w_sample(grid, cnt, touched, &S.touched, Pp, 1u, own, (uint32_t)vr.y, (uint32_t)vr.z);
           }
         }
       }
@@ -196,8 +123,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_wvox(BuildArgs a, VoxLevel v, Dev
     for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
       const uint32_t cell = touched[i];
       if (__ldcg(cnt + cell)) {
-        const uint32_t k = (((cell >> 6) & 1u) << 2) | (((cell >> 13) & 1u) << 1) | ((cell >> 20) & 1u);
-        atomicAdd(&S.occ[k], 1u);
+        atomicAdd(&S.occ[cell_octant(cell)], 1u);
       }
     }
     __syncthreads();
@@ -230,7 +156,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_wvox(BuildArgs a, VoxLevel v, Dev
         const ulonglong2 rg = __ldcg(reinterpret_cast<const ulonglong2*>(e));
         const ulonglong2 bw = __ldcg(reinterpret_cast<const ulonglong2*>(e) + 1);
         const unsigned long long w = bw.y;
-        const uint32_t k = (((cell >> 6) & 1u) << 2) | (((cell >> 13) & 1u) << 1) | ((cell >> 20) & 1u);
+        const uint32_t k = cell_octant(cell);
         const uint32_t o = atomicAdd(&S.cur[k], 1u);
         int4 rec;
         rec.x = (int)cell;
@@ -249,7 +175,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_wvox(BuildArgs a, VoxLevel v, Dev
   }
 }
 
-size_t wgrid_bytes_per_cta() { return (size_t(1) << 21) * (32 + 4 + 4); }
+size_t wgrid_bytes_per_cta() { return (size_t)kGridCells * (32 + 4 + 4); }
 
 cudaError_t launch_wvox(const BuildArgs& a, const VoxLevel& v, DevCounters* ctr, int ctas, cudaStream_t st) {
   if (!v.n_parents) return cudaSuccess;

@@ -56,6 +56,7 @@ struct VoxLevel {
   unsigned long long* wgrid;
   uint32_t* wcnt;
   uint32_t* wtouch;
+  ulonglong2* root_sums;  // filtered: exact sums of the top level's voxels, parallel to dense (or null)
 };
 cudaError_t launch_vox(const BuildArgs& a, const VoxLevel& v, DevCounters* ctr, cudaStream_t st);
 // Section 4.2.4: one persistent CTA per grid over the parents of a level.
@@ -74,6 +75,48 @@ cudaError_t launch_gather_voxels(const lod_node_t* nodes, uint32_t n_nodes, cons
                                  const int4* src, int4* dst, cudaStream_t st);
 
 int vox_smem_bytes();
+
+// ----- out-of-core build (Section 7) -----
+struct OocGrid {  // top grid: 8^D cells at depth D below the root cube [min, min + 2^L)^3
+  int32_t min[3];
+  uint32_t L, D;
+};
+struct MergeSeg {  // the samples one child gives its parent
+  const int4* recs;         // points (x, y, z, rgba) or voxels (cell, rgba, count, pick_index)
+  const ulonglong2* sums;   // voxels, filtered mode: packed exact sums
+  const uint32_t* idx;      // points, single-sample modes: input indices
+  uint32_t n;
+  uint32_t kind;            // 0 points, 1 voxels
+  uint32_t octant;          // voxels: the child's octant in the parent
+  uint32_t pad;
+};
+struct MergeJob {  // one root-side node
+  int32_t min[3];
+  uint32_t log2, level, seg0, nseg, pad;
+};
+struct MergeOut {
+  unsigned long long* grid;  // per CTA: kGridCells x 4 u64
+  uint32_t* cnt;             // per CTA: kGridCells
+  uint32_t* touched;         // per CTA: kGridCells
+  unsigned int* job_head;
+  int4* recs;                // voxels of every job, bump-allocated
+  ulonglong2* sums;          // filtered: their packed exact sums
+  unsigned long long* used;
+  uint64_t cap;
+  ulonglong2* result;        // per job: {first voxel, count}
+  unsigned int* error;
+};
+cudaError_t launch_ooc_bbox(const int4* pts, uint64_t n, int* box, int sms, cudaStream_t st);
+cudaError_t launch_ooc_count(const int4* pts, uint64_t n, const OocGrid& g, unsigned int* counts, int sms,
+                             cudaStream_t st);
+cudaError_t launch_ooc_chunk_of(const int4* pts, uint64_t n, const OocGrid& g, const uint32_t* cell_chunk,
+                                uint32_t n_chunks, uint32_t* chunk_of, unsigned int* hist, unsigned int* err, int sms,
+                                cudaStream_t st);
+cudaError_t launch_ooc_partition(const int4* pts, uint64_t n, uint32_t first, const uint32_t* chunk_of,
+                                 uint32_t n_chunks, unsigned int* cursor, int4* out, uint32_t* out_idx, int sms,
+                                 cudaStream_t st);
+cudaError_t launch_merge(uint32_t mode, const MergeJob* jobs, uint32_t n_jobs, const MergeSeg* segs,
+                         const MergeOut& o, int ctas, cudaStream_t st);
 
 // ----- rendering (Section 5) -----
 cudaError_t launch_render(const lod_node_t* nodes, uint32_t n_nodes, const int4* points, const int4* voxels,

@@ -41,6 +41,7 @@ EXPORTED = [
     "lod_server_destroy", "lod_profile_enable", "lod_profile_reset", "lod_profile_read", "lod_launch_count",
     "lod_root_cubes_noalloc", "lod_set_tuning", "lod_get_tuning", "lod_autotune", "lod_scratch_bytes",
     "lod_trim", "lod_result_voxel_points", "lod_result_copy_voxel_points_to_host", "lod_render",
+    "lod_build_out_of_core",
 ]
 
 
@@ -82,6 +83,11 @@ class Camera(ctypes.Structure):
 class RenderStats(ctypes.Structure):
     _fields_ = [("visible_nodes", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("samples_drawn", ctypes.c_uint64)]
+
+
+class OocConfig(ctypes.Structure):
+    _fields_ = [("chunk_points", ctypes.c_uint64), ("stream_points", ctypes.c_uint64),
+                ("batch_points", ctypes.c_uint64)]
 
 
 class KernelStat(ctypes.Structure):
@@ -136,6 +142,7 @@ def _load():
         "lod_trim": (i, [vp]),
         "lod_result_voxel_points": (i, [vp, P(vp)]),
         "lod_render": (i, [vp, P(Camera), vp, vp, P(RenderStats)]),
+        "lod_build_out_of_core": (i, [vp, u64, P(Params), P(OocConfig), vp, P(vp)]),
         "lod_result_copy_voxel_points_to_host": (i, [vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -400,6 +407,34 @@ def build_from_host(points, leaf_threshold=50000, mode=FILTER, max_depth=21, kee
     h = ctypes.c_void_p()
     _check(lib().lod_build_from_host(ptr if n else None, n, ctypes.byref(p), _stream_handle(stream),
                                      ctypes.byref(h)), "lod_build_from_host")
+    del keep
+    return Result(h.value)
+
+
+def _host_ptr(points):
+    """Pointer and length of host points: a numpy array or a CPU int32 tensor shaped (N, 4)."""
+    if isinstance(points, np.ndarray):
+        if points.ndim != 2 or points.shape[1] != 4:
+            raise TypeError("host points must have shape (N, 4)")
+        arr = np.ascontiguousarray(points, dtype=np.int32)
+        return arr.ctypes.data, arr.shape[0], arr
+    import torch
+    if not isinstance(points, torch.Tensor) or points.is_cuda or points.dtype != torch.int32 \
+            or points.dim() != 2 or points.shape[1] != 4 or not points.is_contiguous():
+        raise TypeError("host points must be a numpy array or a contiguous int32 CPU tensor of shape (N, 4)")
+    return points.data_ptr(), points.shape[0], points
+
+
+def build_out_of_core(points, leaf_threshold=50000, mode=FILTER, max_depth=21, keep_index=False,
+                      chunk_points=0, stream_points=0, batch_points=0, stream=None) -> Result:
+    """lod_build_out_of_core: the octree of host points built chunk by
+    chunk (0 selects each size's default)."""
+    ptr, n, keep = _host_ptr(points)
+    p = make_params(leaf_threshold, mode, max_depth, keep_index)
+    cfg = OocConfig(int(chunk_points), int(stream_points), int(batch_points))
+    h = ctypes.c_void_p()
+    _check(lib().lod_build_out_of_core(ptr if n else None, n, ctypes.byref(p), ctypes.byref(cfg),
+                                       _stream_handle(stream), ctypes.byref(h)), "lod_build_out_of_core")
     del keep
     return Result(h.value)
 

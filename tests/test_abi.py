@@ -82,6 +82,15 @@ def test_invalid_arguments_rejected_on_host(lodmod):
     cam = lodmod.make_camera(np.eye(4, dtype=np.float32), [0, 0, 0], 8, 8)
     assert L.lod_render(None, ctypes.byref(cam), dev, None, None) == lodmod.LOD_ERR_INVALID_ARG
     assert L.lod_result_voxel_points(None, None) == lodmod.LOD_ERR_INVALID_ARG
+    assert L.lod_build_out_of_core(None, 5, ctypes.byref(p), None, None, ctypes.byref(h)) == \
+        lodmod.LOD_ERR_INVALID_ARG  # no points
+    small_chunk = lodmod.OocConfig(10, 0, 0)  # chunks smaller than T
+    pts = np.zeros((5, 4), np.int32)
+    assert L.lod_build_out_of_core(pts.ctypes.data, 5, ctypes.byref(p), ctypes.byref(small_chunk), None,
+                                   ctypes.byref(h)) == lodmod.LOD_ERR_INVALID_ARG
+    fp = lodmod.make_params(mode=1, full_precision=True)
+    assert L.lod_build_out_of_core(pts.ctypes.data, 5, ctypes.byref(fp), None, None, ctypes.byref(h)) == \
+        lodmod.LOD_ERR_INVALID_ARG
     assert L.lod_result_copy_voxel_points_to_host(None, None, None) == lodmod.LOD_ERR_INVALID_ARG
     assert L.lod_profile_read(None, 0, None) == lodmod.LOD_ERR_INVALID_ARG
 

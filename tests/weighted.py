@@ -1,14 +1,11 @@
 """Checks of neighbourhood-weighted results (Section 4.2.4) node by node.
 
 A weighted voxel's colour depends on the colours of the child voxels it
-samples (8-bit, already rounded), so a one-unit difference in a child can
-move its parent by a unit as well.  ``per_node_check`` therefore recomputes
-every inner node with the oracle from that node's own children *in the
-result being checked* (the leaf children's points and the inner children's
-voxels): with equal inputs the only differences left come from arithmetic
-(the oracle is exact in double precision, the CUDA path sums 24-bit
-fixed-point weights exactly), which can move a channel by one unit only
-where the weighted mean lies within about 1e-5 of a rounding boundary."""
+samples (8-bit, already rounded), so a mistake in a child also moves its
+ancestors.  ``per_node_check`` recomputes every inner node with the oracle
+from that node's own children *in the result being checked* (the leaf
+children's points and the inner children's voxels), which locates a
+difference at the node where it arises."""
 from __future__ import annotations
 
 import numpy as np
