@@ -499,6 +499,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra-modes", action="store_true", help="skip timing the weighted / first / random modes")
     ap.add_argument("--no-render", action="store_true", help="skip timing the rasteriser")
+    ap.add_argument("--tuning", default="", help="lod_set_tuning knobs for this run, e.g. "
+                    "'vox_spill_records=1,dense_bins_max=512' (default: the library's defaults)")
     ap.add_argument("--suite", default="single", choices=["single", "batched", "serve"],
                     help="single: the headline line; batched: many independent tiles per launch "
                          "(lod_build_batched); serve: Poisson request stream through lod_submit/lod_poll")
@@ -531,6 +533,9 @@ def main():
     __graft_entry__.build()
     from paper_2302_14801_gb300 import lod
 
+    tuning = {k: int(v) for k, v in (kv.split("=") for kv in args.tuning.split(",") if kv)}
+    if tuning:
+        lod.set_tuning(**tuning)
     name = args.workload
     _, n, _, T = WORKLOADS[name]
     if on_device(name):
@@ -729,7 +734,8 @@ def main():
             "config": {"workload": f"{name}: {n} points (seeded synthetic"
                                    f"{', drawn on the device' if on_device(name) else ''}), T={T}, 128^3 grid; "
                                    "step = 1 filtered + 1 pick build, input resident in HBM",
-                       "l2": f"inputs ({n * 16 / 1e6:.0f} MB) larger than L2; no flush", "replicas": world},
+                       "l2": f"inputs ({n * 16 / 1e6:.0f} MB) larger than L2; no flush", "replicas": world,
+                       "tuning": lod.get_tuning()},
             "modes": per_mode, "modes_extra": extra, "render": render, "roofline": roof, "kernels": kern,
             "gpu_launches": launches,
             "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,

@@ -325,26 +325,41 @@ int lod_root_cubes_noalloc(const lod_point_t* const* d_tiles, const uint64_t* n,
  *                   1..8, still capped by the cube and max_depth); default:
  *                   one more level than a surface-like cloud needs to reach
  *                   the leaf threshold.
- *   stream_ctas_per_sm  CTAs per SM of the streaming passes (default 2). */
+ *   stream_ctas_per_sm  CTAs per SM of the streaming passes (default 2).
+ *   dense_bins_max  counting grids of at most this many cells are counted
+ *                   in a dense shared-memory histogram, larger ones through
+ *                   per-CTA shared-memory hash tables (8..4096, a power of
+ *                   8; default 4096).
+ *   vox_spill_records  records of each of the two spill lists a voxel CTA
+ *                   keeps in global memory: a sample whose cell finds no
+ *                   slot in the CTA's shared-memory table goes there and is
+ *                   processed by another pass, instead of the item being
+ *                   redone in hash partitions (default 65536; 1 turns the
+ *                   lists off). */
 typedef struct lod_tuning {
   uint32_t root_depth;
   uint32_t stream_ctas_per_sm;
-  uint32_t reserved[6];
+  uint32_t dense_bins_max;
+  uint32_t vox_spill_records;
+  uint32_t reserved[4];
 } lod_tuning_t;
 
 int lod_set_tuning(const lod_tuning_t* t);
 int lod_get_tuning(lod_tuning_t* t);
 
 /* Autotuner: times lod_build of the caller's cloud (device pointer, n points,
- * params; on `stream`) under each candidate tuning — root_depth the default,
- * one less and one more; stream_ctas_per_sm 1, 2 and 3 — two builds each
- * (the first untimed), keeps the fastest with lod_set_tuning and returns it
- * in *best (and its build time in *best_ms when not NULL).  Results are
- * freed; nothing else is kept.  Costs about 18 builds; like lod_set_tuning
- * it changes process-wide state, so call it while no other build runs.
- * Returns LOD_ERR_INVALID_ARG for n == 0 or a missing pointer, or the first
- * build error (the previous tuning is then restored).  The paper has no
- * counterpart (it uses one fixed configuration, Section 4.1.6). */
+ * params; on `stream`) under candidate tunings, two builds each (the first
+ * untimed), by coordinate descent from the defaults: stream_ctas_per_sm 1
+ * and 3; root_depth one less and one more than the default; dense_bins_max
+ * 512; vox_spill_records 1 (off) and 262144 — each knob in turn, the others
+ * held at the best so far.  Keeps the fastest with lod_set_tuning and
+ * returns it in *best (and its build time in *best_ms when not NULL).
+ * Results are freed; nothing else is kept.  Costs about 16 builds; like
+ * lod_set_tuning it changes process-wide state, so call it while no other
+ * build runs.  Returns LOD_ERR_INVALID_ARG for n == 0 or a missing pointer,
+ * or the first build error (the previous tuning is then restored).  The
+ * paper has no counterpart (it uses one fixed configuration, Section
+ * 4.1.6). */
 int lod_autotune(const lod_point_t* d_points, uint64_t n, const lod_params_t* params, void* stream,
                  lod_tuning_t* best, float* best_ms);
 

@@ -286,43 +286,55 @@ int lod_autotune(const lod_point_t* d_points, uint64_t n, const lod_params_t* pa
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   lod_tuning_t before;
   lodk::get_tuning(&before);
-  const uint32_t d0 = lodk::default_root_depth(n, p.leaf_threshold, p.max_depth);
-  std::vector<uint32_t> depths = {0};
-  if (d0 > 1) depths.push_back(d0 - 1);
-  if (d0 >= 1 && d0 < 8) depths.push_back(d0 + 1);
   cudaEvent_t a = nullptr, b = nullptr;
   if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
     if (a) cudaEventDestroy(a);
     return LOD_ERR_CUDA;
   }
-  lod_tuning_t win = before;
-  float win_ms = -1.f;
-  int rc = LOD_OK;
-  for (uint32_t d : depths) {
-    for (uint32_t cps : {1u, 2u, 3u}) {
-      lod_tuning_t t;
-      std::memset(&t, 0, sizeof(t));
-      t.root_depth = d;
-      t.stream_ctas_per_sm = cps;
-      if ((rc = lodk::set_tuning(t)) != LOD_OK) break;
-      float ms = 0.f;
-      for (int rep = 0; rep < 2 && rc == LOD_OK; ++rep) {
-        lod_result_t* r = nullptr;
-        if (rep == 1) cudaEventRecord(a, st);
-        rc = lod_build(d_points, n, &p, stream, &r);
-        if (rep == 1) cudaEventRecord(b, st);
-        if (rc == LOD_OK) {
-          lod_free(r);
-          if (rep == 1 && cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
-        }
+  // one build to warm up, one timed
+  auto time_with = [&](const lod_tuning_t& t, float* ms) -> int {
+    int rc = lodk::set_tuning(t);
+    for (int rep = 0; rep < 2 && rc == LOD_OK; ++rep) {
+      lod_result_t* r = nullptr;
+      if (rep == 1) cudaEventRecord(a, st);
+      rc = lod_build(d_points, n, &p, st, &r);
+      if (rep == 1) cudaEventRecord(b, st);
+      if (rc == LOD_OK) {
+        lod_free(r);
+        if (rep == 1 && cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(ms, a, b);
       }
-      if (rc != LOD_OK) break;
-      if (win_ms < 0.f || ms < win_ms) {
+    }
+    return rc;
+  };
+  // coordinate descent: each knob in turn over its candidates, the others
+  // held at the best found so far
+  const uint32_t d0 = lodk::default_root_depth(n, p.leaf_threshold, p.max_depth);
+  std::vector<uint32_t> depths = {0};
+  if (d0 > 1) depths.push_back(d0 - 1);
+  if (d0 >= 1 && d0 < 8) depths.push_back(d0 + 1);
+  lod_tuning_t win;
+  std::memset(&win, 0, sizeof(win));
+  float win_ms = -1.f;
+  int rc = time_with(win, &win_ms);
+  for (int knob = 0; knob < 4 && rc == LOD_OK; ++knob) {
+    std::vector<uint32_t> cand;
+    if (knob == 0) cand = {1u, 3u};         // CTAs per SM of the streaming passes (default 2)
+    if (knob == 1) cand = std::vector<uint32_t>(depths.begin() + 1, depths.end());
+    if (knob == 2) cand = {512u};           // dense shared histograms up to 512 cells (default 4096)
+    if (knob == 3) cand = {1u, 262144u};    // no spill lists, larger ones (default 65536)
+    for (uint32_t c : cand) {
+      lod_tuning_t t = win;
+      if (knob == 0) t.stream_ctas_per_sm = c;
+      if (knob == 1) t.root_depth = c;
+      if (knob == 2) t.dense_bins_max = c;
+      if (knob == 3) t.vox_spill_records = c;
+      float ms = 0.f;
+      if ((rc = time_with(t, &ms)) != LOD_OK) break;
+      if (ms < win_ms) {
         win_ms = ms;
         win = t;
       }
     }
-    if (rc != LOD_OK) break;
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);

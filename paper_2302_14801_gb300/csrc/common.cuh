@@ -93,6 +93,8 @@ struct BuildArgs {
   // exceeds its cube; the split kernels then do nothing and the host
   // restarts with the depths fixed
   const unsigned int* abort;
+  uint32_t dense_max;  // grids of at most this many cells count in a dense shared histogram (<= kSmemBins)
+  uint32_t pad_;
 };
 
 constexpr uint32_t kPrivSlots = 24576;  // per-CTA table of distinct cells (192 KB counting, 216 KB scatter)

@@ -279,6 +279,8 @@ uint32_t ceil_log4(double x) {
 // level), capped at 256^3 cells, the cube's own size and max_depth.
 std::atomic<uint32_t> g_tune_root_depth{0};
 std::atomic<uint32_t> g_tune_ctas_per_sm{0};
+std::atomic<uint32_t> g_tune_spill_cap{0};  // 0: default, 1: no spill lists
+std::atomic<uint32_t> g_tune_dense_bins{0};  // 0: kSmemBins
 
 uint32_t choose_root_depth(uint64_t n, uint32_t T, uint32_t log2S, uint32_t max_depth) {
   if (n <= T || log2S == 0 || max_depth == 0) return 0;
@@ -472,8 +474,13 @@ uint32_t default_root_depth(uint64_t n, uint32_t T, uint32_t max_depth) {
 
 int set_tuning(const lod_tuning_t& t) {
   if (t.root_depth > kRootMaxD || t.stream_ctas_per_sm > 8) return LOD_ERR_INVALID_ARG;
+  const uint32_t b = t.dense_bins_max;
+  if (b && (b != 8 && b != 64 && b != 512 && b != 4096)) return LOD_ERR_INVALID_ARG;
+  if (t.vox_spill_records > (1u << 24)) return LOD_ERR_INVALID_ARG;
   g_tune_root_depth.store(t.root_depth);
   g_tune_ctas_per_sm.store(t.stream_ctas_per_sm);
+  g_tune_dense_bins.store(b);
+  g_tune_spill_cap.store(t.vox_spill_records);
   return LOD_OK;
 }
 
@@ -481,6 +488,8 @@ int get_tuning(lod_tuning_t* t) {
   std::memset(t, 0, sizeof(*t));
   t->root_depth = g_tune_root_depth.load();
   t->stream_ctas_per_sm = g_tune_ctas_per_sm.load();
+  t->dense_bins_max = g_tune_dense_bins.load();
+  t->vox_spill_records = g_tune_spill_cap.load();
   return LOD_OK;
 }
 
@@ -651,6 +660,7 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
   if (!valid_params(prm)) return LOD_ERR_INVALID_ARG;
   const bool want_idx = keeps_index(prm);
   const uint32_t T = prm.leaf_threshold;
+  const uint32_t dense_max = g_tune_dense_bins.load() ? g_tune_dense_bins.load() : kSmemBins;
 
   // ---- tile table and round-0 chunk space
   std::vector<TileDesc> td(nt);
@@ -745,7 +755,7 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
       s.d = choose_root_depth(td[t].n, T, 32, prm.max_depth);
       s.n = td[t].n;
       s.chunk0 = chunk0[t];
-      s.priv = ipow8(s.d) > kSmemBins ? 1u : 0u;
+      s.priv = ipow8(s.d) > dense_max ? 1u : 0u;
       src_bound0 += td[t].n / (T + 1ull);
       continue;
     }
@@ -777,7 +787,7 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
     s.pt_off = 0;
     s.n = td[t].n;
     s.chunk0 = chunk0[t];
-    s.priv = ipow8(s.d) > kSmemBins ? 1u : 0u;  // too large for a dense shared histogram
+    s.priv = ipow8(s.d) > dense_max ? 1u : 0u;  // counted through the per-CTA hash tables
     src_bound0 += td[t].n / (T + 1ull);
   }
 
@@ -801,6 +811,7 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
   A.lists = d_lists.as<uint2>();
   A.list_len = d_llen.as<uint32_t>();
   A.abort = sync_roots ? nullptr : d_abort.as<unsigned int>();
+  A.dense_max = dense_max;
   // modes that keep input indices stage each leaf point as one 32-byte record
   DevBuf d_wide(st, ws);
   if (want_idx) {
@@ -1123,6 +1134,13 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
     }
   }
   const uint32_t units_cap = (uint32_t)std::min<uint64_t>((uint64_t)max_items * 64, 1u << 20);
+  // spill lists of the first-attempt voxel kernel (one CTA per SM); sample
+  // positions are 32-bit, so a staging array of 2^32 records or more goes
+  // without them
+  const uint32_t spill_cap = g_tune_spill_cap.load() == 1 ? 0u : (g_tune_spill_cap.load() ? g_tune_spill_cap.load() : 65536u);
+  DevBuf d_spill(st, ws);
+  if (!weighted && spill_cap && n_vlev > 0 && stage_cap < (1ull << 32))
+    LOD_CK(d_spill.alloc((size_t)sm_count() * 2 * spill_cap * sizeof(uint2)));
   LOD_CK(d_units.alloc((size_t)units_cap * sizeof(uint4)));
   const size_t lctr_bytes = (size_t)std::max(n_vlev, 1) * sizeof(DevCounters);
   LOD_CK(d_lctr.alloc(lctr_bytes));
@@ -1174,6 +1192,8 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
       vl.vstate = d_vstate.as<unsigned long long>();
       vl.parent_prefix = d_pref.as<uint32_t>() + (size_t)l * pstride + (nt + 1);
       vl.n_parents = n_par;
+      vl.spill = d_spill.as<uint2>();
+      vl.spill_cap = d_spill.p ? spill_cap : 0u;
       if (weighted) {
         vl.wgrid = reinterpret_cast<unsigned long long*>(wbase);
         vl.wcnt = reinterpret_cast<uint32_t*>(wbase + (size_t)wctas * cells * 32);

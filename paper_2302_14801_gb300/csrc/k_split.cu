@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_count(BuildArgs a, const uint32_t
       __syncthreads();
       cur = sid;
       nbins = 1u << (3 * s.d);
-      smem = nbins <= kSmemBins;
+      smem = !s.priv;  // a dense grid (then nbins <= kSmemBins)
       if (smem)
         for (uint32_t b = threadIdx.x; b < nbins; b += blockDim.x) hist[b] = 0;
       __syncthreads();
@@ -586,7 +586,7 @@ __global__ void __launch_bounds__(512) k_pyr_down(BuildArgs a, const PyrJob* __r
     ns.pt_off = sta[1 + lo[k] + q];
     ns.n = n;
     ns.chunk0 = 0;
-    ns.priv = (1u << (3 * ns.d)) > kSmemBins ? 1u : 0u;  // too large for a dense shared histogram
+    ns.priv = (1u << (3 * ns.d)) > a.dense_max ? 1u : 0u;  // counted through the per-CTA hash tables
     ns.pad = 0;
     a.srcs[g] = ns;
     s.map[c] = g;

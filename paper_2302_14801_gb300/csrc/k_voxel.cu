@@ -141,12 +141,16 @@ int vox_smem_bytes() { return kSmemBytes; }
 struct VoxShared {
   uint32_t used, out, fail, sp, seen, queued;
   uint32_t clean;  // the table holds no entry (set by a complete extraction)
+  uint32_t spill_n[2];  // records in the CTA's two spill lists
+  uint32_t spill_in;    // records the current spill pass reads
+  uint32_t spilling;    // the item spilled: its staging block is reserved whole
   unsigned long long base;  // first staging record of the current pass's output
   ItemInfo I;
   uint2 stack[48];          // pending {partition, log2 partitions} of the item
 };
 
 constexpr uint32_t kMaxQueuedLog = 6;  // an overflowing item is queued as at most 64 units
+constexpr uint32_t kSpillMark = 0xFFu;  // stack entry {list, kSpillMark}: a pass over a spill list
 constexpr uint32_t kMaxPartLog = 16;   // deeper partitions cannot overflow (a few cells each)
 
 // Reserve `n` consecutive slots of the unit queue; false when it is full
@@ -198,6 +202,8 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
     S.stack[0] = make_uint2(p_first, m_first);
     S.sp = 1;
     S.queued = 0;
+    S.spilling = 0;
+    S.spill_n[0] = S.spill_n[1] = 0;
   }
   __syncthreads();
   const ItemInfo& I = S.I;
@@ -243,6 +249,18 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
     if (S.sp == 0) break;
     const uint2 pm = S.stack[S.sp - 1];
     const uint32_t part = pm.x, mlog = pm.y;
+    // Spill lists: in the item's first pass and in the passes over its
+    // spill lists, a sample whose cell finds no slot is appended (its cell
+    // key and its position) to a list in global memory instead of failing
+    // the pass; the cells in the table are then complete and are extracted,
+    // and the list is processed by another pass over an empty table.  Only
+    // a list that outgrows its space fails the item (which is then redone
+    // in hash partitions).
+    const bool spill_pass = mlog == kSpillMark;
+    const bool can_spill = v.spill != nullptr && first && (spill_pass || mlog == 0);
+    const uint32_t sp_out_id = spill_pass ? 1u - part : 0u;
+    uint2* const sp_out = can_spill ? v.spill + ((uint64_t)blockIdx.x * 2 + sp_out_id) * v.spill_cap : nullptr;
+    const uint2* const sp_in = spill_pass ? v.spill + ((uint64_t)blockIdx.x * 2 + part) * v.spill_cap : nullptr;
     if (!S.clean) {
       // an empty entry is all zero bytes in filtered mode whatever the
       // table's layout, so a clean table serves every item
@@ -264,12 +282,90 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
       S.fail = 0;
       S.seen = 0;
       S.clean = 0;
+      S.spill_in = spill_pass ? S.spill_n[part] : 0u;
+      if (can_spill) S.spill_n[sp_out_id] = 0;
     }
     __syncthreads();
     ++passes;
+    // append this lane's sample (cell key, position) to the output list when
+    // `want`; warp-aggregated, called by every lane of the warp
+    auto spill_warp = [&](bool want, uint32_t key1, uint32_t src) {
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, want);
+      if (!m) return;
+      const int leader = __ffs(m) - 1;
+      uint32_t base = 0;
+      if ((int)lane == leader) base = atomicAdd(&S.spill_n[sp_out_id], (uint32_t)__popc(m));
+      base = __shfl_sync(0xFFFFFFFFu, base, leader);
+      if (!want) return;
+      const uint32_t pos = base + __popc(m & ((1u << lane) - 1u));
+      if (pos < v.spill_cap) sp_out[pos] = make_uint2(key1, src);
+      else S.fail = 1;
+    };
+    auto spill_one = [&](uint32_t key1, uint32_t src) {
+      const uint32_t pos = atomicAdd(&S.spill_n[sp_out_id], 1u);
+      if (pos < v.spill_cap) sp_out[pos] = make_uint2(key1, src);
+      else S.fail = 1;
+    };
     uint32_t seen = 0;  // samples this thread went through (for the overflow estimate)
 
-    if (I.leaf) {
+    if (spill_pass) {
+      // a spill list: every record names its cell and where its sample is
+      for (uint32_t i = threadIdx.x; i < S.spill_in; i += blockDim.x) {
+        const uint2 sr = sp_in[i];
+        const uint32_t key1 = sr.x, src = sr.y;
+        ++seen;
+        const int slot = find_or_insert(keys, H, key1);
+        if (slot < 0) {
+          spill_one(key1, src);
+          continue;
+        }
+        if (I.leaf) {
+          int4 q;
+          uint32_t ix = 0;
+          if (wsrc) {
+            ld_wide(wsrc + 2 * (uint64_t)src, q, ix);
+          } else {
+            q = pts[src];
+            if (PICKLIKE) ix = pidx[src];
+          }
+          const uint32_t rgba = (uint32_t)q.w;
+          if (PICKLIKE) {
+            if (!pick_update(&E[slot], pick_key<MODE>(ix, td.level0 + v.level), (uint64_t)rgba | ((uint64_t)ix << 32)))
+              atomicOr(&ctr->error, kErrInternal);
+            atomicAdd(&cnt32[slot], 1u);
+          } else if (narrow) {
+            atomicAdd(&A0[slot], (uint64_t)(rgba & 255u) | ((uint64_t)((rgba >> 8) & 255u) << 32));
+            atomicAdd(&A1[slot], (uint64_t)((rgba >> 16) & 255u) | (1ull << 32));
+          } else {
+            atomicAdd(&A0[slot], (uint64_t)(rgba & 255u));
+            atomicAdd(&A1[slot], (uint64_t)((rgba >> 8) & 255u));
+            atomicAdd(&A2[slot], (uint64_t)((rgba >> 16) & 255u));
+            atomicAdd(&cnt32[slot], 1u);
+          }
+        } else {
+          const int4 vr = v.stage_in[src];
+          if (PICKLIKE) {
+            const uint32_t idx = (uint32_t)vr.w;
+            if (!pick_update(&E[slot], pick_key<MODE>(idx, td.level0 + v.level),
+                             (uint64_t)(uint32_t)vr.y | ((uint64_t)idx << 32)))
+              atomicOr(&ctr->error, kErrInternal);
+            atomicAdd(&cnt32[slot], (uint32_t)vr.z);
+          } else {
+            const ulonglong2 sm = v.stage_in_sum[src];
+            const uint64_t sr = sm.x & kMask40, sg = (sm.x >> 40) | ((sm.y & 0xFFFFull) << 24), sb = sm.y >> 16;
+            if (narrow) {
+              atomicAdd(&A0[slot], sr | (sg << 32));
+              atomicAdd(&A1[slot], sb | ((uint64_t)(uint32_t)vr.z << 32));
+            } else {
+              atomicAdd(&A0[slot], sr);
+              atomicAdd(&A1[slot], sg);
+              atomicAdd(&A2[slot], sb);
+              atomicAdd(&cnt32[slot], (uint32_t)vr.z);
+            }
+          }
+        }
+      }
+    } else if (I.leaf) {
       const uint64_t n = I.n;
       const uint64_t step = 2ull * blockDim.x;
       // Lanes of a warp whose points share a cell are merged first (point
@@ -280,18 +376,19 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
       // colours; returns whether this lane carries the update (a leader, or
       // any lane with a sample in pick mode).
       auto merge = [&](uint32_t key1, const int4& q, uint32_t& r, uint32_t& g, uint32_t& b,
-                       uint32_t& n_same) -> bool {
+                       uint32_t& n_same, unsigned& peers) -> bool {
         const unsigned act = __ballot_sync(0xFFFFFFFFu, key1 != 0u);
         const uint32_t rgba = (uint32_t)q.w;
         r = rgba & 255u;
         g = (rgba >> 8) & 255u;
         b = (rgba >> 16) & 255u;
         n_same = 1;
+        peers = 1u << lane;
         if (key1 == 0u) return false;
         // most pick updates lose the comparison against the entry they
         // read, so the single-sample modes skip the merge
         if (PICKLIKE) return true;
-        const unsigned peers = __match_any_sync(act, key1);
+        peers = __match_any_sync(act, key1);
         n_same = __popc(peers);
         if (n_same > 1) {
           r = __reduce_add_sync(peers, r);
@@ -303,7 +400,7 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
       auto update = [&](int slot, uint32_t key1, const int4& q, uint32_t ix, uint32_t r, uint32_t g, uint32_t b,
                         uint32_t n_same) {
         if (slot < 0) {
-          S.fail = 1;
+          if (!can_spill) S.fail = 1;  // else every lane of the group spills its own sample
           return;
         }
         if (PICKLIKE) {
@@ -324,10 +421,12 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
       // both samples of a pair are merged, then both home slots are read
       // before either probe is resolved, so their shared-memory latencies
       // overlap
-      auto accumulate2 = [&](uint32_t k0, const int4& q0, uint32_t x0, uint32_t k1, const int4& q1, uint32_t x1) {
+      auto accumulate2 = [&](uint32_t k0, const int4& q0, uint32_t x0, uint32_t i0, uint32_t k1, const int4& q1,
+                             uint32_t x1, uint32_t i1) {
         uint32_t r0, g0, b0, n0, r1, g1, b1, n1;
-        const bool l0 = merge(k0, q0, r0, g0, b0, n0);
-        const bool l1 = merge(k1, q1, r1, g1, b1, n1);
+        unsigned p0, p1;
+        const bool l0 = merge(k0, q0, r0, g0, b0, n0, p0);
+        const bool l1 = merge(k1, q1, r1, g1, b1, n1, p1);
         uint32_t h0 = 0, h1 = 0, e0 = 0, e1 = 0;
         if (l0) {
           h0 = home_slot(k0, H);
@@ -337,8 +436,16 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
           h1 = home_slot(k1, H);
           e1 = ((volatile uint32_t*)keys)[h1];
         }
-        if (l0) update(resolve_slot(keys, H, k0, h0, e0), k0, q0, x0, r0, g0, b0, n0);
-        if (l1) update(resolve_slot(keys, H, k1, h1, e1), k1, q1, x1, r1, g1, b1, n1);
+        int s0 = 0, s1 = 0;
+        if (l0) update(s0 = resolve_slot(keys, H, k0, h0, e0), k0, q0, x0, r0, g0, b0, n0);
+        if (l1) update(s1 = resolve_slot(keys, H, k1, h1, e1), k1, q1, x1, r1, g1, b1, n1);
+        if (can_spill) {
+          // a group whose leader found no slot spills all its samples
+          const unsigned f0 = __ballot_sync(0xFFFFFFFFu, l0 && s0 < 0);
+          const unsigned f1 = __ballot_sync(0xFFFFFFFFu, l1 && s1 < 0);
+          spill_warp(k0 != 0u && ((f0 >> (__ffs(p0) - 1)) & 1u), k0, i0);
+          spill_warp(k1 != 0u && ((f1 >> (__ffs(p1) - 1)) & 1u), k1, i1);
+        }
       };
       // Software pipeline over pairs of points: the loads of the next pair
       // are in flight while the current pair is hashed and accumulated.
@@ -389,7 +496,7 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
           k1 = point_key1(q1, I);
           if (part_of(k1, mlog) != part) k1 = 0u;
         }
-        accumulate2(k0, q0, x0, k1, q1, x1);
+        accumulate2(k0, q0, x0, (uint32_t)a0, k1, q1, x1, (uint32_t)a1);
         q0 = r0;
         q1 = r1;
         x0 = y0;
@@ -413,7 +520,8 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
           if (part_of(key1, mlog) != part) continue;
           const int slot = find_or_insert(keys, H, key1);
           if (slot < 0) {
-            S.fail = 1;
+            if (can_spill) spill_one(key1, (uint32_t)(ca.stage + i));
+            else S.fail = 1;
             continue;
           }
           if (PICKLIKE) {
@@ -456,6 +564,7 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
     if (S.fail) {
       split = true;
       if (threadIdx.x == 0) {
+        if (spill_pass || S.spilling) atomicOr(&ctr->error, kErrInternal);  // spill lists only shrink
         bool handed = false;
         if (first && mlog == 0) {
           // the cells of the whole item get one staging block, filled by
@@ -494,18 +603,30 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
 
     // extract this pass's occupied cells into staging
     if (threadIdx.x == 0) {
-      if (first && mlog == 0) {  // the whole item in one pass
+      const bool spilled = can_spill && S.spill_n[sp_out_id] > 0;
+      if (first && mlog == 0 && !spilled) {  // the whole item in one pass
         S.base = atomicAdd(v.stage_used, (unsigned long long)used);
         if (S.base + used > v.stage_cap) atomicOr(&ctr->error, kErrStageCap);
         v.aux[I.g].stage = S.base;
         v.aux[I.g].occ = used;
-      } else {  // one partition: append to the item's block
+      } else {  // one partition or one spill pass: append to the item's block
+        if (first && mlog == 0) {  // the first pass spilled: reserve the item's whole block
+          const unsigned long long blk = atomicAdd(v.stage_used, (unsigned long long)bound);
+          if (blk + bound > v.stage_cap) atomicOr(&ctr->error, kErrStageCap);
+          v.aux[I.g].stage = blk;
+          v.aux[I.g].occ = 0u;
+          S.spilling = 1;
+        }
         const uint64_t blk = v.aux[I.g].stage;
         const uint32_t o = atomicAdd(&v.aux[I.g].occ, used);
         S.base = blk + o;
         if (o + used > bound || blk + o + used > v.stage_cap) atomicOr(&ctr->error, kErrStageCap);
       }
       S.out = 0;
+      if (spilled) {  // next: a pass over the samples this one spilled
+        S.stack[S.sp] = make_uint2(sp_out_id, kSpillMark);
+        S.sp += 1;
+      }
     }
     __syncthreads();
     const bool room = S.base + used <= v.stage_cap;

@@ -57,6 +57,11 @@ struct VoxLevel {
   uint32_t* wcnt;
   uint32_t* wtouch;
   ulonglong2* root_sums;  // filtered: exact sums of the top level's voxels, parallel to dense (or null)
+  // spill lists of the first-attempt kernel: two lists of spill_cap
+  // {cell key, sample position} records per CTA (null: items that overflow
+  // the table are redone in hash partitions right away)
+  uint2* spill;
+  uint32_t spill_cap;
 };
 cudaError_t launch_vox(const BuildArgs& a, const VoxLevel& v, DevCounters* ctr, cudaStream_t st);
 // Section 4.2.4: one persistent CTA per grid over the parents of a level.

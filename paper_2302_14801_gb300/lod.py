@@ -72,7 +72,8 @@ class ServerConfig(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("root_depth", ctypes.c_uint32), ("stream_ctas_per_sm", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 6)]
+                ("dense_bins_max", ctypes.c_uint32), ("vox_spill_records", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 4)]
 
 
 class Camera(ctypes.Structure):
@@ -205,15 +206,18 @@ def profile_read() -> dict:
                                    "alg_bytes": float(arr[i].alg_bytes)} for i in range(n.value)}
 
 
-def set_tuning(root_depth: int = 0, stream_ctas_per_sm: int = 0) -> None:
+def set_tuning(root_depth: int = 0, stream_ctas_per_sm: int = 0, dense_bins_max: int = 0,
+               vox_spill_records: int = 0) -> None:
     """Process-wide speed knobs (never change results); 0 = default."""
-    _check(lib().lod_set_tuning(ctypes.byref(Tuning(int(root_depth), int(stream_ctas_per_sm)))), "lod_set_tuning")
+    t = Tuning(int(root_depth), int(stream_ctas_per_sm), int(dense_bins_max), int(vox_spill_records))
+    _check(lib().lod_set_tuning(ctypes.byref(t)), "lod_set_tuning")
 
 
 def get_tuning() -> dict:
     t = Tuning()
     _check(lib().lod_get_tuning(ctypes.byref(t)), "lod_get_tuning")
-    return {"root_depth": t.root_depth, "stream_ctas_per_sm": t.stream_ctas_per_sm}
+    return {"root_depth": t.root_depth, "stream_ctas_per_sm": t.stream_ctas_per_sm,
+            "dense_bins_max": t.dense_bins_max, "vox_spill_records": t.vox_spill_records}
 
 
 def autotune(points, leaf_threshold=50000, mode=FILTER, max_depth=21, stream=None) -> dict:
@@ -225,7 +229,8 @@ def autotune(points, leaf_threshold=50000, mode=FILTER, max_depth=21, stream=Non
     ms = ctypes.c_float()
     _check(lib().lod_autotune(ptr if n else None, n, ctypes.byref(p), _stream_handle(stream), ctypes.byref(t),
                               ctypes.byref(ms)), "lod_autotune")
-    return {"root_depth": t.root_depth, "stream_ctas_per_sm": t.stream_ctas_per_sm, "ms": ms.value}
+    return {"root_depth": t.root_depth, "stream_ctas_per_sm": t.stream_ctas_per_sm,
+            "dense_bins_max": t.dense_bins_max, "vox_spill_records": t.vox_spill_records, "ms": ms.value}
 
 
 def launch_count() -> int:
