@@ -312,6 +312,14 @@ def _tile_offsets(n_tiles: int, seed0: int) -> list:
     return out
 
 
+def apply_tuning(args):
+    """The --tuning knobs (lod_set_tuning), if any."""
+    tuning = {k: int(v) for k, v in (kv.split("=") for kv in args.tuning.split(",") if kv)}
+    if tuning:
+        from paper_2302_14801_gb300 import lod
+        lod.set_tuning(**tuning)
+
+
 def run_batched(args):
     """Many independent tiles (point counts log-uniform in [1e4, tile_max],
     each a sphere with its own seed and bbox), filtered mode, built with one
@@ -323,6 +331,7 @@ def run_batched(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2302_14801_gb300 import lod, synth, synth_gpu
+    apply_tuning(args)
     T = 50000
     sizes = synth.tile_sizes(args.tiles, 1e4, args.tile_max, seed=4 + rank)
     offs = _tile_offsets(args.tiles, 1000 + 100000 * rank)
@@ -391,7 +400,7 @@ def run_batched(args):
             "single_calls": {"value": total / (t_single * 1e-3) / 1e6, "unit": "M points/s",
                              "ms": t_single, "what": "the same tiles, one lod_build call each"},
             "batched_vs_single_calls": t_single / t_batch,
-            "wave_ms": wave_ms, "gpu_launches": launches,
+            "wave_ms": wave_ms, "gpu_launches": launches, "tuning": lod.get_tuning(),
         }
         print(json.dumps(line), flush=True)
     return 0
@@ -411,6 +420,7 @@ def run_serve(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2302_14801_gb300 import lod, synth, synth_gpu
+    apply_tuning(args)
     T = 50000
     n_max = 50_000_000
     g = torch.Generator(device="cuda")
@@ -532,10 +542,8 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     from paper_2302_14801_gb300 import lod
+    apply_tuning(args)
 
-    tuning = {k: int(v) for k, v in (kv.split("=") for kv in args.tuning.split(",") if kv)}
-    if tuning:
-        lod.set_tuning(**tuning)
     name = args.workload
     _, n, _, T = WORKLOADS[name]
     if on_device(name):

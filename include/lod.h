@@ -335,13 +335,18 @@ int lod_root_cubes_noalloc(const lod_point_t* const* d_tiles, const uint64_t* n,
  *                   slot in the CTA's shared-memory table goes there and is
  *                   processed by another pass, instead of the item being
  *                   redone in hash partitions (default 65536; 1 turns the
- *                   lists off). */
+ *                   lists off).
+ *   graph_voxel_levels  1: every build captures the launches of all its
+ *                   voxel levels (which need no host round trip between
+ *                   them) into one CUDA graph and launches that (0: plain
+ *                   launches, the default).  Ignored while profiling. */
 typedef struct lod_tuning {
   uint32_t root_depth;
   uint32_t stream_ctas_per_sm;
   uint32_t dense_bins_max;
   uint32_t vox_spill_records;
-  uint32_t reserved[4];
+  uint32_t graph_voxel_levels;
+  uint32_t reserved[3];
 } lod_tuning_t;
 
 int lod_set_tuning(const lod_tuning_t* t);

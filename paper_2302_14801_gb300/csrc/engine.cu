@@ -281,6 +281,41 @@ std::atomic<uint32_t> g_tune_root_depth{0};
 std::atomic<uint32_t> g_tune_ctas_per_sm{0};
 std::atomic<uint32_t> g_tune_spill_cap{0};  // 0: default, 1: no spill lists
 std::atomic<uint32_t> g_tune_dense_bins{0};  // 0: kSmemBins
+std::atomic<uint32_t> g_tune_graph{0};       // 1: the voxel levels run as one CUDA graph
+
+// Stream capture of a build's voxel levels into a CUDA graph, launched as
+// one unit; a capture still open when the build returns early is ended and
+// dropped.
+struct GraphCapture {
+  cudaStream_t st;
+  bool active = false;
+  explicit GraphCapture(cudaStream_t s) : st(s) {}
+  GraphCapture(const GraphCapture&) = delete;
+  cudaError_t begin() {
+    const cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    active = e == cudaSuccess;
+    return e;
+  }
+  cudaError_t launch() {
+    active = false;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (e != cudaSuccess) return e;
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(x, st);
+    if (x) cudaGraphExecDestroy(x);  // an executable graph in flight is freed when it completes
+    cudaGraphDestroy(g);
+    return e;
+  }
+  ~GraphCapture() {
+    if (!active) return;
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(st, &g);
+    if (g) cudaGraphDestroy(g);
+    (void)cudaGetLastError();
+  }
+};
 
 uint32_t choose_root_depth(uint64_t n, uint32_t T, uint32_t log2S, uint32_t max_depth) {
   if (n <= T || log2S == 0 || max_depth == 0) return 0;
@@ -476,7 +511,8 @@ int set_tuning(const lod_tuning_t& t) {
   if (t.root_depth > kRootMaxD || t.stream_ctas_per_sm > 8) return LOD_ERR_INVALID_ARG;
   const uint32_t b = t.dense_bins_max;
   if (b && (b != 8 && b != 64 && b != 512 && b != 4096)) return LOD_ERR_INVALID_ARG;
-  if (t.vox_spill_records > (1u << 24)) return LOD_ERR_INVALID_ARG;
+  if (t.vox_spill_records > (1u << 24) || t.graph_voxel_levels > 1) return LOD_ERR_INVALID_ARG;
+  g_tune_graph.store(t.graph_voxel_levels);
   g_tune_root_depth.store(t.root_depth);
   g_tune_ctas_per_sm.store(t.stream_ctas_per_sm);
   g_tune_dense_bins.store(b);
@@ -490,6 +526,7 @@ int get_tuning(lod_tuning_t* t) {
   t->stream_ctas_per_sm = g_tune_ctas_per_sm.load();
   t->dense_bins_max = g_tune_dense_bins.load();
   t->vox_spill_records = g_tune_spill_cap.load();
+  t->graph_voxel_levels = g_tune_graph.load();
   return LOD_OK;
 }
 
@@ -1166,6 +1203,14 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
     LOD_CK(cudaMemsetAsync(d_tvox.p, 0, nt * 8, st));
     LOD_CK(cudaMemsetAsync(d_lctr.p, 0, lctr_bytes, st));
     LOD_CK(cudaMemsetAsync(d_vstate.p, 0, 2 * sizeof(unsigned long long), st));
+    // optionally, every level's launches go into one CUDA graph (the
+    // levels need no host round trip, so they can be captured as a unit)
+    GraphCapture cap(st);
+    const bool use_graph = g_tune_graph.load() != 0 && !prof.on && n_vlev > 0;
+    if (use_graph) {
+      vox_init();  // kernel attributes are set outside the capture
+      LOD_CK(cap.begin());
+    }
     VoxLevel vl;
     std::memset(&vl, 0, sizeof(vl));
     for (int l = n_vlev - 1; l >= 0; --l) {
@@ -1215,6 +1260,7 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
       LOD_LAUNCH("publish_top", 0, launch_copy_items(A, vl, st));
       vl.root_sums = nullptr;
     }
+    if (use_graph) LOD_CK(cap.launch());
     LOD_CK(cudaMemcpyAsync(lctr.data(), d_lctr.p, lctr_bytes, cudaMemcpyDeviceToHost, st));
     LOD_CK(cudaMemcpyAsync(vstate, d_vstate.p, sizeof(vstate), cudaMemcpyDeviceToHost, st));
     LOD_CK(cudaMemcpyAsync(tvox.data(), d_tvox.p, nt * 8, cudaMemcpyDeviceToHost, st));

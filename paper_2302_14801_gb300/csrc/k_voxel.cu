@@ -766,15 +766,30 @@ __global__ void k_vox_split(BuildArgs a, VoxLevel v, DevCounters* __restrict__ c
 }
 
 template <int MODE>
-static cudaError_t launch_vox_mode(const BuildArgs& a, const VoxLevel& v, DevCounters* ctr, cudaStream_t st) {
+static void vox_attrs() {
+  cudaFuncSetAttribute(k_vox<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  cudaFuncSetAttribute(k_vox_units<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+}
+
+// One-time kernel attributes of the voxel pass (called before any launch,
+// and before a stream capture of the voxel levels); returns the SM count.
+int vox_init() {
   static int sms = [] {
-    cudaFuncSetAttribute(k_vox<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    cudaFuncSetAttribute(k_vox_units<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    vox_attrs<LOD_FILTER>();
+    vox_attrs<LOD_PICK>();
+    vox_attrs<LOD_FIRST>();
+    vox_attrs<LOD_RANDOM>();
     int dev = 0, n = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     return n > 0 ? n : 1;
   }();
+  return sms;
+}
+
+template <int MODE>
+static cudaError_t launch_vox_mode(const BuildArgs& a, const VoxLevel& v, DevCounters* ctr, cudaStream_t st) {
+  const int sms = vox_init();
   if (v.units && v.n_items * 4u <= (uint32_t)sms) {
     uint32_t m = 0;
     while (m < 3 && (v.n_items << (m + 1)) <= (uint32_t)sms) ++m;

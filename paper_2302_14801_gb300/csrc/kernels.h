@@ -80,6 +80,7 @@ cudaError_t launch_gather_voxels(const lod_node_t* nodes, uint32_t n_nodes, cons
                                  const int4* src, int4* dst, cudaStream_t st);
 
 int vox_smem_bytes();
+int vox_init();
 
 // ----- out-of-core build (Section 7) -----
 struct OocGrid {  // top grid: 8^D cells at depth D below the root cube [min, min + 2^L)^3

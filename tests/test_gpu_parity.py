@@ -405,3 +405,25 @@ def test_full_precision_voxel_points(lod, mode):
         with pytest.raises(lod.LodError) as e:
             lod.build(d, 5000, m, full_precision=True)
         assert e.value.status == lod.LOD_ERR_INVALID_ARG
+
+
+# ------------------------------------------------- CUDA-graph voxel levels
+
+def test_graph_captured_voxel_levels_equal_oracle(lod):
+    # with graph_voxel_levels every build launches its voxel levels as one
+    # captured CUDA graph: single and batched builds, every mode
+    import torch
+    pts = synth.aerial(700_000, seed=45, n_buildings=30)
+    sizes = [0, 1, 5000, 70_000, 300_000]
+    tiles = [synth.sphere_tile(int(m), seed=600 + i) for i, m in enumerate(sizes)]
+    before = lod.get_tuning()
+    try:
+        lod.set_tuning(graph_voxel_levels=1)
+        for mode in (0, 1, 2, 3, 4):
+            compare(gpu_build(lod, pts, 5000, mode), oracle.build(pts, 5000, mode, 21), inp=pts)
+        rs = lod.build_batched([torch.from_numpy(t).cuda() for t in tiles], 20000, 0)
+        for t, r in zip(tiles, rs):
+            compare(r.to_host(), oracle.build(t, 20000, 0, 21), inp=t)
+            r.free()
+    finally:
+        lod.set_tuning(**before)
