@@ -44,8 +44,9 @@ WORKLOADS = {
     "aerial50m": ("aerial", 50_000_000, 2, 50000),
     "sphere1m": ("sphere", 1_000_000, 1, 50000),
     "indoor100m": ("indoor", 100_000_000, 3, 50000),
-    # small case of the aerial workload (inputs still larger than L2) for profiler captures
+    # small cases (inputs still larger than L2) for profiler captures
     "aerial12m": ("aerial", 12_000_000, 2, 50000),
+    "indoor20m": ("indoor", 20_000_000, 3, 50000),
     # the billion-point indoor scan, drawn on the device (same recipe, torch RNG)
     "indoor1b": ("indoor_gpu", 1_000_000_000, 3, 50000),
 }

@@ -33,7 +33,10 @@ constexpr uint32_t kHp = kSmemBytes / 24;  // pick: key + {u64 hash, u64 payload
 constexpr uint64_t kNarrowMaxSamples = 0xFFFFFFFFull / 255;  // 32-bit channel sums cannot overflow
 constexpr uint64_t kMask40 = (1ull << 40) - 1;
 
-constexpr uint32_t kProbe = 48;  // longest probe sequence before the table counts as full
+constexpr uint32_t kProbe = 48;       // longest probe sequence before the table counts as full
+constexpr uint32_t kProbeSpill = 8;   // ... in passes that spill: cells that find no slot this close to
+                                      // home go to the spill list, so the table stays at a load where
+                                      // every lookup is short
 
 // Cells one table pass can be expected to hold (linear probing stays short
 // up to about three quarters full); sizes the partitioning after an overflow.
@@ -76,8 +79,9 @@ __device__ __forceinline__ bool pick_update(ulonglong2* e, uint64_t h, uint64_t 
 // consecutive slots hold other cells: the table is too full and the item
 // is redone in more partitions.  No shared fill counter is updated, so
 // inserts of different warps never serialise on one address.
-__device__ __forceinline__ int resolve_slot(uint32_t* keys, uint32_t H, uint32_t key1, uint32_t slot, uint32_t k) {
-  for (uint32_t probe = 0; probe < kProbe; ++probe) {
+__device__ __forceinline__ int resolve_slot(uint32_t* keys, uint32_t H, uint32_t key1, uint32_t slot, uint32_t k,
+                                            uint32_t limit = kProbe) {
+  for (uint32_t probe = 0; probe < limit; ++probe) {
     if (k == key1) return (int)slot;
     if (k == 0u) {
       const uint32_t old = atomicCAS(&keys[slot], 0u, key1);
@@ -89,9 +93,9 @@ __device__ __forceinline__ int resolve_slot(uint32_t* keys, uint32_t H, uint32_t
   return -1;
 }
 
-__device__ __forceinline__ int find_or_insert(uint32_t* keys, uint32_t H, uint32_t key1) {
+__device__ __forceinline__ int find_or_insert(uint32_t* keys, uint32_t H, uint32_t key1, uint32_t limit = kProbe) {
   const uint32_t slot = home_slot(key1, H);
-  return resolve_slot(keys, H, key1, slot, ((volatile uint32_t*)keys)[slot]);
+  return resolve_slot(keys, H, key1, slot, ((volatile uint32_t*)keys)[slot], limit);
 }
 
 struct ItemInfo {
@@ -261,6 +265,7 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
     const uint32_t sp_out_id = spill_pass ? 1u - part : 0u;
     uint2* const sp_out = can_spill ? v.spill + ((uint64_t)blockIdx.x * 2 + sp_out_id) * v.spill_cap : nullptr;
     const uint2* const sp_in = spill_pass ? v.spill + ((uint64_t)blockIdx.x * 2 + part) * v.spill_cap : nullptr;
+    const uint32_t probe_limit = can_spill ? kProbeSpill : kProbe;
     if (!S.clean) {
       // an empty entry is all zero bytes in filtered mode whatever the
       // table's layout, so a clean table serves every item
@@ -314,7 +319,7 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
         const uint2 sr = sp_in[i];
         const uint32_t key1 = sr.x, src = sr.y;
         ++seen;
-        const int slot = find_or_insert(keys, H, key1);
+        const int slot = find_or_insert(keys, H, key1, probe_limit);
         if (slot < 0) {
           spill_one(key1, src);
           continue;
@@ -437,10 +442,11 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
           e1 = ((volatile uint32_t*)keys)[h1];
         }
         int s0 = 0, s1 = 0;
-        if (l0) update(s0 = resolve_slot(keys, H, k0, h0, e0), k0, q0, x0, r0, g0, b0, n0);
-        if (l1) update(s1 = resolve_slot(keys, H, k1, h1, e1), k1, q1, x1, r1, g1, b1, n1);
-        if (can_spill) {
-          // a group whose leader found no slot spills all its samples
+        if (l0) update(s0 = resolve_slot(keys, H, k0, h0, e0, probe_limit), k0, q0, x0, r0, g0, b0, n0);
+        if (l1) update(s1 = resolve_slot(keys, H, k1, h1, e1, probe_limit), k1, q1, x1, r1, g1, b1, n1);
+        // a group whose leader found no slot spills all its samples (one
+        // vote when no lane of the warp failed)
+        if (can_spill && __any_sync(0xFFFFFFFFu, (l0 && s0 < 0) || (l1 && s1 < 0))) {
           const unsigned f0 = __ballot_sync(0xFFFFFFFFu, l0 && s0 < 0);
           const unsigned f1 = __ballot_sync(0xFFFFFFFFu, l1 && s1 < 0);
           spill_warp(k0 != 0u && ((f0 >> (__ffs(p0) - 1)) & 1u), k0, i0);
@@ -518,7 +524,7 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
           if (part == 0 && fits) dst[i] = vr;  // publish the child's voxel (idempotent)
           const uint32_t key1 = voxel_key1((uint32_t)vr.x);
           if (part_of(key1, mlog) != part) continue;
-          const int slot = find_or_insert(keys, H, key1);
+          const int slot = find_or_insert(keys, H, key1, probe_limit);
           if (slot < 0) {
             if (can_spill) spill_one(key1, (uint32_t)(ca.stage + i));
             else S.fail = 1;
