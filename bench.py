@@ -518,7 +518,7 @@ def main():
     ap.add_argument("--tiles", type=int, default=2048, help="batched: number of tiles")
     ap.add_argument("--tile-max", type=float, default=2e7, help="batched: largest tile size (points)")
     ap.add_argument("--wave-points", type=float, default=1e9, help="batched: points built per wave")
-    ap.add_argument("--rates", default="10,20,50,100,200,500", help="serve: arrival rates (requests/s)")
+    ap.add_argument("--rates", default="10,20,50,100,200,500,1000,2000", help="serve: arrival rates (requests/s)")
     ap.add_argument("--requests", type=int, default=200, help="serve: timed requests per rate")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: HBM budget")
     ap.add_argument("--inflight", type=int, default=8, help="serve: concurrent builds")

@@ -284,22 +284,30 @@ std::atomic<uint32_t> g_tune_dense_bins{0};  // 0: kSmemBins
 std::atomic<uint32_t> g_tune_graph{0};       // 1: the voxel levels run as one CUDA graph
 
 // Stream capture of a build's voxel levels into a CUDA graph, launched as
-// one unit; a capture still open when the build returns early is ended and
-// dropped.
+// one unit on the build's stream.  The capture runs on a stream of the
+// calling thread's own (the legacy default stream cannot be captured); a
+// capture still open when the build returns early is ended and dropped.
 struct GraphCapture {
-  cudaStream_t st;
+  cudaStream_t st;   // the build's stream: the graph is launched here
+  cudaStream_t cap = nullptr;
   bool active = false;
   explicit GraphCapture(cudaStream_t s) : st(s) {}
   GraphCapture(const GraphCapture&) = delete;
   cudaError_t begin() {
-    const cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    thread_local cudaStream_t own = nullptr;
+    if (!own) {
+      const cudaError_t e = cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return e;
+    }
+    cap = own;
+    const cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     active = e == cudaSuccess;
     return e;
   }
   cudaError_t launch() {
     active = false;
     cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamEndCapture(st, &g);
+    cudaError_t e = cudaStreamEndCapture(cap, &g);
     if (e != cudaSuccess) return e;
     cudaGraphExec_t x = nullptr;
     e = cudaGraphInstantiate(&x, g, 0);
@@ -311,7 +319,7 @@ struct GraphCapture {
   ~GraphCapture() {
     if (!active) return;
     cudaGraph_t g = nullptr;
-    cudaStreamEndCapture(st, &g);
+    cudaStreamEndCapture(cap, &g);
     if (g) cudaGraphDestroy(g);
     (void)cudaGetLastError();
   }
@@ -1211,6 +1219,7 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
       vox_init();  // kernel attributes are set outside the capture
       LOD_CK(cap.begin());
     }
+    const cudaStream_t vst = use_graph ? cap.cap : st;  // where the levels are enqueued
     VoxLevel vl;
     std::memset(&vl, 0, sizeof(vl));
     for (int l = n_vlev - 1; l >= 0; --l) {
@@ -1244,20 +1253,20 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
         vl.wcnt = reinterpret_cast<uint32_t*>(wbase + (size_t)wctas * cells * 32);
         vl.wtouch = reinterpret_cast<uint32_t*>(wbase + (size_t)wctas * cells * 36);
         LOD_LAUNCH(debug_stats() ? kVoxLevelNames[l] : "voxelize", 0,
-                   launch_wvox(A, vl, lc, (int)std::min<uint32_t>((uint32_t)wctas, n_par), st));
+                   launch_wvox(A, vl, lc, (int)std::min<uint32_t>((uint32_t)wctas, n_par), vst));
       } else {
-        LOD_LAUNCH(debug_stats() ? kVoxLevelNames[l] : "voxelize", 0, launch_vox(A, vl, lc, st));
+        LOD_LAUNCH(debug_stats() ? kVoxLevelNames[l] : "voxelize", 0, launch_vox(A, vl, lc, vst));
       }
       vox_rec[l] = prof.recs.size();
       LOD_LAUNCH("level_scan", 0,
                  launch_level_scan(A, vl, d_pref.as<uint32_t>() + (size_t)l * pstride + (nt + 1), n_par,
-                                   d_tvox.as<unsigned long long>(), lc, st));
+                                   d_tvox.as<unsigned long long>(), lc, vst));
     }
     if (n_vlev > 0) {
       // the roots' voxels: the items of the top level have no parent pass
       // that would copy their staged records
       vl.root_sums = d_rsums.as<ulonglong2>();
-      LOD_LAUNCH("publish_top", 0, launch_copy_items(A, vl, st));
+      LOD_LAUNCH("publish_top", 0, launch_copy_items(A, vl, vst));
       vl.root_sums = nullptr;
     }
     if (use_graph) LOD_CK(cap.launch());
