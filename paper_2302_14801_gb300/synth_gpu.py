@@ -83,8 +83,14 @@ def indoor(n: int, seed: int = 3, n_prims: int = 4096, cube_log2: int = 22, sigm
     s = 0
     chunk = 1 << 24
     for i in range(n_prims):
-        q, _ = torch.linalg.qr(torch.randn((3, 3), generator=gen, **f64))
-        t1, t2, nrm = q[:, 0], q[:, 1], q[:, 2]
+        # a random orthonormal frame: Gram-Schmidt on two Gaussian vectors
+        # (plain tensor arithmetic, no linear-algebra library)
+        g2 = torch.randn((2, 3), generator=gen, **f64)
+        t1 = g2[0] / g2[0].norm()
+        t2 = g2[1] - (g2[1] @ t1) * t1
+        t2 = t2 / t2.norm()
+        nrm = torch.stack([t1[1] * t2[2] - t1[2] * t2[1], t1[2] * t2[0] - t1[0] * t2[2],
+                           t1[0] * t2[1] - t1[1] * t2[0]])
         done = 0
         while done < counts[i]:
             m = min(chunk, counts[i] - done)
