@@ -339,14 +339,18 @@ int lod_root_cubes_noalloc(const lod_point_t* const* d_tiles, const uint64_t* n,
  *   graph_voxel_levels  1: every build captures the launches of all its
  *                   voxel levels (which need no host round trip between
  *                   them) into one CUDA graph and launches that (0: plain
- *                   launches, the default).  Ignored while profiling. */
+ *                   launches, the default).  Ignored while profiling.
+ *   vox_no_merge    1: in filtered mode the lanes of a warp whose points share
+ *                   a cell do not add their colours together before updating
+ *                   the table (0: they do, the default). */
 typedef struct lod_tuning {
   uint32_t root_depth;
   uint32_t stream_ctas_per_sm;
   uint32_t dense_bins_max;
   uint32_t vox_spill_records;
   uint32_t graph_voxel_levels;
-  uint32_t reserved[3];
+  uint32_t vox_no_merge;
+  uint32_t reserved[2];
 } lod_tuning_t;
 
 int lod_set_tuning(const lod_tuning_t* t);
@@ -356,8 +360,8 @@ int lod_get_tuning(lod_tuning_t* t);
  * params; on `stream`) under candidate tunings, two builds each (the first
  * untimed), by coordinate descent from the defaults: stream_ctas_per_sm 1
  * and 3; root_depth one less and one more than the default; dense_bins_max
- * 512; vox_spill_records 1 (off) and 262144 — each knob in turn, the others
- * held at the best so far.  Keeps the fastest with lod_set_tuning and
+ * 512; vox_spill_records 1 (off) and 262144; in filtered mode
+ * vox_no_merge 1 — each knob in turn, the others held at the best so far.  Keeps the fastest with lod_set_tuning and
  * returns it in *best (and its build time in *best_ms when not NULL).
  * Results are freed; nothing else is kept.  Costs about 16 builds; like
  * lod_set_tuning it changes process-wide state, so call it while no other

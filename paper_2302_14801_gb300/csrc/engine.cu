@@ -282,6 +282,7 @@ std::atomic<uint32_t> g_tune_ctas_per_sm{0};
 std::atomic<uint32_t> g_tune_spill_cap{0};  // 0: default, 1: no spill lists
 std::atomic<uint32_t> g_tune_dense_bins{0};  // 0: kSmemBins
 std::atomic<uint32_t> g_tune_graph{0};       // 1: the voxel levels run as one CUDA graph
+std::atomic<uint32_t> g_tune_no_merge{0};    // 1: no warp merge of same-cell samples in the voxel pass
 
 // Stream capture of a build's voxel levels into a CUDA graph, launched as
 // one unit on the build's stream.  The capture runs on a stream of the
@@ -519,8 +520,9 @@ int set_tuning(const lod_tuning_t& t) {
   if (t.root_depth > kRootMaxD || t.stream_ctas_per_sm > 8) return LOD_ERR_INVALID_ARG;
   const uint32_t b = t.dense_bins_max;
   if (b && (b != 8 && b != 64 && b != 512 && b != 4096)) return LOD_ERR_INVALID_ARG;
-  if (t.vox_spill_records > (1u << 24) || t.graph_voxel_levels > 1) return LOD_ERR_INVALID_ARG;
+  if (t.vox_spill_records > (1u << 24) || t.graph_voxel_levels > 1 || t.vox_no_merge > 1) return LOD_ERR_INVALID_ARG;
   g_tune_graph.store(t.graph_voxel_levels);
+  g_tune_no_merge.store(t.vox_no_merge);
   g_tune_root_depth.store(t.root_depth);
   g_tune_ctas_per_sm.store(t.stream_ctas_per_sm);
   g_tune_dense_bins.store(b);
@@ -535,6 +537,7 @@ int get_tuning(lod_tuning_t* t) {
   t->dense_bins_max = g_tune_dense_bins.load();
   t->vox_spill_records = g_tune_spill_cap.load();
   t->graph_voxel_levels = g_tune_graph.load();
+  t->vox_no_merge = g_tune_no_merge.load();
   return LOD_OK;
 }
 
@@ -1248,6 +1251,7 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
       vl.n_parents = n_par;
       vl.spill = d_spill.as<uint2>();
       vl.spill_cap = d_spill.p ? spill_cap : 0u;
+      vl.no_merge = g_tune_no_merge.load();
       if (weighted) {
         vl.wgrid = reinterpret_cast<unsigned long long*>(wbase);
         vl.wcnt = reinterpret_cast<uint32_t*>(wbase + (size_t)wctas * cells * 32);

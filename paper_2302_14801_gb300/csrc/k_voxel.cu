@@ -391,8 +391,9 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
         peers = 1u << lane;
         if (key1 == 0u) return false;
         // most pick updates lose the comparison against the entry they
-        // read, so the single-sample modes skip the merge
-        if (PICKLIKE) return true;
+        // read, so the single-sample modes skip the merge (and so does the
+        // filtered mode when tuned to)
+        if (PICKLIKE || v.no_merge) return true;
         peers = __match_any_sync(act, key1);
         n_same = __popc(peers);
         if (n_same > 1) {

@@ -62,6 +62,7 @@ struct VoxLevel {
   // the table are redone in hash partitions right away)
   uint2* spill;
   uint32_t spill_cap;
+  uint32_t no_merge;  // 1: filtered samples of a warp that share a cell are not merged before the table
 };
 cudaError_t launch_vox(const BuildArgs& a, const VoxLevel& v, DevCounters* ctr, cudaStream_t st);
 // Section 4.2.4: one persistent CTA per grid over the parents of a level.

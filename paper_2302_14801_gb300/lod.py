@@ -73,7 +73,8 @@ class ServerConfig(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("root_depth", ctypes.c_uint32), ("stream_ctas_per_sm", ctypes.c_uint32),
                 ("dense_bins_max", ctypes.c_uint32), ("vox_spill_records", ctypes.c_uint32),
-                ("graph_voxel_levels", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+                ("graph_voxel_levels", ctypes.c_uint32), ("vox_no_merge", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 2)]
 
 
 class Camera(ctypes.Structure):
@@ -207,10 +208,10 @@ def profile_read() -> dict:
 
 
 def set_tuning(root_depth: int = 0, stream_ctas_per_sm: int = 0, dense_bins_max: int = 0,
-               vox_spill_records: int = 0, graph_voxel_levels: int = 0) -> None:
+               vox_spill_records: int = 0, graph_voxel_levels: int = 0, vox_no_merge: int = 0) -> None:
     """Process-wide speed knobs (never change results); 0 = default."""
     t = Tuning(int(root_depth), int(stream_ctas_per_sm), int(dense_bins_max), int(vox_spill_records),
-               int(graph_voxel_levels))
+               int(graph_voxel_levels), int(vox_no_merge))
     _check(lib().lod_set_tuning(ctypes.byref(t)), "lod_set_tuning")
 
 
@@ -219,7 +220,7 @@ def get_tuning() -> dict:
     _check(lib().lod_get_tuning(ctypes.byref(t)), "lod_get_tuning")
     return {"root_depth": t.root_depth, "stream_ctas_per_sm": t.stream_ctas_per_sm,
             "dense_bins_max": t.dense_bins_max, "vox_spill_records": t.vox_spill_records,
-            "graph_voxel_levels": t.graph_voxel_levels}
+            "graph_voxel_levels": t.graph_voxel_levels, "vox_no_merge": t.vox_no_merge}
 
 
 def autotune(points, leaf_threshold=50000, mode=FILTER, max_depth=21, stream=None) -> dict:
@@ -233,7 +234,7 @@ def autotune(points, leaf_threshold=50000, mode=FILTER, max_depth=21, stream=Non
                               ctypes.byref(ms)), "lod_autotune")
     return {"root_depth": t.root_depth, "stream_ctas_per_sm": t.stream_ctas_per_sm,
             "dense_bins_max": t.dense_bins_max, "vox_spill_records": t.vox_spill_records,
-            "graph_voxel_levels": t.graph_voxel_levels, "ms": ms.value}
+            "graph_voxel_levels": t.graph_voxel_levels, "vox_no_merge": t.vox_no_merge, "ms": ms.value}
 
 
 def launch_count() -> int:

@@ -104,7 +104,7 @@ def test_tuning_is_checked_and_restorable(lodmod):
     try:
         lodmod.set_tuning(root_depth=5, stream_ctas_per_sm=3, dense_bins_max=512, vox_spill_records=1000)
         assert lodmod.get_tuning() == {"root_depth": 5, "stream_ctas_per_sm": 3, "dense_bins_max": 512,
-                                       "vox_spill_records": 1000, "graph_voxel_levels": 0}
+                                       "vox_spill_records": 1000, "graph_voxel_levels": 0, "vox_no_merge": 0}
     finally:
         lodmod.set_tuning(**before)
     assert lodmod.get_tuning() == before

@@ -149,8 +149,9 @@ def test_tuning_never_changes_results(lod, mode):
     try:
         # (spill lists of 2 records overflow at once: items fall back to hash
         # partitions after a partial spill; 1 turns the lists off)
-        for rd, cps, bins, spill in ((1, 1, 8, 1), (3, 0, 64, 0), (5, 3, 512, 2), (8, 2, 4096, 262144)):
-            lod.set_tuning(rd, cps, bins, spill)
+        for rd, cps, bins, spill, merge in ((1, 1, 8, 1, 1), (3, 0, 64, 0, 0), (5, 3, 512, 2, 1),
+                                            (8, 2, 4096, 262144, 0)):
+            lod.set_tuning(rd, cps, bins, spill, 0, merge)
             compare(gpu_build(lod, pts, 5000, mode), want, inp=pts)
     finally:
         lod.set_tuning(0, 0)
