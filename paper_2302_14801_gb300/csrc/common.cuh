@@ -177,7 +177,11 @@ __device__ __forceinline__ void ld_wide(const int4* p, int4& q, uint32_t& idx) {
 // integer division.
 __device__ __forceinline__ uint32_t round_mean(uint64_t s, uint64_t n) {
   const uint64_t num = s + (n >> 1);
-  uint32_t q = (uint32_t)__fdividef((float)num, (float)n);
+  // 64-bit integer to float conversions run on the FP64 pipe, which is
+  // narrow on this GPU: convert 32-bit values where they fit
+  const float fnum = (num >> 32) ? (float)num : __uint2float_rn((uint32_t)num);
+  const float fn = (n >> 32) ? (float)n : __uint2float_rn((uint32_t)n);
+  uint32_t q = (uint32_t)__fdividef(fnum, fn);
   q = q > 255u ? 255u : q;
   if ((uint64_t)q * n > num) --q;
   else if ((uint64_t)(q + 1) * n <= num) ++q;

@@ -554,21 +554,20 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
       }
     }
     __syncthreads();  // every insert of the pass is done
-    // occupied cells of this pass, and how far the pass got
-    {
-      uint32_t mine = 0;
-      for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) mine += keys[i] != 0u ? 1u : 0u;
-      mine = __reduce_add_sync(0xFFFFFFFFu, mine);
-      seen = __reduce_add_sync(0xFFFFFFFFu, seen);
-      if (lane == 0) {
-        if (mine) atomicAdd(&S.used, mine);
-        if (seen) atomicAdd(&S.seen, seen);
-      }
-    }
-    __syncthreads();
-    const uint32_t used = S.used;
-
     if (S.fail) {
+      // occupied cells of this pass, and how far the pass got
+      {
+        uint32_t mine = 0;
+        for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) mine += keys[i] != 0u ? 1u : 0u;
+        mine = __reduce_add_sync(0xFFFFFFFFu, mine);
+        seen = __reduce_add_sync(0xFFFFFFFFu, seen);
+        if (lane == 0) {
+          if (mine) atomicAdd(&S.used, mine);
+          if (seen) atomicAdd(&S.seen, seen);
+        }
+      }
+      __syncthreads();
+      const uint32_t used = S.used;
       split = true;
       if (threadIdx.x == 0) {
         if (spill_pass || S.spilling) atomicOr(&ctr->error, kErrInternal);  // spill lists only shrink
@@ -608,95 +607,117 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
       continue;
     }
 
-    // extract this pass's occupied cells into staging
+    // extract this pass's occupied cells into the item's staging block: the
+    // item's first pass reserves its whole block (at most min(samples,
+    // 64^3) cells, what the level's staging is sized for), and every warp
+    // appends its cells through the item's counter
     if (threadIdx.x == 0) {
       const bool spilled = can_spill && S.spill_n[sp_out_id] > 0;
-      if (first && mlog == 0 && !spilled) {  // the whole item in one pass
-        S.base = atomicAdd(v.stage_used, (unsigned long long)used);
-        if (S.base + used > v.stage_cap) atomicOr(&ctr->error, kErrStageCap);
-        v.aux[I.g].stage = S.base;
-        v.aux[I.g].occ = used;
-      } else {  // one partition or one spill pass: append to the item's block
-        if (first && mlog == 0) {  // the first pass spilled: reserve the item's whole block
-          const unsigned long long blk = atomicAdd(v.stage_used, (unsigned long long)bound);
-          if (blk + bound > v.stage_cap) atomicOr(&ctr->error, kErrStageCap);
-          v.aux[I.g].stage = blk;
-          v.aux[I.g].occ = 0u;
-          S.spilling = 1;
-        }
-        const uint64_t blk = v.aux[I.g].stage;
-        const uint32_t o = atomicAdd(&v.aux[I.g].occ, used);
-        S.base = blk + o;
-        if (o + used > bound || blk + o + used > v.stage_cap) atomicOr(&ctr->error, kErrStageCap);
+      if (first && mlog == 0) {
+        const unsigned long long blk = atomicAdd(v.stage_used, (unsigned long long)bound);
+        if (blk + bound > v.stage_cap) atomicOr(&ctr->error, kErrStageCap);
+        v.aux[I.g].stage = blk;
+        v.aux[I.g].occ = 0u;
+        if (spilled) S.spilling = 1;
       }
-      S.out = 0;
+      S.base = v.aux[I.g].stage;
       if (spilled) {  // next: a pass over the samples this one spilled
         S.stack[S.sp] = make_uint2(sp_out_id, kSpillMark);
         S.sp += 1;
       }
     }
     __syncthreads();
-    const bool room = S.base + used <= v.stage_cap;
-    for (uint32_t i0 = 0; i0 < H; i0 += blockDim.x) {
-      const uint32_t i = i0 + threadIdx.x;
-      const uint32_t key1 = i < H ? keys[i] : 0u;
-      const bool occ = key1 != 0u;
-      const unsigned bal = __ballot_sync(0xFFFFFFFFu, occ);
-      uint32_t wbase = 0;
-      if (lane == 0 && bal) wbase = atomicAdd(&S.out, (uint32_t)__popc(bal));
-      wbase = __shfl_sync(0xFFFFFFFFu, wbase, 0);
-      if (!occ) continue;
-      // read the entry and leave it empty for the next pass or item
-      keys[i] = 0u;
-      ulonglong2 e = make_ulonglong2(0ull, 0ull);
-      uint32_t c32 = 0;
-      uint64_t sr = 0, sg = 0, sb = 0, n = 0;
-      if (PICKLIKE) {
-        e = E[i];
-        c32 = cnt32[i];
-        E[i] = make_ulonglong2(~0ull, 0ull);
-        cnt32[i] = 0u;
-      } else if (narrow) {
-        sr = A0[i] & 0xFFFFFFFFull;
-        sg = A0[i] >> 32;
-        sb = A1[i] & 0xFFFFFFFFull;
-        n = A1[i] >> 32;
-        A0[i] = 0ull;
-        A1[i] = 0ull;
-      } else {
-        sr = A0[i];
-        sg = A1[i];
-        sb = A2[i];
-        n = cnt32[i];
-        A0[i] = 0ull;
-        A1[i] = 0ull;
-        A2[i] = 0ull;
-        cnt32[i] = 0u;
-      }
-      if (!room) continue;
-      const uint64_t o = S.base + wbase + __popc(bal & ((1u << lane) - 1u));
-      const uint32_t cell = key_to_cell(key1, I);
-      int4 rec;
-      rec.x = (int)cell;
-      if (PICKLIKE) {
-        const uint32_t best = (uint32_t)(e.y >> 32);
-        if (best >= td.idx_bound || pick_key<MODE>(best, td.level0 + v.level) != e.x) {  // cannot happen for a cell that received a sample
-          atomicOr(&ctr->error, kErrInternal);
-          continue;
+    {
+      unsigned int* const occ_ctr = &v.aux[I.g].occ;
+      const uint64_t base = S.base;
+      // four slots per thread (16-byte key loads), a warp scan of their
+      // occupied counts, one append per warp
+      for (uint32_t q0 = 0; q0 < H; q0 += 4u * blockDim.x) {
+        const uint32_t i = q0 + 4u * threadIdx.x;
+        uint32_t kk[4];
+        if (i + 3u < H) {
+          const uint4 k4 = *reinterpret_cast<const uint4*>(keys + i);
+          kk[0] = k4.x;
+          kk[1] = k4.y;
+          kk[2] = k4.z;
+          kk[3] = k4.w;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) kk[j] = i + j < H ? keys[i + j] : 0u;
         }
-        rec.y = (int)(uint32_t)e.y;
-        rec.z = (int)c32;
-        rec.w = (int)best;
-      } else {
-        rec.y = (int)mean_rgba(sr, sg, sb, n);
-        rec.z = (int)n;
-        rec.w = (int)kNone;
-        ulonglong2 sm;
-        sm.x = sr | (sg << 40);
-        sm.y = (sg >> 24) | (sb << 16);
-        v.stage_out_sum[o] = sm;
+        const uint32_t c = (kk[0] != 0u) + (kk[1] != 0u) + (kk[2] != 0u) + (kk[3] != 0u);
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+          if ((int)lane >= o) incl += t;
+        }
+        const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        if (!total) continue;
+        uint32_t wb = 0;
+        if (lane == 31) wb = atomicAdd(occ_ctr, total);
+        wb = __shfl_sync(0xFFFFFFFFu, wb, 31);
+        const bool room = (uint64_t)wb + total <= bound && base + wb + total <= v.stage_cap;
+        if (lane == 31 && !room) atomicOr(&ctr->error, kErrStageCap);
+        uint32_t pos = wb + incl - c;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t key1 = kk[j];
+          if (!key1) continue;
+          const uint32_t slot = i + j;
+          const uint64_t o = base + pos++;
+          // read the entry and leave it empty for the next pass or item
+          keys[slot] = 0u;
+          ulonglong2 e = make_ulonglong2(0ull, 0ull);
+          uint32_t c32 = 0;
+          uint64_t sr = 0, sg = 0, sb = 0, n = 0;
+          if (PICKLIKE) {
+            e = E[slot];
+            c32 = cnt32[slot];
+            E[slot] = make_ulonglong2(~0ull, 0ull);
+            cnt32[slot] = 0u;
+          } else if (narrow) {
+            sr = A0[slot] & 0xFFFFFFFFull;
+            sg = A0[slot] >> 32;
+            sb = A1[slot] & 0xFFFFFFFFull;
+            n = A1[slot] >> 32;
+            A0[slot] = 0ull;
+            A1[slot] = 0ull;
+          } else {
+            sr = A0[slot];
+            sg = A1[slot];
+            sb = A2[slot];
+            n = cnt32[slot];
+            A0[slot] = 0ull;
+            A1[slot] = 0ull;
+            A2[slot] = 0ull;
+            cnt32[slot] = 0u;
+          }
+          if (!room) continue;
+          const uint32_t cell = key_to_cell(key1, I);
+          int4 rec;
+          rec.x = (int)cell;
+          if (PICKLIKE) {
+            const uint32_t best = (uint32_t)(e.y >> 32);
+            if (best >= td.idx_bound || pick_key<MODE>(best, td.level0 + v.level) != e.x) {
+              atomicOr(&ctr->error, kErrInternal);  // cannot happen for a cell that received a sample
+              continue;
+            }
+            rec.y = (int)(uint32_t)e.y;
+            rec.z = (int)c32;
+            rec.w = (int)best;
+          } else {
+            rec.y = (int)mean_rgba(sr, sg, sb, n);
+            rec.z = (int)n;
+            rec.w = (int)kNone;
+            ulonglong2 sm;
+            sm.x = sr | (sg << 40);
+            sm.y = (sg >> 24) | (sb << 16);
+            v.stage_out_sum[o] = sm;
+          }
+          v.stage_out[o] = rec;
+        }
       }
-      v.stage_out[o] = rec;
     }
     __syncthreads();
     if (threadIdx.x == 0) S.clean = 1;
