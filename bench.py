@@ -511,7 +511,7 @@ def main():
     ap.add_argument("--no-extra-modes", action="store_true", help="skip timing the weighted / first / random modes")
     ap.add_argument("--no-render", action="store_true", help="skip timing the rasteriser")
     ap.add_argument("--tuning", default="", help="lod_set_tuning knobs for this run, e.g. "
-                    "'vox_spill_records=1,dense_bins_max=512' (default: the library's defaults)")
+                    "'vox_queue_ranges=1,dense_bins_max=512' (default: the library's defaults)")
     ap.add_argument("--suite", default="single", choices=["single", "batched", "serve"],
                     help="single: the headline line; batched: many independent tiles per launch "
                          "(lod_build_batched); serve: Poisson request stream through lod_submit/lod_poll")

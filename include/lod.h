@@ -330,27 +330,31 @@ int lod_root_cubes_noalloc(const lod_point_t* const* d_tiles, const uint64_t* n,
  *                   in a dense shared-memory histogram, larger ones through
  *                   per-CTA shared-memory hash tables (8..4096, a power of
  *                   8; default 4096).
- *   vox_spill_records  records of each of the two spill lists a voxel CTA
- *                   keeps in global memory: a sample whose cell finds no
- *                   slot in the CTA's shared-memory table goes there and is
- *                   processed by another pass, instead of the item being
- *                   redone in hash partitions (default 65536; 1 turns the
- *                   lists off).
+ *   vox_queue_ranges  the voxel pass numbers an item's occupied cells in
+ *                   cell order and accumulates them in ranges of what one
+ *                   CTA's shared memory holds (5800 to 11600 cells); an
+ *                   item needing P >= vox_queue_ranges ranges hands ranges
+ *                   2..P to other SMs (default 2; 1: every range stays with
+ *                   the item's CTA; at most 4096).
  *   graph_voxel_levels  1: every build captures the launches of all its
  *                   voxel levels (which need no host round trip between
  *                   them) into one CUDA graph and launches that (0: plain
  *                   launches, the default).  Ignored while profiling.
  *   vox_no_merge    1: in filtered mode the lanes of a warp whose points share
  *                   a cell do not add their colours together before updating
- *                   the table (0: they do, the default). */
+ *                   the table (0: they do, the default).
+ *   vox_range_cells  at most this many cells per accumulate range of the
+ *                   voxel pass (1..262144; default: what shared memory
+ *                   holds); smaller values only add passes. */
 typedef struct lod_tuning {
   uint32_t root_depth;
   uint32_t stream_ctas_per_sm;
   uint32_t dense_bins_max;
-  uint32_t vox_spill_records;
+  uint32_t vox_queue_ranges;
   uint32_t graph_voxel_levels;
   uint32_t vox_no_merge;
-  uint32_t reserved[2];
+  uint32_t vox_range_cells;
+  uint32_t reserved[1];  /* must be 0 */
 } lod_tuning_t;
 
 int lod_set_tuning(const lod_tuning_t* t);
@@ -360,7 +364,7 @@ int lod_get_tuning(lod_tuning_t* t);
  * params; on `stream`) under candidate tunings, two builds each (the first
  * untimed), by coordinate descent from the defaults: stream_ctas_per_sm 1
  * and 3; root_depth one less and one more than the default; dense_bins_max
- * 512; vox_spill_records 1 (off) and 262144; in filtered mode
+ * 512; vox_queue_ranges 1 (never) and 4; in filtered mode
  * vox_no_merge 1 — each knob in turn, the others held at the best so far.  Keeps the fastest with lod_set_tuning and
  * returns it in *best (and its build time in *best_ms when not NULL).
  * Results are freed; nothing else is kept.  Costs about 16 builds; like

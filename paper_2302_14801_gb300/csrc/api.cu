@@ -321,14 +321,14 @@ int lod_autotune(const lod_point_t* d_points, uint64_t n, const lod_params_t* pa
     if (knob == 0) cand = {1u, 3u};         // CTAs per SM of the streaming passes (default 2)
     if (knob == 1) cand = std::vector<uint32_t>(depths.begin() + 1, depths.end());
     if (knob == 2) cand = {512u};           // dense shared histograms up to 512 cells (default 4096)
-    if (knob == 3) cand = {1u, 262144u};    // no spill lists, larger ones (default 65536)
+    if (knob == 3) cand = {1u, 4u};         // an item's rank ranges: never handed to other SMs, from 4 (default 2)
     if (knob == 4 && p.mode == LOD_FILTER) cand = {1u};  // no warp merge of same-cell samples
     for (uint32_t c : cand) {
       lod_tuning_t t = win;
       if (knob == 0) t.stream_ctas_per_sm = c;
       if (knob == 1) t.root_depth = c;
       if (knob == 2) t.dense_bins_max = c;
-      if (knob == 3) t.vox_spill_records = c;
+      if (knob == 3) t.vox_queue_ranges = c;
       if (knob == 4) t.vox_no_merge = c;
       float ms = 0.f;
       if ((rc = time_with(t, &ms)) != LOD_OK) break;

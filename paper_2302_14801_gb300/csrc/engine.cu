@@ -279,7 +279,8 @@ uint32_t ceil_log4(double x) {
 // level), capped at 256^3 cells, the cube's own size and max_depth.
 std::atomic<uint32_t> g_tune_root_depth{0};
 std::atomic<uint32_t> g_tune_ctas_per_sm{0};
-std::atomic<uint32_t> g_tune_spill_cap{0};  // 0: default, 1: no spill lists
+std::atomic<uint32_t> g_tune_queue_ranges{0};  // 0: default (2), 1: an item's ranges stay in its CTA
+std::atomic<uint32_t> g_tune_range_cells{0};   // 0: what the shared memory holds
 std::atomic<uint32_t> g_tune_dense_bins{0};  // 0: kSmemBins
 std::atomic<uint32_t> g_tune_graph{0};       // 1: the voxel levels run as one CUDA graph
 std::atomic<uint32_t> g_tune_no_merge{0};    // 1: no warp merge of same-cell samples in the voxel pass
@@ -520,13 +521,15 @@ int set_tuning(const lod_tuning_t& t) {
   if (t.root_depth > kRootMaxD || t.stream_ctas_per_sm > 8) return LOD_ERR_INVALID_ARG;
   const uint32_t b = t.dense_bins_max;
   if (b && (b != 8 && b != 64 && b != 512 && b != 4096)) return LOD_ERR_INVALID_ARG;
-  if (t.vox_spill_records > (1u << 24) || t.graph_voxel_levels > 1 || t.vox_no_merge > 1) return LOD_ERR_INVALID_ARG;
+  if (t.vox_queue_ranges > 4096 || t.graph_voxel_levels > 1 || t.vox_no_merge > 1) return LOD_ERR_INVALID_ARG;
+  if (t.vox_range_cells > (1u << 18) || t.reserved[0]) return LOD_ERR_INVALID_ARG;
   g_tune_graph.store(t.graph_voxel_levels);
   g_tune_no_merge.store(t.vox_no_merge);
   g_tune_root_depth.store(t.root_depth);
   g_tune_ctas_per_sm.store(t.stream_ctas_per_sm);
   g_tune_dense_bins.store(b);
-  g_tune_spill_cap.store(t.vox_spill_records);
+  g_tune_queue_ranges.store(t.vox_queue_ranges);
+  g_tune_range_cells.store(t.vox_range_cells);
   return LOD_OK;
 }
 
@@ -535,7 +538,8 @@ int get_tuning(lod_tuning_t* t) {
   t->root_depth = g_tune_root_depth.load();
   t->stream_ctas_per_sm = g_tune_ctas_per_sm.load();
   t->dense_bins_max = g_tune_dense_bins.load();
-  t->vox_spill_records = g_tune_spill_cap.load();
+  t->vox_queue_ranges = g_tune_queue_ranges.load();
+  t->vox_range_cells = g_tune_range_cells.load();
   t->graph_voxel_levels = g_tune_graph.load();
   t->vox_no_merge = g_tune_no_merge.load();
   return LOD_OK;
@@ -1182,13 +1186,6 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
     }
   }
   const uint32_t units_cap = (uint32_t)std::min<uint64_t>((uint64_t)max_items * 64, 1u << 20);
-  // spill lists of the first-attempt voxel kernel (one CTA per SM); sample
-  // positions are 32-bit, so a staging array of 2^32 records or more goes
-  // without them
-  const uint32_t spill_cap = g_tune_spill_cap.load() == 1 ? 0u : (g_tune_spill_cap.load() ? g_tune_spill_cap.load() : 65536u);
-  DevBuf d_spill(st, ws);
-  if (!weighted && spill_cap && n_vlev > 0 && stage_cap < (1ull << 32))
-    LOD_CK(d_spill.alloc((size_t)sm_count() * 2 * spill_cap * sizeof(uint2)));
   LOD_CK(d_units.alloc((size_t)units_cap * sizeof(uint4)));
   const size_t lctr_bytes = (size_t)std::max(n_vlev, 1) * sizeof(DevCounters);
   LOD_CK(d_lctr.alloc(lctr_bytes));
@@ -1249,8 +1246,11 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
       vl.vstate = d_vstate.as<unsigned long long>();
       vl.parent_prefix = d_pref.as<uint32_t>() + (size_t)l * pstride + (nt + 1);
       vl.n_parents = n_par;
-      vl.spill = d_spill.as<uint2>();
-      vl.spill_cap = d_spill.p ? spill_cap : 0u;
+      {
+        const uint32_t q = g_tune_queue_ranges.load();
+        vl.queue_ranges = q == 0 ? 2u : (q == 1 ? 0xFFFFFFFFu : q);
+        vl.range_cells = g_tune_range_cells.load();
+      }
       vl.no_merge = g_tune_no_merge.load();
       if (weighted) {
         vl.wgrid = reinterpret_cast<unsigned long long*>(wbase);
@@ -1300,11 +1300,11 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
         prof.recs[vox_rec[l] - 1].bytes = 16.0 * (double)(leaf_cap[kMaxLevels + 1 + l + 1] + V_child + lv);
       if (debug_stats())
         std::fprintf(stderr, "[lod] level %d: items %u (leaf points %llu, child voxels %llu) -> voxels %llu, "
-                     "retried items %llu, table passes %llu, partition units %u\n", l,
+                     "retried items %llu, table passes %llu, partition units %u, samples read %llu\n", l,
                      pref[(size_t)l * pstride + nt], (unsigned long long)leaf_cap[kMaxLevels + 1 + l + 1],
                      (unsigned long long)V_child, (unsigned long long)lv,
                      (unsigned long long)lctr[l].vox_retries, (unsigned long long)lctr[l].vox_passes,
-                     lctr[l].units);
+                     lctr[l].units, (unsigned long long)lctr[l].vox_samples);
       V_child = lv;
     }
     if (prof.on && n_vlev > 0 && !prof.recs.empty()) prof.recs.back().bytes = 32.0 * (double)V_child;

@@ -2,18 +2,32 @@
 //
 // The paper processes one node per workgroup with one 128^3 grid per SM in
 // global memory (8 MB / 33 MB per workgroup, Sections 4.2.2-4.2.3).  Here a
-// CTA handles one (parent, child octant) pair: the child's samples (its
-// leaf points, or the voxels the child itself received one level below)
-// all fall into one 64^3 octant of the parent's 128^3 grid (the observation
-// of Section 4.2), and their cells are accumulated in a 224 KB
-// shared-memory open-addressing hash table instead of a dense grid.  An
-// octant whose occupied cells exceed the table is processed in several
-// hash-partitioned passes.  Colour sums are exact integers (32-bit lanes
-// while they provably cannot overflow, 64-bit otherwise); the single-sample
-// modes (minimal-hash pick, first come of Section 4.2.1, random with the
-// key of Listing 1) keep, per cell, the entry {key, rgba | index << 32} of
-// minimal key, updated by a 128-bit compare-and-swap, so the picked colour
-// travels with the winning key and is never gathered from the input.
+// CTA handles one (parent, child octant) pair, an "item": the child's
+// samples (its leaf points, or the voxels the child itself received one
+// level below) all fall into one 64^3 octant of the parent's 128^3 grid
+// (the observation of Section 4.2).  Sampling an item takes two passes over
+// its samples, both in shared memory:
+//
+//  1. mark: every sample sets its cell's bit in a 32 KB occupancy bitmap of
+//     the octant; a block scan of the bitmap's population counts then
+//     stores, beside every 96 cells of the bitmap, the rank of their first
+//     occupied cell, which numbers the item's D occupied cells 0..D-1 in
+//     cell order;
+//  2. accumulate: every sample finds its cell's rank (one 16-byte read and
+//     three population counts) and updates the dense entry of that rank.
+//
+// No hashing and no probing: every lookup costs the same, D is exact before
+// anything is accumulated (so the item's staging block is reserved to the
+// record), and the voxels come out sorted by cell.  The dense entries of
+// one pass hold 5800 to 11600 cells, depending on the mode; an item with
+// more occupied cells takes its ranks in consecutive ranges, one accumulate
+// pass each, and may hand ranges to other SMs.  Colour sums are exact
+// integers (packed 24- or 32-bit fields while they provably cannot
+// overflow, 64-bit otherwise); the single-sample modes (minimal-hash pick,
+// first come of Section 4.2.1, random with the key of Listing 1) keep, per
+// cell, the entry {key, rgba | index << 32} of minimal key, updated by a
+// 128-bit compare-and-swap, so the picked colour travels with the winning
+// key and is never gathered from the input.
 //
 // Every octant's voxels go to a staging area; a level scan then assigns
 // each parent one contiguous voxel range (children are consecutive in node
@@ -27,26 +41,46 @@ namespace lodk {
 namespace {
 
 constexpr int kSmemBytes = 224 * 1024;
-constexpr uint32_t kHn = kSmemBytes / 20;  // filtered, 32-bit sums: key + 2 x u64
-constexpr uint32_t kHw = kSmemBytes / 32;  // filtered, 64-bit sums: key + 3 x u64 + count
-constexpr uint32_t kHp = kSmemBytes / 24;  // pick: key + {u64 hash, u64 payload} + count
+// occupancy groups: three 32-bit words of the bitmap (96 cells) and the
+// rank of their first occupied cell, {rank, w0, w1, w2}
+constexpr uint32_t kGroups = (kOctCells + 95u) / 96u;  // 2731
+constexpr uint32_t kDenseOff = (kGroups * 16u + 127u) / 128u * 128u;
+constexpr uint32_t kDenseBytes = kSmemBytes - kDenseOff;
+// cells one accumulate pass holds; every layout ends with the u32 cell of each rank
+constexpr uint32_t kCapSmall = kDenseBytes / 16;   // filtered, <= 65535 points: u64 {R:24 G:24 n:16}, u32 B
+constexpr uint32_t kCapNarrow = kDenseBytes / 20;  // filtered, 32-bit sums: u64 {R, G}, u64 {B, n}
+constexpr uint32_t kCapWide = kDenseBytes / 32;    // filtered, 64-bit sums: 3 x u64, u32 n
+constexpr uint32_t kCapPick = kDenseBytes / 24;    // single sample: {u64 key, u64 payload}, u32 n
 constexpr uint64_t kNarrowMaxSamples = 0xFFFFFFFFull / 255;  // 32-bit channel sums cannot overflow
+constexpr uint64_t kSmallMaxSamples = 0xFFFFu;               // 24-bit sums and a 16-bit count cannot
 constexpr uint64_t kMask40 = (1ull << 40) - 1;
+constexpr uint32_t kNoRank = 0xFFFFFFFFu;
 
-constexpr uint32_t kProbe = 48;       // longest probe sequence before the table counts as full
-constexpr uint32_t kProbeSpill = 8;   // ... in passes that spill: cells that find no slot this close to
-                                      // home go to the spill list, so the table stays at a load where
-                                      // every lookup is short
-
-// Cells one table pass can be expected to hold (linear probing stays short
-// up to about three quarters full); sizes the partitioning after an overflow.
-__device__ __forceinline__ uint32_t table_capacity(uint32_t H) { return H / 4 * 3; }
-
-__device__ __forceinline__ uint32_t part_of(uint32_t key1, uint32_t mlog) {
-  return mlog ? (key1 * 0x85EBCA6Bu) >> (32 - mlog) : 0u;
+// Bitmap word of a local cell (x | y << 6 | z << 12): group g, word j of it.
+__device__ __forceinline__ void cell_word(uint32_t cell, uint32_t& g, uint32_t& j) {
+  const uint32_t w = cell >> 5;    // < 8192
+  g = (w * 0xAAABu) >> 17;         // w / 3, exact for w < 2^14
+  j = w - 3u * g;
 }
 
-__device__ __forceinline__ uint32_t home_slot(uint32_t key1, uint32_t H) { return __umulhi(key1 * 0x9E3779B1u, H); }
+// Set a cell's occupancy bit (a read first: most samples find it set).
+__device__ __forceinline__ void mark_cell(uint4* G, uint32_t cell) {
+  uint32_t g, j;
+  cell_word(cell, g, j);
+  uint32_t* w = reinterpret_cast<uint32_t*>(G + g) + 1 + j;
+  const uint32_t bit = 1u << (cell & 31u);
+  if (!(*((volatile uint32_t*)w) & bit)) atomicOr(w, bit);
+}
+
+// Rank of an occupied cell among the item's occupied cells (cell order).
+__device__ __forceinline__ uint32_t cell_rank(const uint4* G, uint32_t cell) {
+  uint32_t g, j;
+  cell_word(cell, g, j);
+  const uint4 e = G[g];
+  const uint32_t below = (1u << (cell & 31u)) - 1u;
+  const uint32_t wj = j == 0 ? e.y : (j == 1 ? e.z : e.w);
+  return e.x + (j >= 1 ? __popc(e.y) : 0u) + (j >= 2 ? __popc(e.z) : 0u) + __popc(wj & below);
+}
 
 // Keep the sample of smaller hash in a pick entry {hash, rgba | index << 32}
 // (hashes of distinct indices differ: splitmix64 is a bijection).  Most
@@ -74,30 +108,6 @@ __device__ __forceinline__ bool pick_update(ulonglong2* e, uint64_t h, uint64_t 
   return true;
 }
 
-// Linear probing from `slot`, whose content was observed as k: the slot of
-// key1 (= local cell + 1), inserting it if absent.  Returns -1 when kProbe
-// consecutive slots hold other cells: the table is too full and the item
-// is redone in more partitions.  No shared fill counter is updated, so
-// inserts of different warps never serialise on one address.
-__device__ __forceinline__ int resolve_slot(uint32_t* keys, uint32_t H, uint32_t key1, uint32_t slot, uint32_t k,
-                                            uint32_t limit = kProbe) {
-  for (uint32_t probe = 0; probe < limit; ++probe) {
-    if (k == key1) return (int)slot;
-    if (k == 0u) {
-      const uint32_t old = atomicCAS(&keys[slot], 0u, key1);
-      if (old == 0u || old == key1) return (int)slot;
-    }
-    slot = (slot + 1 == H) ? 0u : slot + 1;
-    k = ((volatile uint32_t*)keys)[slot];
-  }
-  return -1;
-}
-
-__device__ __forceinline__ int find_or_insert(uint32_t* keys, uint32_t H, uint32_t key1, uint32_t limit = kProbe) {
-  const uint32_t slot = home_slot(key1, H);
-  return resolve_slot(keys, H, key1, slot, ((volatile uint32_t*)keys)[slot], limit);
-}
-
 struct ItemInfo {
   uint32_t tile;
   uint64_t g;        // absolute node id of the item (the child)
@@ -119,43 +129,61 @@ __device__ __forceinline__ uint32_t find_tile(const uint32_t* prefix, uint32_t n
   return lo;
 }
 
-__device__ __forceinline__ uint32_t point_key1(const int4& q, const ItemInfo& I) {
+// Local cell (x | y << 6 | z << 12) of a point in the item's octant.
+__device__ __forceinline__ uint32_t point_cell(const int4& q, const ItemInfo& I) {
   const uint32_t qx = grid_coord((uint32_t)q.x - (uint32_t)I.pmin[0], I.Lp) & 63u;
   const uint32_t qy = grid_coord((uint32_t)q.y - (uint32_t)I.pmin[1], I.Lp) & 63u;
   const uint32_t qz = grid_coord((uint32_t)q.z - (uint32_t)I.pmin[2], I.Lp) & 63u;
-  return (qx | (qy << 6) | (qz << 12)) + 1u;
+  return qx | (qy << 6) | (qz << 12);
 }
 
-__device__ __forceinline__ uint32_t voxel_key1(uint32_t cell) {
-  const uint32_t x = (cell & 127u) >> 1, y = ((cell >> 7) & 127u) >> 1, z = (cell >> 14) >> 1;
-  return (x | (y << 6) | (z << 12)) + 1u;
+// Local cell of a child's voxel (its cell in the child's 128^3 grid).
+__device__ __forceinline__ uint32_t voxel_cell(uint32_t cell) {
+  const uint32_t x = (cell & 127u) >> 1, y = ((cell >> 7) & 127u) >> 1, z = ((cell >> 14) & 127u) >> 1;
+  return x | (y << 6) | (z << 12);
 }
 
-__device__ __forceinline__ uint32_t key_to_cell(uint32_t key1, const ItemInfo& I) {
-  const uint32_t l = key1 - 1u;
-  return ((I.kx << 6) | (l & 63u)) | (((I.ky << 6) | ((l >> 6) & 63u)) << 7) |
-         (((I.kz << 6) | (l >> 12)) << 14);
+// Cell of the parent's 128^3 grid of a local cell.
+__device__ __forceinline__ uint32_t parent_cell(uint32_t l, const ItemInfo& I) {
+  return ((I.kx << 6) | (l & 63u)) | (((I.ky << 6) | ((l >> 6) & 63u)) << 7) | (((I.kz << 6) | (l >> 12)) << 14);
+}
+
+// One 32-byte {point, index} record, kept in L2 (it is read again).
+__device__ __forceinline__ void ld_wide_keep(const int4* p, int4& q, uint32_t& idx) {
+  uint32_t u0, u1, u2;
+  asm("ld.global.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(q.x), "=r"(q.y), "=r"(q.z), "=r"(q.w), "=r"(idx), "=r"(u0), "=r"(u1), "=r"(u2)
+      : "l"(p));
+  (void)u0;
+  (void)u1;
+  (void)u2;
 }
 
 }  // namespace
 
 int vox_smem_bytes() { return kSmemBytes; }
 
+// Cells per accumulate pass of the four entry layouts (statistics and tests).
+void vox_capacities(uint32_t* small, uint32_t* narrow, uint32_t* wide, uint32_t* pick) {
+  *small = kCapSmall;
+  *narrow = kCapNarrow;
+  *wide = kCapWide;
+  *pick = kCapPick;
+}
+
 // Shared state of one voxel CTA.
 struct VoxShared {
-  uint32_t used, out, fail, sp, seen, queued;
-  uint32_t clean;  // the table holds no entry (set by a complete extraction)
-  uint32_t spill_n[2];  // records in the CTA's two spill lists
-  uint32_t spill_in;    // records the current spill pass reads
-  uint32_t spilling;    // the item spilled: its staging block is reserved whole
-  unsigned long long base;  // first staging record of the current pass's output
+  uint32_t D;                  // occupied cells of the item
+  uint32_t r0, r1;             // rank interval this CTA accumulates
+  uint32_t samples;            // samples read by the item's passes (statistics)
+  unsigned long long stage;    // first staging record of the item (rank 0)
+  uint32_t nch;                // inner items: children
+  uint32_t cpre[9];            // inner items: prefix of the children's record counts
+  unsigned long long cstage[8];  // ... their first staging records
+  unsigned long long cdense[8];  // ... their places in the voxel array
+  uint32_t wsum[32];
   ItemInfo I;
-  uint2 stack[48];          // pending {partition, log2 partitions} of the item
 };
-
-constexpr uint32_t kMaxQueuedLog = 6;  // an overflowing item is queued as at most 64 units
-constexpr uint32_t kSpillMark = 0xFFu;  // stack entry {list, kSpillMark}: a pass over a spill list
-constexpr uint32_t kMaxPartLog = 16;   // deeper partitions cannot overflow (a few cells each)
 
 // Reserve `n` consecutive slots of the unit queue; false when it is full
 // (the reservation is all or nothing, so no slot is left unwritten).
@@ -173,17 +201,37 @@ __device__ __forceinline__ bool reserve_units(unsigned int* count, uint32_t cap,
   return false;
 }
 
+// Empty dense entries: all zero bytes in filtered mode (whatever the
+// layout), {~0, 0} and a zero count in the single-sample modes.
+template <int MODE>
+__device__ __forceinline__ void vox_clear_dense(unsigned char* smem) {
+  if (MODE == LOD_FILTER) {
+    uint4* z = reinterpret_cast<uint4*>(smem + kDenseOff);
+    for (uint32_t i = threadIdx.x; i < kDenseBytes / 16u; i += blockDim.x) z[i] = make_uint4(0, 0, 0, 0);
+  } else {
+    ulonglong2* E = reinterpret_cast<ulonglong2*>(smem + kDenseOff);
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(E + kCapPick);
+    for (uint32_t i = threadIdx.x; i < kCapPick; i += blockDim.x) {
+      E[i] = make_ulonglong2(~0ull, 0ull);
+      cnt[i] = 0u;
+    }
+  }
+}
+
+static_assert(3u * kBlock >= kGroups, "the rank scan gives every thread three groups");
+
 // Voxelize one item (a child node c of an inner node p at level v.level):
-// its samples are hashed into the shared table, one pass per partition of
-// its cells.  `first`: the item's first attempt, all cells in one pass; if
-// the table overflows, the item is split into 2^m hash partitions that the
-// partition kernel processes in parallel (or, when the queue is full, this
-// CTA processes them itself).  A partition that still overflows is split in
-// two, depth first, by the CTA that holds it.
+// all of its ranks, or, for a queued unit (r_unit, p_unit), the ranks
+// [D r / P, D (r + 1) / P) of its D occupied cells.  `first`: the item's
+// first attempt, which reserves the item's staging block (D records) and,
+// when its cells need several accumulate passes, may queue the ranges after
+// the first for the partition kernel.  The CTA that holds range 0 also
+// publishes what it reads (the leaf's points, the children's voxels).
 template <int MODE>
 __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, DevCounters* __restrict__ ctr,
-                                         unsigned char* smem, VoxShared& S, uint32_t it, uint32_t p_first,
-                                         uint32_t m_first, bool first) {
+                                         unsigned char* smem, VoxShared& S, uint32_t it, uint32_t r_unit,
+                                         uint32_t p_unit, bool first) {
+  uint4* const G = reinterpret_cast<uint4*>(smem);
   if (threadIdx.x == 0) {
     const uint32_t t = find_tile(v.item_prefix, a.n_tiles, it);
     const uint32_t* ls = v.lvl_start + (uint64_t)t * (kMaxLevels + 1);
@@ -203,560 +251,418 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
     S.I.leaf = (c.flags & LOD_NODE_LEAF) != 0;
     S.I.n = S.I.leaf ? c.point_count : c.voxel_count;
     S.I.npts = c.point_count;
-    S.stack[0] = make_uint2(p_first, m_first);
-    S.sp = 1;
-    S.queued = 0;
-    S.spilling = 0;
-    S.spill_n[0] = S.spill_n[1] = 0;
+    S.samples = 0;
+    S.nch = 0;
+    S.cpre[0] = 0;
+    if (!S.I.leaf) {
+      // the children's staged records, one flat sample sequence
+      const uint32_t nch = __popc(c.child_mask);
+      const uint64_t fc = td.node_base + c.first_child;
+      uint32_t run = 0;
+      for (uint32_t r = 0; r < nch; ++r) {
+        const NodeAux ca = v.aux[fc + r];
+        S.cstage[r] = ca.stage;
+        S.cdense[r] = ca.dense;
+        run += ca.occ;
+        S.cpre[r + 1] = run;
+      }
+      S.nch = nch;
+    }
   }
+  for (uint32_t gi = threadIdx.x; gi < kGroups; gi += blockDim.x) G[gi] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
   const ItemInfo& I = S.I;
   const TileDesc& td = a.tiles[I.tile];
   const lod_node_t& c = v.nodes[I.g];
   constexpr bool PICKLIKE = MODE != LOD_FILTER;  // one sample kept per cell
-  // 32-bit channel sums cannot overflow when the cube holds few enough points
-  const bool narrow = MODE == LOD_FILTER && I.npts <= kNarrowMaxSamples;
-  const uint32_t H = PICKLIKE ? kHp : (narrow ? kHn : kHw);
-  // shared-memory carve-up (u64 arrays first)
-  unsigned long long* A0 = reinterpret_cast<unsigned long long*>(smem);
-  unsigned long long* A1 = A0 + H;
-  unsigned long long* A2 = A1 + H;  // wide only
-  ulonglong2* E = reinterpret_cast<ulonglong2*>(smem);  // pick entries
-  uint32_t* keys;
-  uint32_t* cnt32;
+  // the narrowest sums that provably cannot overflow for the points of this cube
+  const bool small = MODE == LOD_FILTER && I.npts <= kSmallMaxSamples;
+  const bool narrow = MODE == LOD_FILTER && !small && I.npts <= kNarrowMaxSamples;
+  const bool wide = MODE == LOD_FILTER && !small && !narrow;
+  const uint32_t cap = PICKLIKE ? kCapPick : (small ? kCapSmall : (narrow ? kCapNarrow : kCapWide));
+  const uint32_t C = (v.range_cells && v.range_cells < cap) ? v.range_cells : cap;  // ranks per pass
+  // dense entries, one array per field (64-bit arrays first), then the cell of each rank
+  unsigned char* const dn = smem + kDenseOff;
+  unsigned long long* const A0 = reinterpret_cast<unsigned long long*>(dn);
+  ulonglong2* const E = reinterpret_cast<ulonglong2*>(dn);
+  unsigned long long* A1 = nullptr;
+  unsigned long long* A2 = nullptr;
+  uint32_t* B32 = nullptr;
+  uint32_t* cnt = nullptr;
+  uint32_t* K;
   if (PICKLIKE) {
-    keys = reinterpret_cast<uint32_t*>(E + H);
-    cnt32 = keys + H;
+    cnt = reinterpret_cast<uint32_t*>(E + kCapPick);
+    K = cnt + kCapPick;
+  } else if (small) {
+    B32 = reinterpret_cast<uint32_t*>(A0 + kCapSmall);
+    K = B32 + kCapSmall;
   } else if (narrow) {
-    keys = reinterpret_cast<uint32_t*>(A0 + 2 * H);
-    cnt32 = nullptr;
+    A1 = A0 + kCapNarrow;
+    K = reinterpret_cast<uint32_t*>(A1 + kCapNarrow);
   } else {
-    keys = reinterpret_cast<uint32_t*>(A0 + 3 * H);
-    cnt32 = keys + H;
+    A1 = A0 + kCapWide;
+    A2 = A1 + kCapWide;
+    cnt = reinterpret_cast<uint32_t*>(A2 + kCapWide);
+    K = cnt + kCapWide;
   }
 
-  const uint64_t bound = umin64(I.n, kOctCells);  // cells the item can occupy
   const uint64_t pbase = td.pt_base + c.point_offset;
   const int4* pts = a.out + pbase;
   const uint32_t* pidx = PICKLIKE ? a.out_idx + pbase : nullptr;
   // with kept indices the leaf is read from the 32-byte staging records and
   // published to the point / index arrays here, contiguously
   const int4* wsrc = a.wide ? a.wide + 2 * pbase : nullptr;
-  const uint32_t nch = __popc(c.child_mask);
-  const uint64_t fc = td.node_base + (c.first_child == kNone ? 0 : c.first_child);
-  const uint32_t lane = threadIdx.x & 31u;
-  uint32_t passes = 0;
-  bool split = false;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t level = td.level0 + v.level;
+  const bool lead = r_unit == 0;  // the one CTA of the item that publishes
+  uint32_t seen = 0;              // samples this thread read (statistics)
+  uint32_t passes = 1;
 
-  for (;;) {
-    __syncthreads();
-    if (S.sp == 0) break;
-    const uint2 pm = S.stack[S.sp - 1];
-    const uint32_t part = pm.x, mlog = pm.y;
-    // Spill lists: in the item's first pass and in the passes over its
-    // spill lists, a sample whose cell finds no slot is appended (its cell
-    // key and its position) to a list in global memory instead of failing
-    // the pass; the cells in the table are then complete and are extracted,
-    // and the list is processed by another pass over an empty table.  Only
-    // a list that outgrows its space fails the item (which is then redone
-    // in hash partitions).
-    const bool spill_pass = mlog == kSpillMark;
-    const bool can_spill = v.spill != nullptr && first && (spill_pass || mlog == 0);
-    const uint32_t sp_out_id = spill_pass ? 1u - part : 0u;
-    uint2* const sp_out = can_spill ? v.spill + ((uint64_t)blockIdx.x * 2 + sp_out_id) * v.spill_cap : nullptr;
-    const uint2* const sp_in = spill_pass ? v.spill + ((uint64_t)blockIdx.x * 2 + part) * v.spill_cap : nullptr;
-    const uint32_t probe_limit = can_spill ? kProbeSpill : kProbe;
-    if (!S.clean) {
-      // an empty entry is all zero bytes in filtered mode whatever the
-      // table's layout, so a clean table serves every item
-      if (PICKLIKE) {
-        for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) {
-          keys[i] = 0u;
-          E[i] = make_ulonglong2(~0ull, 0ull);
-          cnt32[i] = 0u;
+  // ---- pass 1: mark the occupied cells
+  if (I.leaf) {
+    const uint64_t n = I.n;
+    const bool publish = wsrc != nullptr && lead;  // idempotent: a retried build writes the same values
+    for (uint64_t base = 0; base < n; base += 4ull * blockDim.x) {
+      int4 q[4];
+      uint32_t x[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint64_t i = base + threadIdx.x + (uint64_t)k * blockDim.x;
+        x[k] = 0u;
+        q[k] = make_int4(0, 0, 0, 0);
+        if (i < n) {
+          if (wsrc) ld_wide_keep(wsrc + 2 * i, q[k], x[k]);
+          else q[k] = __ldcg(pts + i);
         }
-      } else {
-        uint4* z = reinterpret_cast<uint4*>(smem);
-        for (uint32_t i = threadIdx.x; i < (uint32_t)kSmemBytes / 16u; i += blockDim.x) z[i] = make_uint4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint64_t i = base + threadIdx.x + (uint64_t)k * blockDim.x;
+        if (i < n) {
+          ++seen;
+          if (publish) {
+            a.out[pbase + i] = q[k];
+            a.out_idx[pbase + i] = x[k];
+          }
+          mark_cell(G, point_cell(q[k], I));
+        }
       }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      S.sp -= 1;
-      S.used = 0;
-      S.fail = 0;
-      S.seen = 0;
-      S.clean = 0;
-      S.spill_in = spill_pass ? S.spill_n[part] : 0u;
-      if (can_spill) S.spill_n[sp_out_id] = 0;
+  } else {
+    const uint32_t total = S.cpre[S.nch];
+    uint32_t ci = 0;  // child of this thread's current sample (samples only move forward)
+    for (uint32_t f0 = 0; f0 < total; f0 += 4u * blockDim.x) {
+      int4 vr[4];
+      uint64_t dst[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t f = f0 + threadIdx.x + (uint32_t)k * blockDim.x;
+        vr[k] = make_int4(0, 0, 0, 0);
+        dst[k] = 0;
+        if (f < total) {
+          while (f >= S.cpre[ci + 1]) ++ci;
+          vr[k] = __ldcg(v.stage_in + S.cstage[ci] + (f - S.cpre[ci]));
+          dst[k] = S.cdense[ci] + (f - S.cpre[ci]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t f = f0 + threadIdx.x + (uint32_t)k * blockDim.x;
+        if (f < total) {
+          ++seen;
+          // publish the child's voxel (idempotent); an array found too
+          // small makes the build rerun with the exact size
+          if (lead && dst[k] < v.dense_cap) v.dense[dst[k]] = vr[k];
+          mark_cell(G, voxel_cell((uint32_t)vr[k].x));
+        }
+      }
     }
-    __syncthreads();
-    ++passes;
-    // append this lane's sample (cell key, position) to the output list when
-    // `want`; warp-aggregated, called by every lane of the warp
-    auto spill_warp = [&](bool want, uint32_t key1, uint32_t src) {
-      const unsigned m = __ballot_sync(0xFFFFFFFFu, want);
-      if (!m) return;
-      const int leader = __ffs(m) - 1;
-      uint32_t base = 0;
-      if ((int)lane == leader) base = atomicAdd(&S.spill_n[sp_out_id], (uint32_t)__popc(m));
-      base = __shfl_sync(0xFFFFFFFFu, base, leader);
-      if (!want) return;
-      const uint32_t pos = base + __popc(m & ((1u << lane) - 1u));
-      if (pos < v.spill_cap) sp_out[pos] = make_uint2(key1, src);
-      else S.fail = 1;
-    };
-    auto spill_one = [&](uint32_t key1, uint32_t src) {
-      const uint32_t pos = atomicAdd(&S.spill_n[sp_out_id], 1u);
-      if (pos < v.spill_cap) sp_out[pos] = make_uint2(key1, src);
-      else S.fail = 1;
-    };
-    uint32_t seen = 0;  // samples this thread went through (for the overflow estimate)
+  }
+  __syncthreads();
 
-    if (spill_pass) {
-      // a spill list: every record names its cell and where its sample is
-      for (uint32_t i = threadIdx.x; i < S.spill_in; i += blockDim.x) {
-        const uint2 sr = sp_in[i];
-        const uint32_t key1 = sr.x, src = sr.y;
-        ++seen;
-        const int slot = find_or_insert(keys, H, key1, probe_limit);
-        if (slot < 0) {
-          spill_one(key1, src);
-          continue;
-        }
-        if (I.leaf) {
-          int4 q;
-          uint32_t ix = 0;
-          if (wsrc) {
-            ld_wide(wsrc + 2 * (uint64_t)src, q, ix);
-          } else {
-            q = pts[src];
-            if (PICKLIKE) ix = pidx[src];
-          }
-          const uint32_t rgba = (uint32_t)q.w;
-          if (PICKLIKE) {
-            if (!pick_update(&E[slot], pick_key<MODE>(ix, td.level0 + v.level), (uint64_t)rgba | ((uint64_t)ix << 32)))
-              atomicOr(&ctr->error, kErrInternal);
-            atomicAdd(&cnt32[slot], 1u);
-          } else if (narrow) {
-            atomicAdd(&A0[slot], (uint64_t)(rgba & 255u) | ((uint64_t)((rgba >> 8) & 255u) << 32));
-            atomicAdd(&A1[slot], (uint64_t)((rgba >> 16) & 255u) | (1ull << 32));
-          } else {
-            atomicAdd(&A0[slot], (uint64_t)(rgba & 255u));
-            atomicAdd(&A1[slot], (uint64_t)((rgba >> 8) & 255u));
-            atomicAdd(&A2[slot], (uint64_t)((rgba >> 16) & 255u));
-            atomicAdd(&cnt32[slot], 1u);
-          }
-        } else {
-          const int4 vr = v.stage_in[src];
-          if (PICKLIKE) {
-            const uint32_t idx = (uint32_t)vr.w;
-            if (!pick_update(&E[slot], pick_key<MODE>(idx, td.level0 + v.level),
-                             (uint64_t)(uint32_t)vr.y | ((uint64_t)idx << 32)))
-              atomicOr(&ctr->error, kErrInternal);
-            atomicAdd(&cnt32[slot], (uint32_t)vr.z);
-          } else {
-            const ulonglong2 sm = v.stage_in_sum[src];
-            const uint64_t sr = sm.x & kMask40, sg = (sm.x >> 40) | ((sm.y & 0xFFFFull) << 24), sb = sm.y >> 16;
-            if (narrow) {
-              atomicAdd(&A0[slot], sr | (sg << 32));
-              atomicAdd(&A1[slot], sb | ((uint64_t)(uint32_t)vr.z << 32));
-            } else {
-              atomicAdd(&A0[slot], sr);
-              atomicAdd(&A1[slot], sg);
-              atomicAdd(&A2[slot], sb);
-              atomicAdd(&cnt32[slot], (uint32_t)vr.z);
-            }
-          }
-        }
+  // ---- rank the occupied cells: exclusive scan of the groups' counts
+  {
+    uint32_t c3[3], sum = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const uint32_t gi = 3u * threadIdx.x + (uint32_t)k;
+      c3[k] = 0;
+      if (gi < kGroups) {
+        const uint4 e = G[gi];
+        c3[k] = __popc(e.y) + __popc(e.z) + __popc(e.w);
       }
-    } else if (I.leaf) {
-      const uint64_t n = I.n;
-      const uint64_t step = 2ull * blockDim.x;
-      // Lanes of a warp whose points share a cell are merged first (point
-      // order follows the scan in real data, so whole warps often hit one
-      // cell); one leader per distinct cell then probes and updates the
-      // table.  All sums stay exact: at most 32 samples are merged.
-      // merge(): lanes of a warp whose points share a cell add up their
-      // colours; returns whether this lane carries the update (a leader, or
-      // any lane with a sample in pick mode).
-      auto merge = [&](uint32_t key1, const int4& q, uint32_t& r, uint32_t& g, uint32_t& b,
-                       uint32_t& n_same, unsigned& peers) -> bool {
-        const unsigned act = __ballot_sync(0xFFFFFFFFu, key1 != 0u);
-        const uint32_t rgba = (uint32_t)q.w;
-        r = rgba & 255u;
-        g = (rgba >> 8) & 255u;
-        b = (rgba >> 16) & 255u;
-        n_same = 1;
-        peers = 1u << lane;
-        if (key1 == 0u) return false;
-        // most pick updates lose the comparison against the entry they
-        // read, so the single-sample modes skip the merge (and so does the
-        // filtered mode when tuned to)
-        if (PICKLIKE || v.no_merge) return true;
-        peers = __match_any_sync(act, key1);
-        n_same = __popc(peers);
-        if (n_same > 1) {
-          r = __reduce_add_sync(peers, r);
-          g = __reduce_add_sync(peers, g);
-          b = __reduce_add_sync(peers, b);
-        }
-        return (int)lane == __ffs(peers) - 1;
-      };
-      auto update = [&](int slot, uint32_t key1, const int4& q, uint32_t ix, uint32_t r, uint32_t g, uint32_t b,
-                        uint32_t n_same) {
-        if (slot < 0) {
-          if (!can_spill) S.fail = 1;  // else every lane of the group spills its own sample
-          return;
-        }
-        if (PICKLIKE) {
-          if (!pick_update(&E[slot], pick_key<MODE>(ix, td.level0 + v.level),
-                           (uint64_t)(uint32_t)q.w | ((uint64_t)ix << 32)))
-            atomicOr(&ctr->error, kErrInternal);
-          atomicAdd(&cnt32[slot], n_same);
-        } else if (narrow) {
-          atomicAdd(&A0[slot], (uint64_t)r | ((uint64_t)g << 32));
-          atomicAdd(&A1[slot], (uint64_t)b | ((uint64_t)n_same << 32));
-        } else {
-          atomicAdd(&A0[slot], (uint64_t)r);
-          atomicAdd(&A1[slot], (uint64_t)g);
-          atomicAdd(&A2[slot], (uint64_t)b);
-          atomicAdd(&cnt32[slot], n_same);
-        }
-      };
-      // both samples of a pair are merged, then both home slots are read
-      // before either probe is resolved, so their shared-memory latencies
-      // overlap
-      auto accumulate2 = [&](uint32_t k0, const int4& q0, uint32_t x0, uint32_t i0, uint32_t k1, const int4& q1,
-                             uint32_t x1, uint32_t i1) {
-        uint32_t r0, g0, b0, n0, r1, g1, b1, n1;
-        unsigned p0, p1;
-        const bool l0 = merge(k0, q0, r0, g0, b0, n0, p0);
-        const bool l1 = merge(k1, q1, r1, g1, b1, n1, p1);
-        uint32_t h0 = 0, h1 = 0, e0 = 0, e1 = 0;
-        if (l0) {
-          h0 = home_slot(k0, H);
-          e0 = ((volatile uint32_t*)keys)[h0];
-        }
-        if (l1) {
-          h1 = home_slot(k1, H);
-          e1 = ((volatile uint32_t*)keys)[h1];
-        }
-        int s0 = 0, s1 = 0;
-        if (l0) update(s0 = resolve_slot(keys, H, k0, h0, e0, probe_limit), k0, q0, x0, r0, g0, b0, n0);
-        if (l1) update(s1 = resolve_slot(keys, H, k1, h1, e1, probe_limit), k1, q1, x1, r1, g1, b1, n1);
-        // a group whose leader found no slot spills all its samples (one
-        // vote when no lane of the warp failed)
-        if (can_spill && __any_sync(0xFFFFFFFFu, (l0 && s0 < 0) || (l1 && s1 < 0))) {
-          const unsigned f0 = __ballot_sync(0xFFFFFFFFu, l0 && s0 < 0);
-          const unsigned f1 = __ballot_sync(0xFFFFFFFFu, l1 && s1 < 0);
-          spill_warp(k0 != 0u && ((f0 >> (__ffs(p0) - 1)) & 1u), k0, i0);
-          spill_warp(k1 != 0u && ((f1 >> (__ffs(p1) - 1)) & 1u), k1, i1);
-        }
-      };
-      // Software pipeline over pairs of points: the loads of the next pair
-      // are in flight while the current pair is hashed and accumulated.
-      auto load = [&](uint64_t i, int4& q, uint32_t& x) {
-        if (wsrc) {
-          ld_wide(wsrc + 2 * i, q, x);
-        } else {
-          q = __ldcs(pts + i);
-          if (PICKLIKE) x = __ldcs(pidx + i);
-        }
-      };
-      const bool publish = wsrc != nullptr && part == 0;
-      int4 q0 = make_int4(0, 0, 0, 0), q1 = q0;
-      uint32_t x0 = 0, x1 = 0;
-      {
-        const uint64_t a0 = threadIdx.x, a1 = a0 + blockDim.x;
-        if (a0 < n) load(a0, q0, x0);
-        if (a1 < n) load(a1, q1, x1);
-      }
-      for (uint64_t base = 0; base < n; base += step) {
-        const uint64_t a0 = base + threadIdx.x, a1 = a0 + blockDim.x;
-        const uint64_t b0 = a0 + step, b1 = a1 + step;
-        int4 r0 = q0, r1 = q1;
-        uint32_t y0 = 0, y1 = 0;
-        if (b0 < n) load(b0, r0, y0);
-        if (b1 < n) load(b1, r1, y1);
-        // the whole warp leaves together: accumulate() uses full-warp
-        // collectives, so no lane may stop while its neighbours go on
-        if (__any_sync(0xFFFFFFFFu, *((volatile uint32_t*)&S.fail) != 0u)) break;
-        if (publish) {  // idempotent: a retried item writes the same values
-          if (a0 < n) {
-            a.out[pbase + a0] = q0;
-            a.out_idx[pbase + a0] = x0;
-          }
-          if (a1 < n) {
-            a.out[pbase + a1] = q1;
-            a.out_idx[pbase + a1] = x1;
-          }
-        }
-        uint32_t k0 = 0u, k1 = 0u;
-        if (a0 < n) {
-          ++seen;
-          k0 = point_key1(q0, I);
-          if (part_of(k0, mlog) != part) k0 = 0u;
-        }
-        if (a1 < n) {
-          ++seen;
-          k1 = point_key1(q1, I);
-          if (part_of(k1, mlog) != part) k1 = 0u;
-        }
-        accumulate2(k0, q0, x0, (uint32_t)a0, k1, q1, x1, (uint32_t)a1);
-        q0 = r0;
-        q1 = r1;
-        x0 = y0;
-        x1 = y1;
-      }
-    } else {
-      // inner child: its voxels are the staged records of its own children
-      for (uint32_t r = 0; r < nch; ++r) {
-        const NodeAux& ca = v.aux[fc + r];
-        const int4* rec = v.stage_in + ca.stage;
-        const ulonglong2* sums = (MODE == LOD_FILTER) ? v.stage_in_sum + ca.stage : nullptr;
-        int4* dst = v.dense + ca.dense;
-        const uint32_t m = ca.occ;
-        const bool fits = ca.dense + m <= v.dense_cap;  // else the build is redone with a larger array
-        for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) {
-          if (*((volatile uint32_t*)&S.fail)) break;
-          const int4 vr = rec[i];
-          ++seen;
-          if (part == 0 && fits) dst[i] = vr;  // publish the child's voxel (idempotent)
-          const uint32_t key1 = voxel_key1((uint32_t)vr.x);
-          if (part_of(key1, mlog) != part) continue;
-          const int slot = find_or_insert(keys, H, key1, probe_limit);
-          if (slot < 0) {
-            if (can_spill) spill_one(key1, (uint32_t)(ca.stage + i));
-            else S.fail = 1;
-            continue;
-          }
-          if (PICKLIKE) {
-            const uint32_t idx = (uint32_t)vr.w;
-            if (!pick_update(&E[slot], pick_key<MODE>(idx, td.level0 + v.level),
-                             (uint64_t)(uint32_t)vr.y | ((uint64_t)idx << 32)))
-              atomicOr(&ctr->error, kErrInternal);
-            atomicAdd(&cnt32[slot], (uint32_t)vr.z);
-          } else {
-            const ulonglong2 sm = sums[i];
-            const uint64_t sr = sm.x & kMask40, sg = (sm.x >> 40) | ((sm.y & 0xFFFFull) << 24), sb = sm.y >> 16;
-            if (narrow) {
-              atomicAdd(&A0[slot], sr | (sg << 32));
-              atomicAdd(&A1[slot], sb | ((uint64_t)(uint32_t)vr.z << 32));
-            } else {
-              atomicAdd(&A0[slot], sr);
-              atomicAdd(&A1[slot], sg);
-              atomicAdd(&A2[slot], sb);
-              atomicAdd(&cnt32[slot], (uint32_t)vr.z);
-            }
-          }
-        }
-      }
+      sum += c3[k];
     }
-    __syncthreads();  // every insert of the pass is done
-    if (S.fail) {
-      // occupied cells of this pass, and how far the pass got
-      {
-        uint32_t mine = 0;
-        for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) mine += keys[i] != 0u ? 1u : 0u;
-        mine = __reduce_add_sync(0xFFFFFFFFu, mine);
-        seen = __reduce_add_sync(0xFFFFFFFFu, seen);
-        if (lane == 0) {
-          if (mine) atomicAdd(&S.used, mine);
-          if (seen) atomicAdd(&S.seen, seen);
-        }
-      }
-      __syncthreads();
-      const uint32_t used = S.used;
-      split = true;
-      if (threadIdx.x == 0) {
-        if (spill_pass || S.spilling) atomicOr(&ctr->error, kErrInternal);  // spill lists only shrink
-        bool handed = false;
-        if (first && mlog == 0) {
-          // the cells of the whole item get one staging block, filled by
-          // the passes over its partitions in any order
-          S.base = atomicAdd(v.stage_used, (unsigned long long)bound);
-          if (S.base + bound > v.stage_cap) atomicOr(&ctr->error, kErrStageCap);
-          v.aux[I.g].stage = S.base;
-          v.aux[I.g].occ = 0u;
-          if (v.units) {
-            // occupied cells projected from the part seen so far
-            const uint64_t sn = S.seen ? S.seen : 1u;
-            const uint64_t est = umin64(bound, (uint64_t)used * I.n / sn + (uint64_t)used / 4 + 1);
-            const uint64_t per = table_capacity(H);
-            uint32_t m = 1;
-            while (m < kMaxQueuedLog && (est >> m) > per) ++m;
-            uint32_t q0 = 0;
-            if (reserve_units(&ctr->units, v.unit_cap, 1u << m, &q0)) {
-              for (uint32_t j = 0; j < (1u << m); ++j) v.units[q0 + j] = make_uint4(it, j, m, 0u);
-              handed = true;
-              S.queued = 1;
-            }
-          }
-        }
-        if (!handed) {
-          if (mlog >= kMaxPartLog) {
-            atomicOr(&ctr->error, kErrInternal);
-          } else {  // split this partition in two, depth first
-            S.stack[S.sp] = make_uint2(2 * part + 1, mlog + 1);
-            S.stack[S.sp + 1] = make_uint2(2 * part, mlog + 1);
-            S.sp += 2;
-          }
-        }
-      }
-      continue;
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if ((int)lane >= o) incl += y;
     }
-
-    // extract this pass's occupied cells into the item's staging block: the
-    // item's first pass reserves its whole block (at most min(samples,
-    // 64^3) cells, what the level's staging is sized for), and every warp
-    // appends its cells through the item's counter
-    if (threadIdx.x == 0) {
-      const bool spilled = can_spill && S.spill_n[sp_out_id] > 0;
-      if (first && mlog == 0) {
-        const unsigned long long blk = atomicAdd(v.stage_used, (unsigned long long)bound);
-        if (blk + bound > v.stage_cap) atomicOr(&ctr->error, kErrStageCap);
-        v.aux[I.g].stage = blk;
-        v.aux[I.g].occ = 0u;
-        if (spilled) S.spilling = 1;
+    if (lane == 31) S.wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t w = S.wsum[lane];
+      uint32_t wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+        if ((int)lane >= o) wi += y;
       }
-      S.base = v.aux[I.g].stage;
-      if (spilled) {  // next: a pass over the samples this one spilled
-        S.stack[S.sp] = make_uint2(sp_out_id, kSpillMark);
-        S.sp += 1;
-      }
+      S.wsum[lane] = wi - w;
+      if (lane == 31) S.D = wi;
     }
     __syncthreads();
-    {
-      unsigned int* const occ_ctr = &v.aux[I.g].occ;
-      const uint64_t base = S.base;
-      // four slots per thread (16-byte key loads), a warp scan of their
-      // occupied counts, one append per warp
-      for (uint32_t q0 = 0; q0 < H; q0 += 4u * blockDim.x) {
-        const uint32_t i = q0 + 4u * threadIdx.x;
-        uint32_t kk[4];
-        if (i + 3u < H) {
-          const uint4 k4 = *reinterpret_cast<const uint4*>(keys + i);
-          kk[0] = k4.x;
-          kk[1] = k4.y;
-          kk[2] = k4.z;
-          kk[3] = k4.w;
-        } else {
+    uint32_t run = S.wsum[warp] + incl - sum;
 #pragma unroll
-          for (int j = 0; j < 4; ++j) kk[j] = i + j < H ? keys[i + j] : 0u;
-        }
-        const uint32_t c = (kk[0] != 0u) + (kk[1] != 0u) + (kk[2] != 0u) + (kk[3] != 0u);
-        uint32_t incl = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-          if ((int)lane >= o) incl += t;
-        }
-        const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        if (!total) continue;
-        uint32_t wb = 0;
-        if (lane == 31) wb = atomicAdd(occ_ctr, total);
-        wb = __shfl_sync(0xFFFFFFFFu, wb, 31);
-        const bool room = (uint64_t)wb + total <= bound && base + wb + total <= v.stage_cap;
-        if (lane == 31 && !room) atomicOr(&ctr->error, kErrStageCap);
-        uint32_t pos = wb + incl - c;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const uint32_t key1 = kk[j];
-          if (!key1) continue;
-          const uint32_t slot = i + j;
-          const uint64_t o = base + pos++;
-          // read the entry and leave it empty for the next pass or item
-          keys[slot] = 0u;
-          ulonglong2 e = make_ulonglong2(0ull, 0ull);
-          uint32_t c32 = 0;
-          uint64_t sr = 0, sg = 0, sb = 0, n = 0;
-          if (PICKLIKE) {
-            e = E[slot];
-            c32 = cnt32[slot];
-            E[slot] = make_ulonglong2(~0ull, 0ull);
-            cnt32[slot] = 0u;
-          } else if (narrow) {
-            sr = A0[slot] & 0xFFFFFFFFull;
-            sg = A0[slot] >> 32;
-            sb = A1[slot] & 0xFFFFFFFFull;
-            n = A1[slot] >> 32;
-            A0[slot] = 0ull;
-            A1[slot] = 0ull;
-          } else {
-            sr = A0[slot];
-            sg = A1[slot];
-            sb = A2[slot];
-            n = cnt32[slot];
-            A0[slot] = 0ull;
-            A1[slot] = 0ull;
-            A2[slot] = 0ull;
-            cnt32[slot] = 0u;
-          }
-          if (!room) continue;
-          const uint32_t cell = key_to_cell(key1, I);
-          int4 rec;
-          rec.x = (int)cell;
-          if (PICKLIKE) {
-            const uint32_t best = (uint32_t)(e.y >> 32);
-            if (best >= td.idx_bound || pick_key<MODE>(best, td.level0 + v.level) != e.x) {
-              atomicOr(&ctr->error, kErrInternal);  // cannot happen for a cell that received a sample
-              continue;
-            }
-            rec.y = (int)(uint32_t)e.y;
-            rec.z = (int)c32;
-            rec.w = (int)best;
-          } else {
-            rec.y = (int)mean_rgba(sr, sg, sb, n);
-            rec.z = (int)n;
-            rec.w = (int)kNone;
-            ulonglong2 sm;
-            sm.x = sr | (sg << 40);
-            sm.y = (sg >> 24) | (sb << 16);
-            v.stage_out_sum[o] = sm;
-          }
-          v.stage_out[o] = rec;
-        }
-      }
+    for (int k = 0; k < 3; ++k) {
+      const uint32_t gi = 3u * threadIdx.x + (uint32_t)k;
+      if (gi < kGroups) G[gi].x = run;
+      run += c3[k];
     }
-    __syncthreads();
-    if (threadIdx.x == 0) S.clean = 1;
   }
   if (threadIdx.x == 0) {
+    const uint32_t D = S.D;
+    if (first) {
+      const unsigned long long blk = atomicAdd(v.stage_used, (unsigned long long)D);
+      if (blk + D > v.stage_cap) atomicOr(&ctr->error, kErrStageCap);
+      v.aux[I.g].stage = blk;
+      v.aux[I.g].occ = D;
+      S.stage = blk;
+      S.r0 = 0;
+      S.r1 = D;
+      const uint32_t P = (D + C - 1) / C;
+      if (P > 1) atomicAdd(&ctr->vox_retries, 1ull);
+      uint32_t q0 = 0;
+      if (P > 1 && v.units && P >= v.queue_ranges && reserve_units(&ctr->units, v.unit_cap, P - 1, &q0)) {
+        for (uint32_t r = 1; r < P; ++r) v.units[q0 + r - 1] = make_uint4(it, r, P, 0u);
+        S.r1 = D / P;
+      }
+    } else {
+      S.stage = v.aux[I.g].stage;  // reserved by the first attempt, or by the up-front split
+      S.r0 = (uint32_t)((uint64_t)D * r_unit / p_unit);
+      S.r1 = (uint32_t)((uint64_t)D * (r_unit + 1) / p_unit);
+      if (r_unit == 0) v.aux[I.g].occ = D;
+    }
+  }
+  __syncthreads();
+  const uint32_t r1 = S.r1;
+  const unsigned long long stage = S.stage;
+  const bool merge = !PICKLIKE && !wide && !v.no_merge;
+
+  // update the dense entry of rank rk (or nothing for kNoRank); called by
+  // every lane of the warp.  Lanes of a warp whose samples share a cell add
+  // their sums first (filtered, 32-bit sums: at most 32 samples of 8-bit
+  // channels or the sums of one cell, which the layout bounds).
+  auto acc = [&](uint32_t rk, uint32_t cell, uint64_t r, uint64_t g, uint64_t b, uint32_t n, uint32_t ix,
+                 uint32_t rgba) {
+    bool doit = rk != kNoRank;
+    if (merge) {
+      const unsigned peers = __match_any_sync(0xFFFFFFFFu, rk);
+      if (doit && __popc(peers) > 1) {
+        r = __reduce_add_sync(peers, (uint32_t)r);
+        g = __reduce_add_sync(peers, (uint32_t)g);
+        b = __reduce_add_sync(peers, (uint32_t)b);
+        n = __reduce_add_sync(peers, n);
+      }
+      doit = doit && (int)lane == __ffs(peers) - 1;
+    }
+    if (!doit) return;
+    K[rk] = cell;
+    if (PICKLIKE) {
+      if (!pick_update(&E[rk], pick_key<MODE>(ix, level), (uint64_t)rgba | ((uint64_t)ix << 32)))
+        atomicOr(&ctr->error, kErrInternal);
+      atomicAdd(&cnt[rk], n);
+    } else if (small) {
+      atomicAdd(&A0[rk], r | (g << 24) | ((uint64_t)n << 48));
+      atomicAdd(&B32[rk], (uint32_t)b);
+    } else if (narrow) {
+      atomicAdd(&A0[rk], r | (g << 32));
+      atomicAdd(&A1[rk], b | ((uint64_t)n << 32));
+    } else {
+      atomicAdd(&A0[rk], r);
+      atomicAdd(&A1[rk], g);
+      atomicAdd(&A2[rk], b);
+      atomicAdd(&cnt[rk], n);
+    }
+  };
+
+  // ---- pass 2: accumulate the ranks [lo, lo + span), one pass per range
+  for (uint32_t lo = S.r0; lo < r1; lo += C) {
+    const uint32_t span = r1 - lo < C ? r1 - lo : C;
+    const bool last = r1 - lo <= C;  // the item's last read: let it leave L2 first
+    ++passes;
+    if (I.leaf) {
+      const uint64_t n = I.n;
+      for (uint64_t base = 0; base < n; base += 4ull * blockDim.x) {
+        int4 q[4];
+        uint32_t x[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint64_t i = base + threadIdx.x + (uint64_t)k * blockDim.x;
+          x[k] = 0u;
+          q[k] = make_int4(0, 0, 0, 0);
+          if (i < n) {
+            if (wsrc) {
+              if (last) ld_wide(wsrc + 2 * i, q[k], x[k]);
+              else ld_wide_keep(wsrc + 2 * i, q[k], x[k]);
+            } else {
+              q[k] = last ? __ldcs(pts + i) : __ldcg(pts + i);
+              if (PICKLIKE) x[k] = last ? __ldcs(pidx + i) : __ldcg(pidx + i);
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint64_t i = base + threadIdx.x + (uint64_t)k * blockDim.x;
+          uint32_t rk = kNoRank, cell = 0;
+          if (i < n) {
+            ++seen;
+            cell = point_cell(q[k], I);
+            const uint32_t rr = cell_rank(G, cell) - lo;
+            if (rr < span) rk = rr;
+          }
+          const uint32_t rgba = (uint32_t)q[k].w;
+          acc(rk, cell, rgba & 255u, (rgba >> 8) & 255u, (rgba >> 16) & 255u, 1u, x[k], rgba);
+        }
+      }
+    } else {
+      const uint32_t total = S.cpre[S.nch];
+      uint32_t ci = 0;
+      for (uint32_t f0 = 0; f0 < total; f0 += 4u * blockDim.x) {
+        int4 vr[4];
+        ulonglong2 sm[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint32_t f = f0 + threadIdx.x + (uint32_t)k * blockDim.x;
+          vr[k] = make_int4(0, 0, 0, 0);
+          sm[k] = make_ulonglong2(0ull, 0ull);
+          if (f < total) {
+            while (f >= S.cpre[ci + 1]) ++ci;
+            const uint64_t src = S.cstage[ci] + (f - S.cpre[ci]);
+            vr[k] = last ? __ldcs(v.stage_in + src) : __ldcg(v.stage_in + src);
+            if (!PICKLIKE) sm[k] = last ? __ldcs(v.stage_in_sum + src) : __ldcg(v.stage_in_sum + src);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint32_t f = f0 + threadIdx.x + (uint32_t)k * blockDim.x;
+          uint32_t rk = kNoRank, cell = 0;
+          if (f < total) {
+            ++seen;
+            cell = voxel_cell((uint32_t)vr[k].x);
+            const uint32_t rr = cell_rank(G, cell) - lo;
+            if (rr < span) rk = rr;
+          }
+          // a child's voxel: {cell, rgba, count, picked index} and packed exact sums
+          const uint64_t sr = sm[k].x & kMask40, sg = (sm[k].x >> 40) | ((sm[k].y & 0xFFFFull) << 24),
+                         sb = sm[k].y >> 16;
+          acc(rk, cell, sr, sg, sb, (uint32_t)vr[k].z, (uint32_t)vr[k].w, (uint32_t)vr[k].y);
+        }
+      }
+    }
+    __syncthreads();  // every update of the pass is done
+
+    // ---- extract: rank lo + i goes to staging record stage + lo + i (cell
+    // order), and the entry is left empty for the next pass or item
+    for (uint32_t i = threadIdx.x; i < span; i += blockDim.x) {
+      const uint32_t cell = K[i];
+      const uint64_t o = stage + lo + i;
+      int4 rec;
+      rec.x = (int)parent_cell(cell, I);
+      ulonglong2 sums = make_ulonglong2(0ull, 0ull);
+      if (PICKLIKE) {
+        const ulonglong2 e = E[i];
+        const uint32_t c32 = cnt[i];
+        E[i] = make_ulonglong2(~0ull, 0ull);
+        cnt[i] = 0u;
+        const uint32_t best = (uint32_t)(e.y >> 32);
+        if (best >= td.idx_bound || pick_key<MODE>(best, level) != e.x) {
+          atomicOr(&ctr->error, kErrInternal);  // cannot happen for a cell that received a sample
+          continue;
+        }
+        rec.y = (int)(uint32_t)e.y;
+        rec.z = (int)c32;
+        rec.w = (int)best;
+      } else {
+        uint64_t sr, sg, sb, n;
+        if (small) {
+          const uint64_t a0 = A0[i];
+          sr = a0 & 0xFFFFFFull;
+          sg = (a0 >> 24) & 0xFFFFFFull;
+          n = a0 >> 48;
+          sb = B32[i];
+          A0[i] = 0ull;
+          B32[i] = 0u;
+        } else if (narrow) {
+          const uint64_t a0 = A0[i], a1 = A1[i];
+          sr = a0 & 0xFFFFFFFFull;
+          sg = a0 >> 32;
+          sb = a1 & 0xFFFFFFFFull;
+          n = a1 >> 32;
+          A0[i] = 0ull;
+          A1[i] = 0ull;
+        } else {
+          sr = A0[i];
+          sg = A1[i];
+          sb = A2[i];
+          n = cnt[i];
+          A0[i] = 0ull;
+          A1[i] = 0ull;
+          A2[i] = 0ull;
+          cnt[i] = 0u;
+        }
+        K[i] = 0u;  // the next item's layout may put an accumulator here
+        rec.y = (int)mean_rgba(sr, sg, sb, n);
+        rec.z = (int)n;
+        rec.w = (int)kNone;
+        sums.x = sr | (sg << 40);
+        sums.y = (sg >> 24) | (sb << 16);
+      }
+      if (o < v.stage_cap) {  // else the reservation reported kErrStageCap
+        v.stage_out[o] = rec;
+        if (!PICKLIKE) v.stage_out_sum[o] = sums;
+      }
+    }
+    __syncthreads();
+  }
+  seen = __reduce_add_sync(0xFFFFFFFFu, seen);
+  if (lane == 0 && seen) atomicAdd(&S.samples, seen);
+  __syncthreads();
+  if (threadIdx.x == 0) {
     atomicAdd(&ctr->vox_passes, (unsigned long long)passes);
-    if (split && first) atomicAdd(&ctr->vox_retries, 1ull);
+    atomicAdd(&ctr->vox_samples, (unsigned long long)S.samples);
   }
   __syncthreads();
 }
 
 // First attempt of every item, taken in order by persistent CTAs (one per
-// SM: the table fills the shared memory).  A table left empty by the last
-// extraction is not cleared again.
+// SM: the bitmap and the dense entries fill the shared memory).
 template <int MODE>
 __global__ void __launch_bounds__(kBlock, 1) k_vox(BuildArgs a, VoxLevel v, DevCounters* __restrict__ ctr) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ VoxShared S;
   __shared__ uint32_t s_item;
-  if (threadIdx.x == 0) S.clean = 0;
+  vox_clear_dense<MODE>(smem);
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(&ctr->item_head, 1u);
     __syncthreads();
     const uint32_t it = s_item;
     __syncthreads();
     if (it >= v.n_items) break;
-    vox_item<MODE>(a, v, ctr, smem, S, it, 0u, 0u, true);
+    vox_item<MODE>(a, v, ctr, smem, S, it, 0u, 1u, true);
   }
 }
 
-// Partitions of the items that overflowed their first attempt, taken from
-// the queue by persistent CTAs (the queue is complete when this starts).
+// Rank ranges of items with many occupied cells, taken from the queue by
+// persistent CTAs (the queue is complete when this starts).
 template <int MODE>
 __global__ void __launch_bounds__(kBlock, 1) k_vox_units(BuildArgs a, VoxLevel v, DevCounters* __restrict__ ctr) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ VoxShared S;
   __shared__ uint32_t s_unit;
   const uint32_t n_units = min(ctr->units, v.unit_cap);
-  if (threadIdx.x == 0) S.clean = 0;
+  vox_clear_dense<MODE>(smem);
   for (;;) {
     if (threadIdx.x == 0) s_unit = atomicAdd(&ctr->unit_head, 1u);
     __syncthreads();
@@ -769,9 +675,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_vox_units(BuildArgs a, VoxLevel v
 }
 
 // Levels with few items (the top of the tree) would leave most SMs idle
-// with one CTA per item: every item is split up front into 2^m hash
-// partitions (its staging block reserved here) and the partition kernel
-// spreads them over the SMs.
+// with one CTA per item: every item is split up front into 2^m rank ranges
+// (its staging block reserved here, for as many cells as it can occupy)
+// and the partition kernel spreads them over the SMs.
 __global__ void k_vox_split(BuildArgs a, VoxLevel v, DevCounters* __restrict__ ctr, uint32_t m) {
   const uint32_t it = blockIdx.x * blockDim.x + threadIdx.x;
   if (it >= v.n_items) return;
@@ -790,7 +696,7 @@ __global__ void k_vox_split(BuildArgs a, VoxLevel v, DevCounters* __restrict__ c
     atomicOr(&ctr->error, kErrInternal);
     return;
   }
-  for (uint32_t j = 0; j < (1u << m); ++j) v.units[q + j] = make_uint4(it, j, m, 0u);
+  for (uint32_t j = 0; j < (1u << m); ++j) v.units[q + j] = make_uint4(it, j, 1u << m, 0u);
 }
 
 template <int MODE>

@@ -45,7 +45,7 @@ struct VoxLevel {
   const ulonglong2* stage_in_sum;
   int4* dense;                 // public voxel array
   unsigned long long* stage_used;
-  uint4* units;                // queue of {item, partition, log2 partitions} for overflowing items
+  uint4* units;                // queue of {item, range r, ranges P} of items with many occupied cells
   uint32_t unit_cap;
   uint64_t dense_cap;          // records the public voxel array holds
   unsigned long long* vstate;  // [0] voxels of the levels done so far, [1] nonzero: dense_cap too small
@@ -57,11 +57,12 @@ struct VoxLevel {
   uint32_t* wcnt;
   uint32_t* wtouch;
   ulonglong2* root_sums;  // filtered: exact sums of the top level's voxels, parallel to dense (or null)
-  // spill lists of the first-attempt kernel: two lists of spill_cap
-  // {cell key, sample position} records per CTA (null: items that overflow
-  // the table are redone in hash partitions right away)
-  uint2* spill;
-  uint32_t spill_cap;
+  // rank ranges: an item whose occupied cells need P >= queue_ranges
+  // accumulate passes hands ranges 1..P-1 to the partition kernel (0xFFFFFFFF:
+  // never); range_cells (nonzero) caps the cells of one pass below what the
+  // shared memory holds
+  uint32_t queue_ranges;
+  uint32_t range_cells;
   uint32_t no_merge;  // 1: filtered samples of a warp that share a cell are not merged before the table
 };
 cudaError_t launch_vox(const BuildArgs& a, const VoxLevel& v, DevCounters* ctr, cudaStream_t st);
@@ -81,6 +82,7 @@ cudaError_t launch_gather_voxels(const lod_node_t* nodes, uint32_t n_nodes, cons
                                  const int4* src, int4* dst, cudaStream_t st);
 
 int vox_smem_bytes();
+void vox_capacities(uint32_t* small, uint32_t* narrow, uint32_t* wide, uint32_t* pick);
 int vox_init();
 
 // ----- out-of-core build (Section 7) -----

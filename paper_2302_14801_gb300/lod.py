@@ -72,9 +72,9 @@ class ServerConfig(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("root_depth", ctypes.c_uint32), ("stream_ctas_per_sm", ctypes.c_uint32),
-                ("dense_bins_max", ctypes.c_uint32), ("vox_spill_records", ctypes.c_uint32),
+                ("dense_bins_max", ctypes.c_uint32), ("vox_queue_ranges", ctypes.c_uint32),
                 ("graph_voxel_levels", ctypes.c_uint32), ("vox_no_merge", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 2)]
+                ("vox_range_cells", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 1)]
 
 
 class Camera(ctypes.Structure):
@@ -208,10 +208,11 @@ def profile_read() -> dict:
 
 
 def set_tuning(root_depth: int = 0, stream_ctas_per_sm: int = 0, dense_bins_max: int = 0,
-               vox_spill_records: int = 0, graph_voxel_levels: int = 0, vox_no_merge: int = 0) -> None:
+               vox_queue_ranges: int = 0, graph_voxel_levels: int = 0, vox_no_merge: int = 0,
+               vox_range_cells: int = 0) -> None:
     """Process-wide speed knobs (never change results); 0 = default."""
-    t = Tuning(int(root_depth), int(stream_ctas_per_sm), int(dense_bins_max), int(vox_spill_records),
-               int(graph_voxel_levels), int(vox_no_merge))
+    t = Tuning(int(root_depth), int(stream_ctas_per_sm), int(dense_bins_max), int(vox_queue_ranges),
+               int(graph_voxel_levels), int(vox_no_merge), int(vox_range_cells))
     _check(lib().lod_set_tuning(ctypes.byref(t)), "lod_set_tuning")
 
 
@@ -219,8 +220,9 @@ def get_tuning() -> dict:
     t = Tuning()
     _check(lib().lod_get_tuning(ctypes.byref(t)), "lod_get_tuning")
     return {"root_depth": t.root_depth, "stream_ctas_per_sm": t.stream_ctas_per_sm,
-            "dense_bins_max": t.dense_bins_max, "vox_spill_records": t.vox_spill_records,
-            "graph_voxel_levels": t.graph_voxel_levels, "vox_no_merge": t.vox_no_merge}
+            "dense_bins_max": t.dense_bins_max, "vox_queue_ranges": t.vox_queue_ranges,
+            "graph_voxel_levels": t.graph_voxel_levels, "vox_no_merge": t.vox_no_merge,
+            "vox_range_cells": t.vox_range_cells}
 
 
 def autotune(points, leaf_threshold=50000, mode=FILTER, max_depth=21, stream=None) -> dict:
@@ -233,8 +235,9 @@ def autotune(points, leaf_threshold=50000, mode=FILTER, max_depth=21, stream=Non
     _check(lib().lod_autotune(ptr if n else None, n, ctypes.byref(p), _stream_handle(stream), ctypes.byref(t),
                               ctypes.byref(ms)), "lod_autotune")
     return {"root_depth": t.root_depth, "stream_ctas_per_sm": t.stream_ctas_per_sm,
-            "dense_bins_max": t.dense_bins_max, "vox_spill_records": t.vox_spill_records,
-            "graph_voxel_levels": t.graph_voxel_levels, "vox_no_merge": t.vox_no_merge, "ms": ms.value}
+            "dense_bins_max": t.dense_bins_max, "vox_queue_ranges": t.vox_queue_ranges,
+            "graph_voxel_levels": t.graph_voxel_levels, "vox_no_merge": t.vox_no_merge,
+            "vox_range_cells": t.vox_range_cells, "ms": ms.value}
 
 
 def launch_count() -> int:

@@ -98,13 +98,15 @@ def test_invalid_arguments_rejected_on_host(lodmod):
 def test_tuning_is_checked_and_restorable(lodmod):
     L = lodmod.lib()
     before = lodmod.get_tuning()
-    for bad in ((9, 0), (0, 9), (0, 0, 100), (0, 0, 0, 1 << 25), (0, 0, 0, 0, 2)):
+    for bad in ((9, 0), (0, 9), (0, 0, 100), (0, 0, 0, 4097), (0, 0, 0, 0, 2), (0, 0, 0, 0, 0, 0, (1 << 18) + 1)):
         assert L.lod_set_tuning(ctypes.byref(lodmod.Tuning(*bad))) == lodmod.LOD_ERR_INVALID_ARG
     assert lodmod.get_tuning() == before  # a rejected setting changes nothing
     try:
-        lodmod.set_tuning(root_depth=5, stream_ctas_per_sm=3, dense_bins_max=512, vox_spill_records=1000)
+        lodmod.set_tuning(root_depth=5, stream_ctas_per_sm=3, dense_bins_max=512, vox_queue_ranges=7,
+                          vox_range_cells=1000)
         assert lodmod.get_tuning() == {"root_depth": 5, "stream_ctas_per_sm": 3, "dense_bins_max": 512,
-                                       "vox_spill_records": 1000, "graph_voxel_levels": 0, "vox_no_merge": 0}
+                                       "vox_queue_ranges": 7, "graph_voxel_levels": 0, "vox_no_merge": 0,
+                                       "vox_range_cells": 1000}
     finally:
         lodmod.set_tuning(**before)
     assert lodmod.get_tuning() == before

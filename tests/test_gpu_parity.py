@@ -147,11 +147,11 @@ def test_tuning_never_changes_results(lod, mode):
     pts = synth.aerial(600_000, seed=12, n_buildings=40)
     want = oracle.build(pts, 5000, mode, 21)
     try:
-        # (spill lists of 2 records overflow at once: items fall back to hash
-        # partitions after a partial spill; 1 turns the lists off)
-        for rd, cps, bins, spill, merge in ((1, 1, 8, 1, 1), (3, 0, 64, 0, 0), (5, 3, 512, 2, 1),
-                                            (8, 2, 4096, 262144, 0)):
-            lod.set_tuning(rd, cps, bins, spill, 0, merge)
+        # (ranges of 300 or 1000 cells make most items take several
+        # accumulate passes, in their own CTA (queue 1) or handed to others)
+        for rd, cps, bins, queue, merge, cells in ((1, 1, 8, 1, 1, 300), (3, 0, 64, 0, 0, 0),
+                                                   (5, 3, 512, 2, 1, 1000), (8, 2, 4096, 4096, 0, 0)):
+            lod.set_tuning(rd, cps, bins, queue, 0, merge, cells)
             compare(gpu_build(lod, pts, 5000, mode), want, inp=pts)
     finally:
         lod.set_tuning(0, 0)
@@ -164,7 +164,7 @@ def test_autotune_picks_a_candidate_and_keeps_results(lod):
     try:
         best = lod.autotune(d, 5000, 0)
         assert best["stream_ctas_per_sm"] in (0, 1, 3) and best["ms"] > 0
-        assert best["vox_spill_records"] in (0, 1, 262144) and best["dense_bins_max"] in (0, 512)
+        assert best["vox_queue_ranges"] in (0, 1, 4) and best["dense_bins_max"] in (0, 512)
         assert lod.get_tuning()["stream_ctas_per_sm"] == best["stream_ctas_per_sm"]
         compare(gpu_build(lod, pts, 5000, 0), oracle.build(pts, 5000, 0, 21), inp=pts)
     finally:
@@ -195,15 +195,31 @@ def test_indoor_dense_clusters_refinement(lod, mode, T):
 @pytest.mark.parametrize("mode", [0, 1, 3, 4])
 def test_volumetric_octants_overflow_tables(lod, mode):
     # 400k points uniform in a cube with T = 150k: every child octant of the
-    # root holds ~50k distinct cells, more than one shared-memory table pass
-    # can take, so items are redone in hash partitions (and the parent of
-    # inner children merges wide sums).
+    # root holds ~50k distinct cells, more than one accumulate pass can hold,
+    # so items take several rank ranges (handed to other SMs at the default
+    # setting).
     rng = np.random.default_rng(31)
     pts = np.empty((400_000, 4), np.int32)
     pts[:, :3] = rng.integers(0, 1 << 16, size=(400_000, 3))
     pts[:, 3] = rng.integers(-(2**31), 2**31, size=400_000)
     parity(lod, pts, 150_000, mode)
     parity(lod, pts, 20_000, mode)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 3, 4])
+def test_rank_ranges_all_modes(lod, mode):
+    # accumulate ranges of 97 or 500 cells: nearly every item is taken in
+    # several ranges, all in its own CTA (queue setting 1) or handed to the
+    # partition kernel (2), and the top levels' up-front split units each
+    # hold several ranges too
+    pts = synth.indoor(300_000, seed=21, n_prims=64)
+    want = oracle.build(pts, 5000, mode, 21)
+    try:
+        for queue, cells in ((1, 97), (2, 500), (3, 97)):
+            lod.set_tuning(vox_queue_ranges=queue, vox_range_cells=cells)
+            compare(gpu_build(lod, pts, 5000, mode), want, inp=pts)
+    finally:
+        lod.set_tuning()
 
 
 def test_keep_index_filtered(lod):
