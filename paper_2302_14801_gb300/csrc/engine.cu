@@ -1128,7 +1128,7 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
   // once more with the exact size (every step of it is idempotent).
   DevBuf d_dense(st);  // result
   DevBuf d_stage0(st, ws), d_stage1(st, ws), d_sum0(st, ws), d_sum1(st, ws), d_pref(st, ws), d_tvox(st, ws);
-  DevBuf d_units(st, ws), d_lctr(st, ws), d_vstate(st, ws);
+  DevBuf d_units(st, ws), d_lctr(st, ws), d_vstate(st, ws), d_order(st, ws);
   const bool filt = prm.mode == LOD_FILTER;
   const int n_vlev = max_levels >= 2 ? (int)max_levels - 1 : 0;  // parent levels max_levels-2 .. 0
   const size_t pstride = 2 * (size_t)(nt + 1);
@@ -1187,6 +1187,7 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
   }
   const uint32_t units_cap = (uint32_t)std::min<uint64_t>((uint64_t)max_items * 64, 1u << 20);
   LOD_CK(d_units.alloc((size_t)units_cap * sizeof(uint4)));
+  if (!weighted) LOD_CK(d_order.alloc((size_t)max_items * 4));
   const size_t lctr_bytes = (size_t)std::max(n_vlev, 1) * sizeof(DevCounters);
   LOD_CK(d_lctr.alloc(lctr_bytes));
   LOD_CK(d_vstate.alloc(2 * sizeof(unsigned long long)));
@@ -1246,6 +1247,10 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
       vl.vstate = d_vstate.as<unsigned long long>();
       vl.parent_prefix = d_pref.as<uint32_t>() + (size_t)l * pstride + (nt + 1);
       vl.n_parents = n_par;
+      // the deepest level takes its items in node order; every level scan
+      // orders the items of the level above, larger ones first
+      vl.order = (l == n_vlev - 1 || weighted) ? nullptr : d_order.as<uint32_t>();
+      vl.next_order = (l == 0 || weighted) ? nullptr : d_order.as<uint32_t>();
       {
         const uint32_t q = g_tune_queue_ranges.load();
         vl.queue_ranges = q == 0 ? 2u : (q == 1 ? 0xFFFFFFFFu : q);

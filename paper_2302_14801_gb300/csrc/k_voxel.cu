@@ -227,10 +227,12 @@ static_assert(3u * kBlock >= kGroups, "the rank scan gives every thread three gr
 // when its cells need several accumulate passes, may queue the ranges after
 // the first for the partition kernel.  The CTA that holds range 0 also
 // publishes what it reads (the leaf's points, the children's voxels).
+// `next_item` (first attempts): where thread 0 leaves the item the CTA
+// takes next, fetched while this one is marked.
 template <int MODE>
 __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, DevCounters* __restrict__ ctr,
                                          unsigned char* smem, VoxShared& S, uint32_t it, uint32_t r_unit,
-                                         uint32_t p_unit, bool first) {
+                                         uint32_t p_unit, bool first, uint32_t* next_item) {
   uint4* const G = reinterpret_cast<uint4*>(smem);
   if (threadIdx.x == 0) {
     const uint32_t t = find_tile(v.item_prefix, a.n_tiles, it);
@@ -317,6 +319,9 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
   const bool lead = r_unit == 0;  // the one CTA of the item that publishes
   uint32_t seen = 0;              // samples this thread read (statistics)
   uint32_t passes = 1;
+  // the next item's counter value; its latency hides behind the mark pass
+  uint32_t next_k = 0;
+  if (next_item && threadIdx.x == 0) next_k = atomicAdd(&ctr->item_head, 1u);
 
   // ---- pass 1: mark the occupied cells
   if (I.leaf) {
@@ -381,6 +386,8 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
   __syncthreads();
 
   // ---- rank the occupied cells: exclusive scan of the groups' counts
+  uint32_t next_it = next_k;
+  if (next_item && threadIdx.x == 0 && v.order && next_k < v.n_items) next_it = v.order[next_k];
   {
     uint32_t c3[3], sum = 0;
 #pragma unroll
@@ -422,6 +429,7 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
     }
   }
   if (threadIdx.x == 0) {
+    if (next_item) *next_item = next_it;  // read after this item's last barrier
     const uint32_t D = S.D;
     if (first) {
       const unsigned long long blk = atomicAdd(v.stage_used, (unsigned long long)D);
@@ -451,21 +459,38 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
   const bool merge = !PICKLIKE && !wide && !v.no_merge;
 
   // update the dense entry of rank rk (or nothing for kNoRank); called by
-  // every lane of the warp.  Lanes of a warp whose samples share a cell add
-  // their sums first (filtered, 32-bit sums: at most 32 samples of 8-bit
-  // channels or the sums of one cell, which the layout bounds).
+  // every lane of the warp.  Runs of consecutive lanes whose samples share a
+  // cell (points in scan order often do) add their sums first, so that one
+  // lane updates the entry (filtered, 32-bit sums: at most 32 samples of
+  // 8-bit channels or the sums of one cell, which the layout bounds); a warp
+  // without such a run pays one shuffle and one vote.
   auto acc = [&](uint32_t rk, uint32_t cell, uint64_t r, uint64_t g, uint64_t b, uint32_t n, uint32_t ix,
                  uint32_t rgba) {
     bool doit = rk != kNoRank;
     if (merge) {
-      const unsigned peers = __match_any_sync(0xFFFFFFFFu, rk);
-      if (doit && __popc(peers) > 1) {
-        r = __reduce_add_sync(peers, (uint32_t)r);
-        g = __reduce_add_sync(peers, (uint32_t)g);
-        b = __reduce_add_sync(peers, (uint32_t)b);
-        n = __reduce_add_sync(peers, n);
+      const uint32_t nxt = __shfl_down_sync(0xFFFFFFFFu, rk, 1);
+      const unsigned dm = __ballot_sync(0xFFFFFFFFu, lane < 31u && doit && nxt == rk);  // bit i: lane i + 1 continues i's run
+      if (dm) {
+        const uint32_t end = (uint32_t)__ffs(~dm & (0xFFFFFFFFu << lane)) - 1u;  // last lane of this lane's run
+        uint32_t vr = (uint32_t)r, vg = (uint32_t)g, vb = (uint32_t)b, vn = n;
+#pragma unroll
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+          const uint32_t tr = __shfl_down_sync(0xFFFFFFFFu, vr, o), tg = __shfl_down_sync(0xFFFFFFFFu, vg, o);
+          const uint32_t tb = __shfl_down_sync(0xFFFFFFFFu, vb, o), tn = __shfl_down_sync(0xFFFFFFFFu, vn, o);
+          if (lane + o <= end) {
+            vr += tr;
+            vg += tg;
+            vb += tb;
+            vn += tn;
+          }
+        }
+        // the run's first lane carries the run's sums
+        doit = doit && (lane == 0 || !((dm >> (lane - 1)) & 1u));
+        r = vr;
+        g = vg;
+        b = vb;
+        n = vn;
       }
-      doit = doit && (int)lane == __ffs(peers) - 1;
     }
     if (!doit) return;
     K[rk] = cell;
@@ -636,21 +661,24 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
   __syncthreads();
 }
 
-// First attempt of every item, taken in order by persistent CTAs (one per
-// SM: the bitmap and the dense entries fill the shared memory).
+// First attempt of every item, taken by persistent CTAs (one per SM: the
+// bitmap and the dense entries fill the shared memory) in the level's item
+// order.  While an item is marked, its CTA already takes the next one.
 template <int MODE>
 __global__ void __launch_bounds__(kBlock, 1) k_vox(BuildArgs a, VoxLevel v, DevCounters* __restrict__ ctr) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ VoxShared S;
   __shared__ uint32_t s_item;
   vox_clear_dense<MODE>(smem);
+  if (threadIdx.x == 0) {
+    const uint32_t k = atomicAdd(&ctr->item_head, 1u);
+    s_item = (v.order && k < v.n_items) ? v.order[k] : k;
+  }
+  __syncthreads();
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(&ctr->item_head, 1u);
-    __syncthreads();
-    const uint32_t it = s_item;
-    __syncthreads();
+    const uint32_t it = s_item;  // every thread reads it before the item's first barrier
     if (it >= v.n_items) break;
-    vox_item<MODE>(a, v, ctr, smem, S, it, 0u, 1u, true);
+    vox_item<MODE>(a, v, ctr, smem, S, it, 0u, 1u, true, &s_item);
   }
 }
 
@@ -670,7 +698,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_vox_units(BuildArgs a, VoxLevel v
     __syncthreads();
     if (u >= n_units) break;
     const uint4 w = v.units[u];
-    vox_item<MODE>(a, v, ctr, smem, S, w.x, w.y, w.z, false);
+    vox_item<MODE>(a, v, ctr, smem, S, w.x, w.y, w.z, false, nullptr);
   }
 }
 
@@ -820,6 +848,35 @@ __global__ void __launch_bounds__(kBlock) k_level_scan(BuildArgs a, VoxLevel v, 
   }
   __syncthreads();  // every thread has read vstate[0]
   if (threadIdx.x == 0) v.vstate[0] = level_base + s_carry;
+  if (!v.next_order) return;
+  // The order in which the next level up takes its items (the nodes of this
+  // level): classes of equal bit length of the sample count, largest first,
+  // so that the big items start early and every SM ends the level on small
+  // ones.  Order within a class is immaterial (results do not depend on it).
+  __shared__ uint32_t cls[33];
+  if (threadIdx.x < 33) cls[threadIdx.x] = 0;
+  __syncthreads();
+  auto samples_class = [&](uint32_t ip) -> uint32_t {
+    const uint32_t t = find_tile(parent_prefix, a.n_tiles, ip);
+    const TileDesc& td = a.tiles[t];
+    const lod_node_t& p = v.nodes[td.node_base + v.lvl_start[(uint64_t)t * (kMaxLevels + 1) + v.level] +
+                                  (ip - parent_prefix[t])];
+    const uint32_t n = (p.flags & LOD_NODE_LEAF) ? p.point_count : p.voxel_count;
+    return 32u - (uint32_t)__clz(n);  // 0 for n = 0
+  };
+  for (uint32_t ip = threadIdx.x; ip < n_parents; ip += blockDim.x) atomicAdd(&cls[samples_class(ip)], 1u);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int c = 32; c >= 0; --c) {
+      const uint32_t k = cls[c];
+      cls[c] = run;
+      run += k;
+    }
+  }
+  __syncthreads();
+  for (uint32_t ip = threadIdx.x; ip < n_parents; ip += blockDim.x)
+    v.next_order[atomicAdd(&cls[samples_class(ip)], 1u)] = ip;
 }
 
 cudaError_t launch_level_scan(const BuildArgs& a, const VoxLevel& v, const uint32_t* parent_prefix,

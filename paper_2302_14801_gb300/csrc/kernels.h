@@ -63,6 +63,8 @@ struct VoxLevel {
   // shared memory holds
   uint32_t queue_ranges;
   uint32_t range_cells;
+  const uint32_t* order;  // the order in which the first-attempt kernel takes the items (null: node order)
+  uint32_t* next_order;   // written by the level scan: the order of the next level's items (or null)
   uint32_t no_merge;  // 1: filtered samples of a warp that share a cell are not merged before the table
 };
 cudaError_t launch_vox(const BuildArgs& a, const VoxLevel& v, DevCounters* ctr, cudaStream_t st);
