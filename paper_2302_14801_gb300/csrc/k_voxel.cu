@@ -228,11 +228,13 @@ static_assert(3u * kBlock >= kGroups, "the rank scan gives every thread three gr
 // the first for the partition kernel.  The CTA that holds range 0 also
 // publishes what it reads (the leaf's points, the children's voxels).
 // `next_item` (first attempts): where thread 0 leaves the item the CTA
-// takes next, fetched while this one is marked.
+// takes next, fetched while this one is marked.  `split_unit`: a range of an
+// item split up front, whose leaf may not be published yet (the units of one
+// item run side by side).
 template <int MODE>
 __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, DevCounters* __restrict__ ctr,
                                          unsigned char* smem, VoxShared& S, uint32_t it, uint32_t r_unit,
-                                         uint32_t p_unit, bool first, uint32_t* next_item) {
+                                         uint32_t p_unit, bool first, uint32_t* next_item, bool split_unit = false) {
   uint4* const G = reinterpret_cast<uint4*>(smem);
   if (threadIdx.x == 0) {
     const uint32_t t = find_tile(v.item_prefix, a.n_tiles, it);
@@ -513,6 +515,10 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
   };
 
   // ---- pass 2: accumulate the ranks [lo, lo + span), one pass per range
+  // a leaf read from 32-byte staging records is published (points and
+  // indices, 20 bytes) by the mark pass of its first attempt: later passes
+  // read the published copy
+  const bool from_wide = wsrc != nullptr && split_unit;
   for (uint32_t lo = S.r0; lo < r1; lo += C) {
     const uint32_t span = r1 - lo < C ? r1 - lo : C;
     const bool last = r1 - lo <= C;  // the item's last read: let it leave L2 first
@@ -528,7 +534,7 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
           x[k] = 0u;
           q[k] = make_int4(0, 0, 0, 0);
           if (i < n) {
-            if (wsrc) {
+            if (from_wide) {
               if (last) ld_wide(wsrc + 2 * i, q[k], x[k]);
               else ld_wide_keep(wsrc + 2 * i, q[k], x[k]);
             } else {
@@ -698,7 +704,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_vox_units(BuildArgs a, VoxLevel v
     __syncthreads();
     if (u >= n_units) break;
     const uint4 w = v.units[u];
-    vox_item<MODE>(a, v, ctr, smem, S, w.x, w.y, w.z, false, nullptr);
+    vox_item<MODE>(a, v, ctr, smem, S, w.x, w.y, w.z, false, nullptr, w.w != 0u);
   }
 }
 
@@ -724,7 +730,7 @@ __global__ void k_vox_split(BuildArgs a, VoxLevel v, DevCounters* __restrict__ c
     atomicOr(&ctr->error, kErrInternal);
     return;
   }
-  for (uint32_t j = 0; j < (1u << m); ++j) v.units[q + j] = make_uint4(it, j, 1u << m, 0u);
+  for (uint32_t j = 0; j < (1u << m); ++j) v.units[q + j] = make_uint4(it, j, 1u << m, 1u);
 }
 
 template <int MODE>
