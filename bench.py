@@ -152,8 +152,8 @@ def oracle_sample(cloud, min_points: int = 3_000_000) -> np.ndarray:
     """The bounded sample of a workload that the CPU oracle is timed on
     (the cpu_baseline leg and the reference arm use this one definition):
     the points inside the square x-y window at the cloud's lower x-y corner
-    whose area is the smallest of 1/4096, 1/1024, ... of the cloud's x-y
-    extent that holds at least ``min_points`` points (the same density and
+    whose area is the smallest of 1/4096, 1/2048, 1/1024, ... of the cloud's
+    x-y extent that holds at least ``min_points`` points (the same density and
     structure as the full cloud, at a size the oracle builds in seconds).
     ``cloud`` is an (N, 4) int32 numpy array or CUDA tensor."""
     is_np = isinstance(cloud, np.ndarray)
@@ -178,7 +178,7 @@ def oracle_sample(cloud, min_points: int = 3_000_000) -> np.ndarray:
             cnt = int(sel.sum().item())
         if cnt >= min_points or frac >= 1.0:
             break
-        frac = min(1.0, frac * 4)
+        frac = min(1.0, frac * 2)
     out = np.ascontiguousarray(cloud[sel]) if is_np else cloud[sel].cpu().numpy()
     return out, frac
 
@@ -502,7 +502,7 @@ def run_serve(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="indoor1b", choices=sorted(WORKLOADS))

@@ -332,7 +332,7 @@ int lod_root_cubes_noalloc(const lod_point_t* const* d_tiles, const uint64_t* n,
  *                   8; default 4096).
  *   vox_queue_ranges  the voxel pass numbers an item's occupied cells in
  *                   cell order and accumulates them in ranges of what one
- *                   CTA's shared memory holds (5800 to 11600 cells); an
+ *                   CTA's shared memory holds (5120 to 10240 cells); an
  *                   item needing P >= vox_queue_ranges ranges hands ranges
  *                   2..P to other SMs (default 2; 1: every range stays with
  *                   the item's CTA; at most 4096).

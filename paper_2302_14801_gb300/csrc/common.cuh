@@ -118,6 +118,7 @@ struct DevCounters {
   unsigned long long vox_retries;     // voxel items that needed more table passes
   unsigned long long vox_passes;      // table passes over all voxel items
   unsigned long long vox_samples;     // samples read by all table passes (re-reads included)
+  unsigned long long vox_max_item;    // samples of the level's largest item (statistics)
   unsigned int error;                 // nonzero: a kernel detected a problem
   unsigned int units;                 // voxel partition units queued this level
   unsigned int unit_head;             // units taken by the partition kernel

@@ -889,7 +889,9 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
   // [0, L): per level sum over all nodes of min(points, 64^3); [L, 2L): exact leaf points
   std::vector<unsigned long long> leaf_cap(2 * (kMaxLevels + 1));
   uint64_t total_cap = 0;
-  auto enqueue_nodes = [&]() -> int {
+  // refined: the first round's count of refinement grids (the pass stands
+  // down when it is nonzero), or null after the last round
+  auto enqueue_nodes = [&](const unsigned long long* refined) -> int {
     total_cap = 0;
     for (uint32_t t = 0; t < nt; ++t) {
       td[t].node_base = total_cap;
@@ -907,7 +909,8 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
     LOD_CK(cudaMemsetAsync(d_nctr.p, 0, sizeof(DevCounters), st));
     LOD_LAUNCH("nodes", 0,
                launch_nodes(A, d_nodes.as<lod_node_t>(), d_aux.as<NodeAux>(), d_lvl.as<uint32_t>(),
-                            d_nn.as<uint32_t>(), d_leafcap.as<unsigned long long>(), d_nctr.as<DevCounters>(), st));
+                            d_nn.as<uint32_t>(), d_leafcap.as<unsigned long long>(), d_nctr.as<DevCounters>(),
+                            refined, st));
     LOD_CK(cudaMemcpyAsync(n_nodes.data(), d_nn.p, nt * 4, cudaMemcpyDeviceToHost, st));
     LOD_CK(cudaMemcpyAsync(lvl.data(), d_lvl.p, lvl.size() * 4, cudaMemcpyDeviceToHost, st));
     LOD_CK(cudaMemcpyAsync(leaf_cap.data(), d_leafcap.p, leaf_cap.size() * 8, cudaMemcpyDeviceToHost, st));
@@ -1023,7 +1026,7 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
     LOD_LAUNCH("scatter", 32.0 * round_points,
                launch_scatter(A, d_chunk_src.as<uint32_t>(), d_nchunks.as<unsigned long long>(), round, cgrid, st));
     if (round == 0) {
-      const int rc = enqueue_nodes();
+      const int rc = enqueue_nodes(&d_ctr.as<DevCounters>()->new_srcs);
       if (rc != LOD_OK) return rc;
       nodes_enqueued = true;
     }
@@ -1087,7 +1090,7 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
   // build it now), growing the capacity of tiles that overflowed
   for (int attempt = 0;; ++attempt) {
     if (!nodes_enqueued) {
-      const int rc = enqueue_nodes();
+      const int rc = enqueue_nodes(nullptr);
       if (rc != LOD_OK) return rc;
       LOD_CK(cudaStreamSynchronize(st));
       clk.tick("nodes");
@@ -1305,11 +1308,12 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
         prof.recs[vox_rec[l] - 1].bytes = 16.0 * (double)(leaf_cap[kMaxLevels + 1 + l + 1] + V_child + lv);
       if (debug_stats())
         std::fprintf(stderr, "[lod] level %d: items %u (leaf points %llu, child voxels %llu) -> voxels %llu, "
-                     "retried items %llu, table passes %llu, partition units %u, samples read %llu\n", l,
+                     "retried items %llu, table passes %llu, partition units %u, samples read %llu, largest item %llu\n", l,
                      pref[(size_t)l * pstride + nt], (unsigned long long)leaf_cap[kMaxLevels + 1 + l + 1],
                      (unsigned long long)V_child, (unsigned long long)lv,
                      (unsigned long long)lctr[l].vox_retries, (unsigned long long)lctr[l].vox_passes,
-                     lctr[l].units, (unsigned long long)lctr[l].vox_samples);
+                     lctr[l].units, (unsigned long long)lctr[l].vox_samples,
+                     (unsigned long long)lctr[l].vox_max_item);
       V_child = lv;
     }
     if (prof.on && n_vlev > 0 && !prof.recs.empty()) prof.recs.back().bytes = 32.0 * (double)V_child;

@@ -775,14 +775,23 @@ cudaError_t launch_scatter(const BuildArgs& a, const uint32_t* chunk_src, const 
 // holds more than T points, is above max_depth and larger than a unit cube.
 // Children are the non-empty octants in octant order, their counts read
 // from the pyramid of the grid that covers them (switching to the
-// refinement grid of a cell at the bottom of a grid).
+// refinement grid of a cell at the bottom of a grid).  `refined` (the
+// first round's count of refinement grids, or null): when the pass runs
+// right after the first round and that round created refinement grids, the
+// table would have to follow later rounds anyway, so the pass stands down
+// at once (the host builds the table after the last round).
 
 __global__ void __launch_bounds__(kBlock) k_nodes(BuildArgs a, lod_node_t* __restrict__ nodes,
                                                   NodeAux* __restrict__ aux, uint32_t* __restrict__ lvl_start,
                                                   uint32_t* __restrict__ n_nodes,
                                                   unsigned long long* __restrict__ leaf_cap,
-                                                  DevCounters* __restrict__ ctr) {
+                                                  DevCounters* __restrict__ ctr,
+                                                  const unsigned long long* __restrict__ refined) {
   if (a.abort && *a.abort) return;
+  if (refined && *refined) {
+    if (threadIdx.x == 0) n_nodes[blockIdx.x] = kNone;
+    return;
+  }
   __shared__ uint32_t warp_sum[32];
   __shared__ uint32_t s_total;
   __shared__ int s_fail;
@@ -949,8 +958,9 @@ __global__ void __launch_bounds__(kBlock) k_nodes(BuildArgs a, lod_node_t* __res
 }
 
 cudaError_t launch_nodes(const BuildArgs& a, lod_node_t* nodes, NodeAux* aux, uint32_t* lvl_start,
-                         uint32_t* n_nodes, unsigned long long* leaf_cap, DevCounters* ctr, cudaStream_t st) {
-  k_nodes<<<a.n_tiles, kBlock, 0, st>>>(a, nodes, aux, lvl_start, n_nodes, leaf_cap, ctr);
+                         uint32_t* n_nodes, unsigned long long* leaf_cap, DevCounters* ctr,
+                         const unsigned long long* refined, cudaStream_t st) {
+  k_nodes<<<a.n_tiles, kBlock, 0, st>>>(a, nodes, aux, lvl_start, n_nodes, leaf_cap, ctr, refined);
   note_launch();
   return cudaGetLastError();
 }

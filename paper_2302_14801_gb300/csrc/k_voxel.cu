@@ -9,17 +9,17 @@
 // its samples, both in shared memory:
 //
 //  1. mark: every sample sets its cell's bit in a 32 KB occupancy bitmap of
-//     the octant; a block scan of the bitmap's population counts then
-//     stores, beside every 96 cells of the bitmap, the rank of their first
-//     occupied cell, which numbers the item's D occupied cells 0..D-1 in
-//     cell order;
-//  2. accumulate: every sample finds its cell's rank (one 16-byte read and
-//     three population counts) and updates the dense entry of that rank.
+//     the octant (the item's samples were asked into L2 when it started); a
+//     block scan of the bitmap's population counts then stores, beside
+//     every 32-cell word of the bitmap, the rank of its first occupied
+//     cell, which numbers the item's D occupied cells 0..D-1 in cell order;
+//  2. accumulate: every sample finds its cell's rank (one 8-byte read and
+//     one population count) and updates the dense entry of that rank.
 //
 // No hashing and no probing: every lookup costs the same, D is exact before
 // anything is accumulated (so the item's staging block is reserved to the
 // record), and the voxels come out sorted by cell.  The dense entries of
-// one pass hold 5800 to 11600 cells, depending on the mode; an item with
+// one pass hold 5120 to 10240 cells, depending on the mode; an item with
 // more occupied cells takes its ranks in consecutive ranges, one accumulate
 // pass each, and may hand ranges to other SMs.  Colour sums are exact
 // integers (packed 24- or 32-bit fields while they provably cannot
@@ -41,10 +41,11 @@ namespace lodk {
 namespace {
 
 constexpr int kSmemBytes = 224 * 1024;
-// occupancy groups: three 32-bit words of the bitmap (96 cells) and the
-// rank of their first occupied cell, {rank, w0, w1, w2}
-constexpr uint32_t kGroups = (kOctCells + 95u) / 96u;  // 2731
-constexpr uint32_t kDenseOff = (kGroups * 16u + 127u) / 128u * 128u;
+// occupancy words: 32 cells of the bitmap and the rank of their first
+// occupied cell, {word, rank} (8 bytes, one read and one population count
+// per lookup)
+constexpr uint32_t kWords = kOctCells / 32u;  // 8192
+constexpr uint32_t kDenseOff = kWords * 8u;
 constexpr uint32_t kDenseBytes = kSmemBytes - kDenseOff;
 // cells one accumulate pass holds; every layout ends with the u32 cell of each rank
 constexpr uint32_t kCapSmall = kDenseBytes / 16;   // filtered, <= 65535 points: u64 {R:24 G:24 n:16}, u32 B
@@ -55,40 +56,79 @@ constexpr uint64_t kNarrowMaxSamples = 0xFFFFFFFFull / 255;  // 32-bit channel s
 constexpr uint64_t kSmallMaxSamples = 0xFFFFu;               // 24-bit sums and a 16-bit count cannot
 constexpr uint64_t kMask40 = (1ull << 40) - 1;
 constexpr uint32_t kNoRank = 0xFFFFFFFFu;
+// an item's samples prefetched into L2 when it starts: at most this many
+// bytes (152 SMs x 256 KB stays well inside the 126 MB L2)
+constexpr uint64_t kPrefetchBytes = 256u * 1024u;
 
-// Bitmap word of a local cell (x | y << 6 | z << 12): group g, word j of it.
-__device__ __forceinline__ void cell_word(uint32_t cell, uint32_t& g, uint32_t& j) {
-  const uint32_t w = cell >> 5;    // < 8192
-  g = (w * 0xAAABu) >> 17;         // w / 3, exact for w < 2^14
-  j = w - 3u * g;
+// Ask the bulk-copy unit to bring [p, p + bytes) into L2 (p 16-byte
+// aligned, bytes a multiple of 16; nothing waits on it).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// Set a cell's occupancy bit (a read first: most samples find it set).
-__device__ __forceinline__ void mark_cell(uint4* G, uint32_t cell) {
-  uint32_t g, j;
-  cell_word(cell, g, j);
-  uint32_t* w = reinterpret_cast<uint32_t*>(G + g) + 1 + j;
-  const uint32_t bit = 1u << (cell & 31u);
-  if (!(*((volatile uint32_t*)w) & bit)) atomicOr(w, bit);
+// Set the occupancy bits of a thread's four samples (cells with ok[k]).
+// The four bitmap words are read first, back to back, so the thread waits
+// for shared memory once; only bits found clear are then set (most samples
+// find theirs set already).  A read that misses a concurrent update only
+// costs a redundant atomic.
+__device__ __forceinline__ void mark_cells4(uint2* W, const uint32_t (&cell)[4], const bool (&ok)[4]) {
+  uint32_t* w[4];
+  uint32_t bit[4], cur[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    w[k] = &W[cell[k] >> 5].x;  // local cell x | y << 6 | z << 12: word cell / 32
+    bit[k] = 1u << (cell[k] & 31u);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) cur[k] = ok[k] ? *((volatile uint32_t*)w[k]) : ~0u;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (!(cur[k] & bit[k])) atomicOr(w[k], bit[k]);
 }
 
-// Rank of an occupied cell among the item's occupied cells (cell order).
-__device__ __forceinline__ uint32_t cell_rank(const uint4* G, uint32_t cell) {
-  uint32_t g, j;
-  cell_word(cell, g, j);
-  const uint4 e = G[g];
-  const uint32_t below = (1u << (cell & 31u)) - 1u;
-  const uint32_t wj = j == 0 ? e.y : (j == 1 ? e.z : e.w);
-  return e.x + (j >= 1 ? __popc(e.y) : 0u) + (j >= 2 ? __popc(e.z) : 0u) + __popc(wj & below);
+// Ranks, among the item's occupied cells (cell order), of a thread's four
+// samples' cells, minus lo; kNoRank for samples without ok[k] or outside
+// [lo, lo + span).  The bitmap is read-only during an accumulate pass, so
+// the four 8-byte word reads are issued together.
+__device__ __forceinline__ void cell_ranks4(const uint2* W, const uint32_t (&cell)[4], const bool (&ok)[4],
+                                            uint32_t lo, uint32_t span, uint32_t (&rk)[4]) {
+  uint2 e[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) e[k] = ok[k] ? W[cell[k] >> 5] : make_uint2(0u, 0u);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t below = (1u << (cell[k] & 31u)) - 1u;
+    const uint32_t r = e[k].y + __popc(e[k].x & below) - lo;
+    rk[k] = (ok[k] && r < span) ? r : kNoRank;
+  }
 }
 
-// Keep the sample of smaller hash in a pick entry {hash, rgba | index << 32}
-// (hashes of distinct indices differ: splitmix64 is a bijection).  Most
-// samples lose against the value read first and never write; an improvement
-// is installed with a 128-bit compare-and-swap, retried while others lower
-// the entry meanwhile (each retry sees a strictly smaller hash, so the loop
-// ends; the bound only guards against a broken invariant).
-__device__ __forceinline__ bool pick_update(ulonglong2* e, uint64_t h, uint64_t pay) {
+// Single-sample modes: the keys of the pick entries of a thread's four
+// ranks, read together before any of them is updated (kNoRank: a key no
+// sample beats).
+template <bool PICKLIKE>
+__device__ __forceinline__ void pre_keys4(const ulonglong2* E, const uint32_t (&rk)[4], uint64_t (&pre)[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    pre[k] = 0ull;
+    if (PICKLIKE && rk[k] != kNoRank) {
+      asm volatile("ld.volatile.shared.u64 %0, [%1];"
+                   : "=l"(pre[k])
+                   : "r"((uint32_t)__cvta_generic_to_shared(E + rk[k])));
+    }
+  }
+}
+
+// Keep the sample of smaller key in a pick entry {key, rgba | index << 32}
+// (keys of distinct samples differ).  `seen` is the entry's key as read
+// earlier: keys only decrease while a pass runs, so a sample whose key is
+// not below that read loses for sure and writes nothing.  Otherwise the
+// entry is read again and the improvement installed with a 128-bit
+// compare-and-swap, retried while others lower the entry meanwhile (each
+// retry sees a strictly smaller key, so the loop ends; the bound only
+// guards against a broken invariant).
+__device__ __forceinline__ bool pick_update(ulonglong2* e, uint64_t h, uint64_t pay, uint64_t seen) {
+  if (h >= seen) return true;
   const uint32_t addr = (uint32_t)__cvta_generic_to_shared(e);
   uint64_t c0, c1;
   asm volatile("ld.volatile.shared.v2.u64 {%0, %1}, [%2];" : "=l"(c0), "=l"(c1) : "r"(addr) : "memory");
@@ -178,6 +218,9 @@ struct VoxShared {
   uint32_t samples;            // samples read by the item's passes (statistics)
   unsigned long long stage;    // first staging record of the item (rank 0)
   uint32_t nch;                // inner items: children
+  int32_t cmin[3];             // header: the child's min corner
+  unsigned long long cparent, cfirst;  // header: parent node, first child (absolute)
+  unsigned long long pbase;    // header: the child's first leaf point (absolute)
   uint32_t cpre[9];            // inner items: prefix of the children's record counts
   unsigned long long cstage[8];  // ... their first staging records
   unsigned long long cdense[8];  // ... their places in the voxel array
@@ -218,7 +261,7 @@ __device__ __forceinline__ void vox_clear_dense(unsigned char* smem) {
   }
 }
 
-static_assert(3u * kBlock >= kGroups, "the rank scan gives every thread three groups");
+static_assert(8u * kBlock == kWords, "the rank scan gives every warp 256 words");
 
 // Voxelize one item (a child node c of an inner node p at level v.level):
 // all of its ranks, or, for a queued unit (r_unit, p_unit), the ranks
@@ -235,45 +278,75 @@ template <int MODE>
 __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, DevCounters* __restrict__ ctr,
                                          unsigned char* smem, VoxShared& S, uint32_t it, uint32_t r_unit,
                                          uint32_t p_unit, bool first, uint32_t* next_item, bool split_unit = false) {
-  uint4* const G = reinterpret_cast<uint4*>(smem);
-  if (threadIdx.x == 0) {
-    const uint32_t t = find_tile(v.item_prefix, a.n_tiles, it);
-    const uint32_t* ls = v.lvl_start + (uint64_t)t * (kMaxLevels + 1);
-    const TileDesc& td = a.tiles[t];
-    const uint64_t g = td.node_base + ls[v.level + 1] + (it - v.item_prefix[t]);
-    const lod_node_t c = v.nodes[g];
-    const lod_node_t p = v.nodes[td.node_base + c.parent];
-    S.I.tile = t;
-    S.I.g = g;
-    S.I.Lp = p.log2_size;
-    S.I.pmin[0] = p.min[0];
-    S.I.pmin[1] = p.min[1];
-    S.I.pmin[2] = p.min[2];
-    S.I.kx = c.min[0] != p.min[0];
-    S.I.ky = c.min[1] != p.min[1];
-    S.I.kz = c.min[2] != p.min[2];
-    S.I.leaf = (c.flags & LOD_NODE_LEAF) != 0;
-    S.I.n = S.I.leaf ? c.point_count : c.voxel_count;
-    S.I.npts = c.point_count;
-    S.samples = 0;
-    S.nch = 0;
-    S.cpre[0] = 0;
-    if (!S.I.leaf) {
-      // the children's staged records, one flat sample sequence
-      const uint32_t nch = __popc(c.child_mask);
-      const uint64_t fc = td.node_base + c.first_child;
-      uint32_t run = 0;
-      for (uint32_t r = 0; r < nch; ++r) {
-        const NodeAux ca = v.aux[fc + r];
-        S.cstage[r] = ca.stage;
-        S.cdense[r] = ca.dense;
-        run += ca.occ;
-        S.cpre[r + 1] = run;
+  uint2* const W = reinterpret_cast<uint2*>(smem);    // {word, rank} per 32 cells
+  uint4* const W4 = reinterpret_cast<uint4*>(smem);   // two of them
+  // The item's header, read by warp 0 in two dependent steps: lane 0 reads
+  // the child node; then lane 8 reads the parent node while lanes 0..7 read
+  // the children's records (inner items), all at once.
+  if (threadIdx.x < 32) {
+    const uint32_t ln = threadIdx.x;
+    if (ln == 0) {
+      const uint32_t t = find_tile(v.item_prefix, a.n_tiles, it);
+      const uint32_t* ls = v.lvl_start + (uint64_t)t * (kMaxLevels + 1);
+      const TileDesc& td = a.tiles[t];
+      const uint64_t g = td.node_base + ls[v.level + 1] + (it - v.item_prefix[t]);
+      const lod_node_t c = v.nodes[g];
+      S.I.tile = t;
+      S.I.g = g;
+      S.cmin[0] = c.min[0];
+      S.cmin[1] = c.min[1];
+      S.cmin[2] = c.min[2];
+      S.I.leaf = (c.flags & LOD_NODE_LEAF) != 0;
+      S.I.n = S.I.leaf ? c.point_count : c.voxel_count;
+      S.I.npts = c.point_count;
+      S.cparent = td.node_base + c.parent;
+      S.cfirst = td.node_base + c.first_child;
+      S.pbase = td.pt_base + c.point_offset;
+      S.nch = S.I.leaf ? 0u : (uint32_t)__popc(c.child_mask);
+      S.samples = 0;
+    }
+    __syncwarp();
+    const uint32_t nch = S.nch;
+    if (S.I.leaf) {
+      // the leaf's points (32-byte records where indices are kept), in
+      // 64 KB pieces, one per lane
+      const bool wsrc = a.wide != nullptr;
+      const char* base = wsrc ? (const char*)(a.wide + 2 * S.pbase) : (const char*)(a.out + S.pbase);
+      const uint64_t bytes = umin64(S.I.n * (wsrc ? 32u : 16u), kPrefetchBytes);
+      const uint64_t off = (uint64_t)ln << 16;
+      if (off < bytes) prefetch_l2(base + off, (uint32_t)umin64(bytes - off, 1u << 16));
+    }
+    if (ln == 8) {
+      const lod_node_t p = v.nodes[S.cparent];
+      S.I.Lp = p.log2_size;
+      S.I.pmin[0] = p.min[0];
+      S.I.pmin[1] = p.min[1];
+      S.I.pmin[2] = p.min[2];
+      S.I.kx = S.cmin[0] != p.min[0];
+      S.I.ky = S.cmin[1] != p.min[1];
+      S.I.kz = S.cmin[2] != p.min[2];
+    }
+    // the children's staged records, one flat sample sequence
+    uint32_t occ = 0;
+    if (ln < nch) {
+      const NodeAux ca = v.aux[S.cfirst + ln];
+      S.cstage[ln] = ca.stage;
+      S.cdense[ln] = ca.dense;
+      occ = ca.occ;
+      if (occ) prefetch_l2(v.stage_in + ca.stage, (uint32_t)umin64((uint64_t)occ * 16u, 1u << 16));
+    }
+    if (ln < 8) {
+      uint32_t incl = occ;  // prefix over lanes 0..7
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFu, incl, o);
+        if ((int)ln >= o) incl += y;
       }
-      S.nch = nch;
+      if (ln == 0) S.cpre[0] = 0;
+      S.cpre[ln + 1] = incl;
     }
   }
-  for (uint32_t gi = threadIdx.x; gi < kGroups; gi += blockDim.x) G[gi] = make_uint4(0u, 0u, 0u, 0u);
+  for (uint32_t i = threadIdx.x; i < kWords / 2u; i += blockDim.x) W4[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
   const ItemInfo& I = S.I;
   const TileDesc& td = a.tiles[I.tile];
@@ -342,18 +415,22 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
           else q[k] = __ldcg(pts + i);
         }
       }
+      uint32_t cell[4];
+      bool ok[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const uint64_t i = base + threadIdx.x + (uint64_t)k * blockDim.x;
-        if (i < n) {
+        ok[k] = i < n;
+        cell[k] = point_cell(q[k], I);
+        if (ok[k]) {
           ++seen;
           if (publish) {
             a.out[pbase + i] = q[k];
             a.out_idx[pbase + i] = x[k];
           }
-          mark_cell(G, point_cell(q[k], I));
         }
       }
+      mark_cells4(W, cell, ok);
     }
   } else {
     const uint32_t total = S.cpre[S.nch];
@@ -372,43 +449,49 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
           dst[k] = S.cdense[ci] + (f - S.cpre[ci]);
         }
       }
+      uint32_t cell[4];
+      bool ok[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const uint32_t f = f0 + threadIdx.x + (uint32_t)k * blockDim.x;
-        if (f < total) {
+        ok[k] = f < total;
+        cell[k] = voxel_cell((uint32_t)vr[k].x);
+        if (ok[k]) {
           ++seen;
           // publish the child's voxel (idempotent); an array found too
           // small makes the build rerun with the exact size
           if (lead && dst[k] < v.dense_cap) v.dense[dst[k]] = vr[k];
-          mark_cell(G, voxel_cell((uint32_t)vr[k].x));
         }
       }
+      mark_cells4(W, cell, ok);
     }
   }
   __syncthreads();
 
-  // ---- rank the occupied cells: exclusive scan of the groups' counts
+  // ---- rank the occupied cells: exclusive scan of the words' counts.  Warp
+  // w ranks words [256 w, 256 w + 256), read as pairs {word, rank, word,
+  // rank} by coalesced 16-byte loads: lane l holds pairs l, l + 32, l + 64
+  // and l + 96 of the warp's 128.
   uint32_t next_it = next_k;
   if (next_item && threadIdx.x == 0 && v.order && next_k < v.n_items) next_it = v.order[next_k];
   {
-    uint32_t c3[3], sum = 0;
+    const uint32_t wbase = warp * 128u;
+    uint4 e[4];
+    uint32_t pre[4], tot = 0;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const uint32_t gi = 3u * threadIdx.x + (uint32_t)k;
-      c3[k] = 0;
-      if (gi < kGroups) {
-        const uint4 e = G[gi];
-        c3[k] = __popc(e.y) + __popc(e.z) + __popc(e.w);
+    for (int m = 0; m < 4; ++m) {
+      e[m] = W4[wbase + lane + 32u * (uint32_t)m];
+      const uint32_t c = __popc(e[m].x) + __popc(e[m].z);
+      uint32_t incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if ((int)lane >= o) incl += y;
       }
-      sum += c3[k];
+      pre[m] = tot + incl - c;
+      tot += __shfl_sync(0xFFFFFFFFu, incl, 31);
     }
-    uint32_t incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-      if ((int)lane >= o) incl += y;
-    }
-    if (lane == 31) S.wsum[warp] = incl;
+    if (lane == 0) S.wsum[warp] = tot;
     __syncthreads();
     if (warp == 0) {
       const uint32_t w = S.wsum[lane];
@@ -422,23 +505,24 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
       if (lane == 31) S.D = wi;
     }
     __syncthreads();
-    uint32_t run = S.wsum[warp] + incl - sum;
+    const uint32_t base = S.wsum[warp];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const uint32_t gi = 3u * threadIdx.x + (uint32_t)k;
-      if (gi < kGroups) G[gi].x = run;
-      run += c3[k];
+    for (int m = 0; m < 4; ++m) {
+      e[m].y = base + pre[m];
+      e[m].w = e[m].y + __popc(e[m].x);
+      W4[wbase + lane + 32u * (uint32_t)m] = e[m];
     }
   }
+  // thread 0: the item's first staging record.  The reservation (or, for
+  // a unit, the read of the first attempt's) is issued here and its value
+  // first used before the first extraction, so its latency overlaps the
+  // accumulate pass.
+  unsigned long long stg = 0;
   if (threadIdx.x == 0) {
-    if (next_item) *next_item = next_it;  // read after this item's last barrier
     const uint32_t D = S.D;
     if (first) {
-      const unsigned long long blk = atomicAdd(v.stage_used, (unsigned long long)D);
-      if (blk + D > v.stage_cap) atomicOr(&ctr->error, kErrStageCap);
-      v.aux[I.g].stage = blk;
+      stg = atomicAdd(v.stage_used, (unsigned long long)D);
       v.aux[I.g].occ = D;
-      S.stage = blk;
       S.r0 = 0;
       S.r1 = D;
       const uint32_t P = (D + C - 1) / C;
@@ -449,7 +533,7 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
         S.r1 = D / P;
       }
     } else {
-      S.stage = v.aux[I.g].stage;  // reserved by the first attempt, or by the up-front split
+      stg = v.aux[I.g].stage;  // reserved by the first attempt, or by the up-front split
       S.r0 = (uint32_t)((uint64_t)D * r_unit / p_unit);
       S.r1 = (uint32_t)((uint64_t)D * (r_unit + 1) / p_unit);
       if (r_unit == 0) v.aux[I.g].occ = D;
@@ -457,47 +541,59 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
   }
   __syncthreads();
   const uint32_t r1 = S.r1;
-  const unsigned long long stage = S.stage;
   const bool merge = !PICKLIKE && !wide && !v.no_merge;
 
-  // update the dense entry of rank rk (or nothing for kNoRank); called by
-  // every lane of the warp.  Runs of consecutive lanes whose samples share a
-  // cell (points in scan order often do) add their sums first, so that one
-  // lane updates the entry (filtered, 32-bit sums: at most 32 samples of
-  // 8-bit channels or the sums of one cell, which the layout bounds); a warp
-  // without such a run pays one shuffle and one vote.
-  auto acc = [&](uint32_t rk, uint32_t cell, uint64_t r, uint64_t g, uint64_t b, uint32_t n, uint32_t ix,
-                 uint32_t rgba) {
-    bool doit = rk != kNoRank;
-    if (merge) {
-      const uint32_t nxt = __shfl_down_sync(0xFFFFFFFFu, rk, 1);
-      const unsigned dm = __ballot_sync(0xFFFFFFFFu, lane < 31u && doit && nxt == rk);  // bit i: lane i + 1 continues i's run
-      if (dm) {
-        const uint32_t end = (uint32_t)__ffs(~dm & (0xFFFFFFFFu << lane)) - 1u;  // last lane of this lane's run
-        uint32_t vr = (uint32_t)r, vg = (uint32_t)g, vb = (uint32_t)b, vn = n;
+  // Filtered, 32-bit sums (merge): runs of consecutive lanes whose k-th
+  // samples share a rank (points in scan order often do) add their sums
+  // first, so that only the run's first lane updates the entry (at most 32
+  // samples of 8-bit channels or the sums of one cell, which the layout
+  // bounds).  The four samples of a thread are reduced side by side
+  // (segmented suffix sums by doubling, only as many steps as the longest
+  // run needs); a warp without runs pays four shuffles and four votes.
+  // dt[k] is cleared for the lanes whose sums went to another lane.
+  auto merge4 = [&](const uint32_t (&rk)[4], uint32_t (&vr)[4], uint32_t (&vg)[4], uint32_t (&vb)[4],
+                    uint32_t (&vn)[4], bool (&dt)[4]) {
+    unsigned dm[4];  // bit i: lane i + 1 continues lane i's run
 #pragma unroll
-        for (uint32_t o = 1; o < 32; o <<= 1) {
-          const uint32_t tr = __shfl_down_sync(0xFFFFFFFFu, vr, o), tg = __shfl_down_sync(0xFFFFFFFFu, vg, o);
-          const uint32_t tb = __shfl_down_sync(0xFFFFFFFFu, vb, o), tn = __shfl_down_sync(0xFFFFFFFFu, vn, o);
-          if (lane + o <= end) {
-            vr += tr;
-            vg += tg;
-            vb += tb;
-            vn += tn;
-          }
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t nxt = __shfl_down_sync(0xFFFFFFFFu, rk[k], 1);
+      dm[k] = __ballot_sync(0xFFFFFFFFu, lane < 31u && dt[k] && nxt == rk[k]);
+    }
+    uint32_t x = dm[0] | dm[1] | dm[2] | dm[3];
+    if (!x) return;
+    uint32_t longest = 0;  // longest run of set bits (an upper bound over the four masks)
+    while (x) {
+      x &= x >> 1;
+      ++longest;
+    }
+    uint32_t end[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) end[k] = (uint32_t)__ffs(~dm[k] & (0xFFFFFFFFu << lane)) - 1u;  // last lane of the run
+    for (uint32_t o = 1; o <= longest; o <<= 1) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (!dm[k]) continue;  // warp-uniform
+        const uint32_t tr = __shfl_down_sync(0xFFFFFFFFu, vr[k], o), tg = __shfl_down_sync(0xFFFFFFFFu, vg[k], o);
+        const uint32_t tb = __shfl_down_sync(0xFFFFFFFFu, vb[k], o), tn = __shfl_down_sync(0xFFFFFFFFu, vn[k], o);
+        if (lane + o <= end[k]) {
+          vr[k] += tr;
+          vg[k] += tg;
+          vb[k] += tb;
+          vn[k] += tn;
         }
-        // the run's first lane carries the run's sums
-        doit = doit && (lane == 0 || !((dm >> (lane - 1)) & 1u));
-        r = vr;
-        g = vg;
-        b = vb;
-        n = vn;
       }
     }
-    if (!doit) return;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dt[k] = dt[k] && (lane == 0 || !((dm[k] >> (lane - 1)) & 1u));
+  };
+
+  // update the dense entry of rank rk with one sample (or a run's sums).
+  // Single-sample modes: pre is the entry's key as read before (see pick_update).
+  auto update = [&](uint32_t rk, uint32_t cell, uint64_t r, uint64_t g, uint64_t b, uint32_t n, uint32_t ix,
+                    uint32_t rgba, uint64_t pre) {
     K[rk] = cell;
     if (PICKLIKE) {
-      if (!pick_update(&E[rk], pick_key<MODE>(ix, level), (uint64_t)rgba | ((uint64_t)ix << 32)))
+      if (!pick_update(&E[rk], pick_key<MODE>(ix, level), (uint64_t)rgba | ((uint64_t)ix << 32), pre))
         atomicOr(&ctr->error, kErrInternal);
       atomicAdd(&cnt[rk], n);
     } else if (small) {
@@ -543,19 +639,33 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
             }
           }
         }
+        uint32_t cell[4], rk[4];
+        bool ok[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const uint64_t i = base + threadIdx.x + (uint64_t)k * blockDim.x;
-          uint32_t rk = kNoRank, cell = 0;
-          if (i < n) {
-            ++seen;
-            cell = point_cell(q[k], I);
-            const uint32_t rr = cell_rank(G, cell) - lo;
-            if (rr < span) rk = rr;
-          }
-          const uint32_t rgba = (uint32_t)q[k].w;
-          acc(rk, cell, rgba & 255u, (rgba >> 8) & 255u, (rgba >> 16) & 255u, 1u, x[k], rgba);
+          ok[k] = i < n;
+          seen += ok[k] ? 1u : 0u;
+          cell[k] = point_cell(q[k], I);
         }
+        cell_ranks4(W, cell, ok, lo, span, rk);
+        uint64_t pre[4];
+        pre_keys4<PICKLIKE>(E, rk, pre);
+        uint32_t vr[4], vg[4], vb[4], vn[4];
+        bool dt[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint32_t rgba = (uint32_t)q[k].w;
+          vr[k] = rgba & 255u;
+          vg[k] = (rgba >> 8) & 255u;
+          vb[k] = (rgba >> 16) & 255u;
+          vn[k] = 1u;
+          dt[k] = rk[k] != kNoRank;
+        }
+        if (merge) merge4(rk, vr, vg, vb, vn, dt);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (dt[k]) update(rk[k], cell[k], vr[k], vg[k], vb[k], vn[k], x[k], (uint32_t)q[k].w, pre[k]);
       }
     } else {
       const uint32_t total = S.cpre[S.nch];
@@ -575,24 +685,48 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
             if (!PICKLIKE) sm[k] = last ? __ldcs(v.stage_in_sum + src) : __ldcg(v.stage_in_sum + src);
           }
         }
+        uint32_t cell[4], rk[4];
+        bool ok[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const uint32_t f = f0 + threadIdx.x + (uint32_t)k * blockDim.x;
-          uint32_t rk = kNoRank, cell = 0;
-          if (f < total) {
-            ++seen;
-            cell = voxel_cell((uint32_t)vr[k].x);
-            const uint32_t rr = cell_rank(G, cell) - lo;
-            if (rr < span) rk = rr;
+          ok[k] = f < total;
+          seen += ok[k] ? 1u : 0u;
+          cell[k] = voxel_cell((uint32_t)vr[k].x);
+        }
+        cell_ranks4(W, cell, ok, lo, span, rk);
+        uint64_t pre[4];
+        pre_keys4<PICKLIKE>(E, rk, pre);
+        // a child's voxel: {cell, rgba, count, picked index} and packed exact sums
+        bool dt[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dt[k] = rk[k] != kNoRank;
+        if (merge) {
+          uint32_t mr[4], mg[4], mb[4], mn[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            mr[k] = (uint32_t)(sm[k].x & kMask40);
+            mg[k] = (uint32_t)((sm[k].x >> 40) | ((sm[k].y & 0xFFFFull) << 24));
+            mb[k] = (uint32_t)(sm[k].y >> 16);
+            mn[k] = (uint32_t)vr[k].z;
           }
-          // a child's voxel: {cell, rgba, count, picked index} and packed exact sums
-          const uint64_t sr = sm[k].x & kMask40, sg = (sm[k].x >> 40) | ((sm[k].y & 0xFFFFull) << 24),
-                         sb = sm[k].y >> 16;
-          acc(rk, cell, sr, sg, sb, (uint32_t)vr[k].z, (uint32_t)vr[k].w, (uint32_t)vr[k].y);
+          merge4(rk, mr, mg, mb, mn, dt);
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (dt[k]) update(rk[k], cell[k], mr[k], mg[k], mb[k], mn[k], 0u, 0u, 0ull);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint64_t sr = sm[k].x & kMask40, sg = (sm[k].x >> 40) | ((sm[k].y & 0xFFFFull) << 24),
+                           sb = sm[k].y >> 16;
+            if (dt[k]) update(rk[k], cell[k], sr, sg, sb, (uint32_t)vr[k].z, (uint32_t)vr[k].w, (uint32_t)vr[k].y, pre[k]);
+          }
         }
       }
     }
+    if (threadIdx.x == 0) S.stage = stg;
     __syncthreads();  // every update of the pass is done
+    const unsigned long long stage = S.stage;
 
     // ---- extract: rank lo + i goes to staging record stage + lo + i (cell
     // order), and the entry is left empty for the next pass or item
@@ -661,8 +795,14 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
   if (lane == 0 && seen) atomicAdd(&S.samples, seen);
   __syncthreads();
   if (threadIdx.x == 0) {
+    if (first) {
+      v.aux[I.g].stage = stg;
+      if (stg + S.D > v.stage_cap) atomicOr(&ctr->error, kErrStageCap);
+    }
+    if (next_item) *next_item = next_it;  // read after this item's last barrier
     atomicAdd(&ctr->vox_passes, (unsigned long long)passes);
     atomicAdd(&ctr->vox_samples, (unsigned long long)S.samples);
+    if (first) atomicMax(&ctr->vox_max_item, (unsigned long long)I.n);
   }
   __syncthreads();
 }

@@ -28,7 +28,8 @@ cudaError_t launch_pyr_down(const BuildArgs& a, const PyrJob* jobs, uint32_t n_j
 cudaError_t launch_scatter(const BuildArgs& a, const uint32_t* chunk_src, const unsigned long long* n_chunks,
                            uint32_t round, int grid, cudaStream_t st);
 cudaError_t launch_nodes(const BuildArgs& a, lod_node_t* nodes, NodeAux* aux, uint32_t* lvl_start,
-                         uint32_t* n_nodes, unsigned long long* leaf_cap, DevCounters* ctr, cudaStream_t st);
+                         uint32_t* n_nodes, unsigned long long* leaf_cap, DevCounters* ctr,
+                         const unsigned long long* refined, cudaStream_t st);
 
 // ----- voxel sampling (Section 4.2) -----
 struct VoxLevel {

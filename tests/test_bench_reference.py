@@ -43,7 +43,7 @@ def test_reference_arm_other_ranks_exit_quietly():
 
 def test_oracle_sample_is_one_definition():
     # the cpu_baseline leg and the reference arm time the oracle on the
-    # same sample: the smallest lower-corner x-y window (1/4096, 1/1024, ...
+    # same sample: the smallest lower-corner x-y window (1/4096, 1/2048, ...
     # of the area) that holds at least the requested number of points
     sys.path.insert(0, ROOT)
     import numpy as np
@@ -52,7 +52,7 @@ def test_oracle_sample_is_one_definition():
     pts = np.zeros((200_000, 4), np.int32)
     pts[:, :3] = rng.integers(0, 1 << 20, size=(200_000, 3))
     s, frac = bench.oracle_sample(pts, min_points=5_000)
-    assert frac == 1.0 / 16 and len(s) >= 5_000
+    assert frac == 1.0 / 32 and len(s) >= 5_000
     side = int(np.floor(np.sqrt(frac) * ((1 << 20) - 1 - 0 + 1)))
     lo = pts[:, :2].min(axis=0)
     assert np.all((s[:, :2] >= lo) & (s[:, :2] < lo + side))
