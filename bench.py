@@ -214,9 +214,10 @@ def cpu_oracle_sample(cloud, T: int, budget_s: float = 12.0) -> dict:
 # the dominant one (the roofline below stays HBM: the path has no dense
 # contraction and no other measured peak applies).
 LIMITERS = {
-    "voxelize": "shared-memory atomics and warp matching (ncu: address-divergence pipe 56 %, DRAM 13 %)",
-    "scatter": "one scattered L2 write request per point (ncu: long-scoreboard stalls, DRAM 30-41 %)",
-    "count": "instruction issue (ncu: 62 % issue active)",
+    "voxelize": "shared-memory pipe, over half of it atomics (ncu: short-scoreboard stalls, 0.6-0.7 shared "
+                "wavefronts per active SM cycle, DRAM 3-6 % on the 20M cut)",
+    "scatter": "scattered stores and load latency (ncu: long-scoreboard stalls, DRAM 45 %, 36 % L2 write hits)",
+    "count": "instruction issue (ncu: 68 % issue active, DRAM 41 %)",
     "bbox": "HBM bandwidth",
 }
 

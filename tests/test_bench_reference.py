@@ -69,12 +69,12 @@ def test_roofline_object_of_the_dominant_kernel():
             "voxelize": {"launches": 24, "total_ms": 4.8, "alg_bytes": 24 * 1.9e8},
             "bbox": {"launches": 4, "total_ms": 0.5, "alg_bytes": 4 * 8e8}}
     pk = {"hbm_gbs": 6785.9, "source": "measured"}
-    r = bench.roofline_of(prof, "aerial50m", pk)
+    r = bench.roofline_of(prof, "indoor1b", pk)
     assert r["kernel"] == "voxelize" and r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert abs(r["achieved"] - 24 * 1.9e8 / 4.8e-3 / 1e9) < 1e-6
     assert abs(r["frac"] - r["achieved"] / 6785.9) < 1e-12
     assert abs(r["avg_launch_ms"] - 0.2) < 1e-12 and r["alg_bytes_per_launch"] == 1.9e8
     assert isinstance(r["traffic"], int) and r["traffic"] > 0  # from profiles/traffic.json
     assert "shared-memory" in r["limiter"]
-    assert bench.roofline_of({}, "aerial50m", pk) is None
+    assert bench.roofline_of({}, "indoor1b", pk) is None
     assert bench.roofline_of(prof, "sphere1m", pk)["traffic"] is None  # no capture of that workload
