@@ -325,7 +325,10 @@ int lod_root_cubes_noalloc(const lod_point_t* const* d_tiles, const uint64_t* n,
  *                   1..8, still capped by the cube and max_depth); default:
  *                   one more level than a surface-like cloud needs to reach
  *                   the leaf threshold.
- *   stream_ctas_per_sm  CTAs per SM of the streaming passes (default 2).
+ *   stream_ctas_per_sm  CTAs per SM of the streaming passes (default: 4
+ *                   for builds of at least 128 chunks of 4096 points per
+ *                   CTA of a 2-per-SM grid, about 160M points on 152 SMs;
+ *                   2 below).
  *   dense_bins_max  counting grids of at most this many cells are counted
  *                   in a dense shared-memory histogram, larger ones through
  *                   per-CTA shared-memory hash tables (8..4096, a power of
@@ -334,7 +337,7 @@ int lod_root_cubes_noalloc(const lod_point_t* const* d_tiles, const uint64_t* n,
  *                   cell order and accumulates them in ranges of what one
  *                   CTA's shared memory holds (5120 to 10240 cells); an
  *                   item needing P >= vox_queue_ranges ranges hands ranges
- *                   2..P to other SMs (default 2; 1: every range stays with
+ *                   2..P to other SMs (default 4; 1: every range stays with
  *                   the item's CTA; at most 4096).
  *   graph_voxel_levels  1: every build captures the launches of all its
  *                   voxel levels (which need no host round trip between
@@ -362,12 +365,12 @@ int lod_get_tuning(lod_tuning_t* t);
 
 /* Autotuner: times lod_build of the caller's cloud (device pointer, n points,
  * params; on `stream`) under candidate tunings, two builds each (the first
- * untimed), by coordinate descent from the defaults: stream_ctas_per_sm 1
- * and 3; root_depth one less and one more than the default; dense_bins_max
- * 512; vox_queue_ranges 1 (never) and 4; in filtered mode
+ * untimed), by coordinate descent from the defaults: stream_ctas_per_sm 2,
+ * 3 and 4; root_depth one less and one more than the default; dense_bins_max
+ * 512; vox_queue_ranges 1 (never) and 2; in filtered mode
  * vox_no_merge 1 — each knob in turn, the others held at the best so far.  Keeps the fastest with lod_set_tuning and
  * returns it in *best (and its build time in *best_ms when not NULL).
- * Results are freed; nothing else is kept.  Costs about 16 builds; like
+ * Results are freed; nothing else is kept.  Costs about 18 builds; like
  * lod_set_tuning it changes process-wide state, so call it while no other
  * build runs.  Returns LOD_ERR_INVALID_ARG for n == 0 or a missing pointer,
  * or the first build error (the previous tuning is then restored).  The

@@ -318,10 +318,10 @@ int lod_autotune(const lod_point_t* d_points, uint64_t n, const lod_params_t* pa
   int rc = time_with(win, &win_ms);
   for (int knob = 0; knob < 5 && rc == LOD_OK; ++knob) {
     std::vector<uint32_t> cand;
-    if (knob == 0) cand = {1u, 3u};         // CTAs per SM of the streaming passes (default 2)
+    if (knob == 0) cand = {2u, 3u, 4u};     // CTAs per SM of the streaming passes (default 2 or 4 by size)
     if (knob == 1) cand = std::vector<uint32_t>(depths.begin() + 1, depths.end());
     if (knob == 2) cand = {512u};           // dense shared histograms up to 512 cells (default 4096)
-    if (knob == 3) cand = {1u, 4u};         // an item's rank ranges: never handed to other SMs, from 4 (default 2)
+    if (knob == 3) cand = {1u, 2u};         // an item's rank ranges: never handed to other SMs, from 2 (default 4)
     if (knob == 4 && p.mode == LOD_FILTER) cand = {1u};  // no warp merge of same-cell samples
     for (uint32_t c : cand) {
       lod_tuning_t t = win;

@@ -279,7 +279,7 @@ uint32_t ceil_log4(double x) {
 // level), capped at 256^3 cells, the cube's own size and max_depth.
 std::atomic<uint32_t> g_tune_root_depth{0};
 std::atomic<uint32_t> g_tune_ctas_per_sm{0};
-std::atomic<uint32_t> g_tune_queue_ranges{0};  // 0: default (2), 1: an item's ranges stay in its CTA
+std::atomic<uint32_t> g_tune_queue_ranges{0};  // 0: default (4), 1: an item's ranges stay in its CTA
 std::atomic<uint32_t> g_tune_range_cells{0};   // 0: what the shared memory holds
 std::atomic<uint32_t> g_tune_dense_bins{0};  // 0: kSmemBins
 std::atomic<uint32_t> g_tune_graph{0};       // 1: the voxel levels run as one CUDA graph
@@ -741,8 +741,14 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
 
   auto sh = std::make_shared<SharedBuffers>();
   LOD_CK(cudaGetDevice(&sh->device));
+  // CTAs per SM of the streaming passes: by default 2, and 4 for builds of
+  // at least 128 chunks per CTA of the 2-per-SM grid (about 160M points),
+  // whose longer per-CTA chunk runs balance better in smaller pieces
+  // (measured: 1B points 2.4 ms faster per build; 50M points 2 % slower
+  // with 4)
   const uint32_t cps = g_tune_ctas_per_sm.load();
-  const int grid = (int)(cps ? cps : 2) * sm_count();
+  const uint32_t cps_default = n_chunks0 >= 128ull * 2u * (uint64_t)sm_count() ? 4u : 2u;
+  const int grid = (int)(cps ? cps : cps_default) * sm_count();
   Uploader up_(st);
   Prof prof(st);
 #define LOD_LAUNCH(name, bytes, call) \
@@ -1256,7 +1262,7 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
       vl.next_order = (l == 0 || weighted) ? nullptr : d_order.as<uint32_t>();
       {
         const uint32_t q = g_tune_queue_ranges.load();
-        vl.queue_ranges = q == 0 ? 2u : (q == 1 ? 0xFFFFFFFFu : q);
+        vl.queue_ranges = q == 0 ? 4u : (q == 1 ? 0xFFFFFFFFu : q);
         vl.range_cells = g_tune_range_cells.load();
       }
       vl.no_merge = g_tune_no_merge.load();

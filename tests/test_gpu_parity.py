@@ -163,8 +163,8 @@ def test_autotune_picks_a_candidate_and_keeps_results(lod):
     d = torch.from_numpy(pts).cuda()
     try:
         best = lod.autotune(d, 5000, 0)
-        assert best["stream_ctas_per_sm"] in (0, 1, 3) and best["ms"] > 0
-        assert best["vox_queue_ranges"] in (0, 1, 4) and best["dense_bins_max"] in (0, 512)
+        assert best["stream_ctas_per_sm"] in (0, 2, 3, 4) and best["ms"] > 0
+        assert best["vox_queue_ranges"] in (0, 1, 2) and best["dense_bins_max"] in (0, 512)
         assert lod.get_tuning()["stream_ctas_per_sm"] == best["stream_ctas_per_sm"]
         compare(gpu_build(lod, pts, 5000, 0), oracle.build(pts, 5000, 0, 21), inp=pts)
     finally:
