@@ -115,8 +115,8 @@ struct DevCounters {
   unsigned long long new_points;      // points inside them
   unsigned long long stage_used[2];   // staging records bump allocators
   unsigned long long level_voxels;    // voxels of the level just scanned
-  unsigned long long vox_retries;     // voxel items that needed more table passes
-  unsigned long long vox_passes;      // table passes over all voxel items
+  unsigned long long vox_retries;     // voxel items whose cells need several accumulate passes
+  unsigned long long vox_passes;      // passes over samples (mark and accumulate) of all voxel items
   unsigned long long vox_samples;     // samples read by all table passes (re-reads included)
   unsigned long long vox_max_item;    // samples of the level's largest item (statistics)
   unsigned int error;                 // nonzero: a kernel detected a problem

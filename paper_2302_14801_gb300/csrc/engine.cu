@@ -1314,7 +1314,7 @@ static int run_build_impl(const TileInput* tin, uint32_t nt, const lod_params_t&
         prof.recs[vox_rec[l] - 1].bytes = 16.0 * (double)(leaf_cap[kMaxLevels + 1 + l + 1] + V_child + lv);
       if (debug_stats())
         std::fprintf(stderr, "[lod] level %d: items %u (leaf points %llu, child voxels %llu) -> voxels %llu, "
-                     "retried items %llu, table passes %llu, partition units %u, samples read %llu, largest item %llu\n", l,
+                     "items with several rank ranges %llu, sample passes %llu, queued ranges %u, samples read %llu, largest item %llu\n", l,
                      pref[(size_t)l * pstride + nt], (unsigned long long)leaf_cap[kMaxLevels + 1 + l + 1],
                      (unsigned long long)V_child, (unsigned long long)lv,
                      (unsigned long long)lctr[l].vox_retries, (unsigned long long)lctr[l].vox_passes,

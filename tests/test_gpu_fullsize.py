@@ -114,7 +114,8 @@ def test_filtered_wide_sums_against_oracle(lod, max_depth):
 # A whole-cloud comparison beyond the 50M aerial cloud: 100M points of the
 # indoor recipe (numpy generator), both modes, at the bench's settings.  Its
 # log-normal clusters need refinement rounds and its deep volumetric levels
-# overflow the voxel tables into partitions, the paths the 1B build takes.
+# hold more occupied cells per octant than one accumulate pass, so items take
+# several rank ranges: the paths the 1B build takes.
 
 @pytest.fixture(scope="module")
 def indoor100m():
