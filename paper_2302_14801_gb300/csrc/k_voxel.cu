@@ -56,6 +56,35 @@ constexpr uint64_t kNarrowMaxSamples = 0xFFFFFFFFull / 255;  // 32-bit channel s
 constexpr uint64_t kSmallMaxSamples = 0xFFFFu;               // 24-bit sums and a 16-bit count cannot
 constexpr uint64_t kMask40 = (1ull << 40) - 1;
 constexpr uint32_t kNoRank = 0xFFFFFFFFu;
+// Filtered staging records of cells of fewer than kPackMaxCount points carry
+// their exact sums in the record's last word (10 bits per channel), so that
+// neither the extraction nor the next level up touches the 16-byte sums
+// array for them; larger cells keep the last word kNone and their sums in
+// that array.
+constexpr uint64_t kPackMaxCount = 1024;
+
+// A channel's exact sum s over n < 1024 points and its rounded mean
+// m = floor((s + floor(n/2)) / n) determine the remainder
+// s + floor(n/2) - m n, which lies in [0, n); the three remainders, 10 bits
+// each, fit below bit 30 (so the word never equals kNone).
+__device__ __forceinline__ uint32_t pack_remainders(uint64_t sr, uint64_t sg, uint64_t sb, uint64_t n, uint32_t m) {
+  const uint32_t nn = (uint32_t)n, h = nn >> 1;
+  const uint32_t rr = (uint32_t)sr + h - (m & 255u) * nn;
+  const uint32_t rg = (uint32_t)sg + h - ((m >> 8) & 255u) * nn;
+  const uint32_t rb = (uint32_t)sb + h - ((m >> 16) & 255u) * nn;
+  return rr | (rg << 10) | (rb << 20);
+}
+
+// The sums of a packed record {cell, mean rgba, n, remainders} in the
+// layout of the sums array: {R | G << 40, G >> 24 | B << 16}.
+__device__ __forceinline__ ulonglong2 unpack_sums(const int4& rec) {
+  const uint32_t m = (uint32_t)rec.y, nn = (uint32_t)rec.z, w = (uint32_t)rec.w, h = nn >> 1;
+  const uint64_t sr = (m & 255u) * nn + (w & 1023u) - h;
+  const uint64_t sg = ((m >> 8) & 255u) * nn + ((w >> 10) & 1023u) - h;
+  const uint64_t sb = ((m >> 16) & 255u) * nn + ((w >> 20) & 1023u) - h;
+  return make_ulonglong2(sr | (sg << 40), (sg >> 24) | (sb << 16));
+}
+
 // an item's samples prefetched into L2 when it starts: at most this many
 // bytes (152 SMs x 256 KB stays well inside the 126 MB L2)
 constexpr uint64_t kPrefetchBytes = 256u * 1024u;
@@ -460,7 +489,9 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
           ++seen;
           // publish the child's voxel (idempotent); an array found too
           // small makes the build rerun with the exact size
-          if (lead && dst[k] < v.dense_cap) v.dense[dst[k]] = vr[k];
+          // (filtered: without the packed sums, pick_index none)
+          if (lead && dst[k] < v.dense_cap)
+            v.dense[dst[k]] = PICKLIKE ? vr[k] : make_int4(vr[k].x, vr[k].y, vr[k].z, (int)kNone);
         }
       }
       mark_cells4(W, cell, ok);
@@ -673,16 +704,28 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
       for (uint32_t f0 = 0; f0 < total; f0 += 4u * blockDim.x) {
         int4 vr[4];
         ulonglong2 sm[4];
+        uint64_t src[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const uint32_t f = f0 + threadIdx.x + (uint32_t)k * blockDim.x;
           vr[k] = make_int4(0, 0, 0, 0);
           sm[k] = make_ulonglong2(0ull, 0ull);
+          src[k] = 0;
           if (f < total) {
             while (f >= S.cpre[ci + 1]) ++ci;
-            const uint64_t src = S.cstage[ci] + (f - S.cpre[ci]);
-            vr[k] = last ? __ldcs(v.stage_in + src) : __ldcg(v.stage_in + src);
-            if (!PICKLIKE) sm[k] = last ? __ldcs(v.stage_in_sum + src) : __ldcg(v.stage_in_sum + src);
+            src[k] = S.cstage[ci] + (f - S.cpre[ci]);
+            vr[k] = last ? __ldcs(v.stage_in + src[k]) : __ldcg(v.stage_in + src[k]);
+          }
+        }
+        if (!PICKLIKE) {
+          // exact sums: in the record (cells of fewer than 1024 points), else
+          // in the sums array
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint32_t f = f0 + threadIdx.x + (uint32_t)k * blockDim.x;
+            if (f >= total) continue;
+            if ((uint32_t)vr[k].w != kNone) sm[k] = unpack_sums(vr[k]);
+            else sm[k] = last ? __ldcs(v.stage_in_sum + src[k]) : __ldcg(v.stage_in_sum + src[k]);
           }
         }
         uint32_t cell[4], rk[4];
@@ -736,6 +779,7 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
       int4 rec;
       rec.x = (int)parent_cell(cell, I);
       ulonglong2 sums = make_ulonglong2(0ull, 0ull);
+      bool packed = false;  // filtered: the sums travel in the record itself
       if (PICKLIKE) {
         const ulonglong2 e = E[i];
         const uint32_t c32 = cnt[i];
@@ -778,15 +822,21 @@ __device__ __forceinline__ void vox_item(const BuildArgs& a, const VoxLevel& v, 
           cnt[i] = 0u;
         }
         K[i] = 0u;  // the next item's layout may put an accumulator here
-        rec.y = (int)mean_rgba(sr, sg, sb, n);
+        const uint32_t m = mean_rgba(sr, sg, sb, n);
+        rec.y = (int)m;
         rec.z = (int)n;
         rec.w = (int)kNone;
-        sums.x = sr | (sg << 40);
-        sums.y = (sg >> 24) | (sb << 16);
+        if (n < kPackMaxCount) {
+          rec.w = (int)pack_remainders(sr, sg, sb, n, m);
+          packed = true;
+        } else {
+          sums.x = sr | (sg << 40);
+          sums.y = (sg >> 24) | (sb << 16);
+        }
       }
       if (o < v.stage_cap) {  // else the reservation reported kErrStageCap
         v.stage_out[o] = rec;
-        if (!PICKLIKE) v.stage_out_sum[o] = sums;
+        if (!PICKLIKE && !packed) v.stage_out_sum[o] = sums;
       }
     }
     __syncthreads();
@@ -1042,9 +1092,13 @@ __global__ void __launch_bounds__(256) k_copy_items(BuildArgs a, VoxLevel v) {
                      (it - v.item_prefix[t]);
   const NodeAux ca = v.aux[g];
   if (ca.dense + ca.occ > v.dense_cap) return;  // the build is redone with a larger array
+  const bool filt = a.mode == LOD_FILTER;  // records may carry their sums packed
   for (uint32_t i = threadIdx.x; i < ca.occ; i += blockDim.x) {
-    v.dense[ca.dense + i] = v.stage_out[ca.stage + i];
-    if (v.root_sums) v.root_sums[ca.dense + i] = v.stage_out_sum[ca.stage + i];
+    int4 rec = v.stage_out[ca.stage + i];
+    const bool packed = filt && (uint32_t)rec.w != kNone;
+    if (v.root_sums) v.root_sums[ca.dense + i] = packed ? unpack_sums(rec) : v.stage_out_sum[ca.stage + i];
+    if (filt) rec.w = (int)kNone;
+    v.dense[ca.dense + i] = rec;
   }
 }
 
